@@ -1,0 +1,281 @@
+"""Pins of the FP64 oracle against what the paper and the mathematics fix (CPU).
+
+Each test names what it pins.  None compares the oracle with itself: closed
+forms, a brute-force dense solve written separately, conservation laws,
+symmetries and limits that reduce to textbook results.
+"""
+import math
+
+import numpy as np
+import pytest
+from scipy import integrate
+
+from paper_2106_02764_gb300 import inputs as I
+from oracle import bte, dense, fourier
+
+
+def _solve(wl, **kw):
+    pr = bte.Problem.from_workload(wl)
+    return pr, bte.solve_mode_B(pr, **kw)
+
+
+# ---------------------------------------------------------------- p1 pore-free
+@pytest.mark.parametrize("quad", [I.circle_quadrature(8), I.projected_quadrature(8, 4),
+                                  I.sphere_quadrature(8, 4)])
+def test_porefree_closed_form(quad):
+    """Pore-free periodic cell: the exact discrete solution is T_L linear with
+    slope -dT/L and T_o = T_L - Lambda_m p_x a (upwind differencing is exact on
+    linear fields); its upwinded face flux is kappa_bulk + (h/2) sum |K_ox|.
+    Pins E1 (diagonal and jump), E2 weights and K weights (c1, c2, c8)."""
+    L = 100e-9
+    wl = I.make_2d("pf", 8, L, [], 3, quad)
+    pr, sol = _solve(wl)
+    od = pr.ords
+    h = L / 8
+    expect = 150.0 + 0.5 * h * np.sum(np.abs(od.K[:, 0]))
+    assert abs(sol.kappa - expect) < 1e-12 * expect
+    x = (pr.mesh.coords[:, 0] + 0.5) * h
+    lin = -(x - x.mean()) / L
+    assert np.abs(sol.T_L - lin).max() < 1e-12
+    # the Fourier first guess is exact, so Algorithm 1 converges in one pass
+    solA = bte.solve_mode_A(pr, tol=1e-14, max_iter=3)
+    assert abs(solA.history[0] - expect) < 1e-12 * expect
+    # kappa_bulk recovered by the discrete flux weights (c2)
+    assert abs(np.sum(od.K[:, 0] * od.lam * od.p[:, 0]) - 150.0) < 1e-11
+
+
+def test_porefree_3d_periodic():
+    L = 60e-9
+    mask = np.ones((4, 4, 4), np.uint8)
+    k, lam = I.mfp_bins(2)
+    wl = I.Workload("pf3", 3, (4, 4, 4), (L, L, L), mask, (1, 1, 1), 1.0, k, lam,
+                    I.sphere_quadrature(4, 2))
+    pr, sol = _solve(wl)
+    expect = 150.0 + 0.5 * (L / 4) * np.sum(np.abs(pr.ords.K[:, 0]))
+    assert abs(sol.kappa - expect) < 1e-12 * expect
+
+
+def test_discrete_bulk_tends_to_kappa_bulk():
+    """As h -> 0 the upwind numerical-diffusion term vanishes."""
+    vals = []
+    for n in (8, 16, 32):
+        wl = I.make_2d("pf", n, 100e-9, [], 4, I.circle_quadrature(8))
+        pr = bte.Problem.from_workload(wl)
+        vals.append(bte.kappa_bulk_discrete(pr) - 150.0)
+    assert vals[0] > 0 and abs(vals[1] / vals[0] - 0.5) < 1e-12 and abs(vals[2] / vals[1] - 0.5) < 1e-12
+
+
+# ---------------------------------------------------------------- p2 dense brute force
+def _wall_map(pr, d):
+    m = {}
+    for f, (c, a, sgn) in enumerate(pr.mesh.walls):
+        xyz = tuple(int(v) for v in pr.mesh.coords[c])
+        m[f] = d["walls"][(xyz, int(a), int(sgn))]
+    return m
+
+
+@pytest.mark.parametrize("case", ["2d", "3d", "2d_s"])
+def test_dense_brute_force(case):
+    if case.startswith("2d"):
+        wl = I.small_2d(n=4, porosity=0, n_bins=2, n_phi=8, s_seed=3 if case == "2d_s" else None)
+        wl.mask = np.ones((1, 4, 4), np.uint8)
+        wl.mask[0, 1:3, 1:3] = 0
+    else:
+        wl = I.small_film(n=4, nz=2, porosity=0, n_bins=2, n_phi=4, n_mu=2)
+        wl.mask[:, 1:3, 1:3] = 0
+    pr, sol = _solve(wl, rtol=1e-13)
+    d = dense.dense_from_workload(wl)
+    assert d["residual"] < 1e-10
+    wm = _wall_map(pr, d)
+    fw = bte.fields(pr, sol)
+    inv = {v: k for k, v in wm.items()}
+    X = np.concatenate([np.concatenate([fw["T"][o] for o in range(pr.ords.n)]), sol.T_L,
+                        np.array([sol.T_w[inv[k]] for k in range(pr.mesh.nw)])])
+    Xd = np.concatenate([d["T"].ravel(), d["T_L"], d["T_w"]])
+    b = d["A"] @ Xd
+    # the oracle's full solution satisfies every row of the dense system
+    assert np.linalg.norm(d["A"] @ X - b) < 1e-10 * np.linalg.norm(b)
+    # values agree to the conditioning of the dense least-squares solve
+    assert abs(sol.kappa - d["kappa"]) < 1e-9 * abs(d["kappa"])
+    assert np.abs(sol.T_L - d["T_L"]).max() < 1e-9
+    for f in range(pr.mesh.nw):
+        assert abs(sol.T_w[f] - d["T_w"][wm[f]]) < 1e-9
+    for o in range(pr.ords.n):
+        assert np.abs(fw["T"][o] - d["T"][o]).max() < 1e-9
+
+
+# ---------------------------------------------------------------- p3 conservation
+def test_conservation_config1():
+    """Net heat flux through every x-section is the same at the fixed point,
+    every cell's upwinded face fluxes balance (div J = 0, the condition that
+    defines T_L in Sec. 2) and every wall face carries zero net flux."""
+    wl = I.config1()
+    pr, sol = _solve(wl)
+    fw = bte.fields(pr, sol)
+    phis = fw["phis"]
+    assert np.abs(phis - phis[0]).max() < 1e-9 * abs(phis[0])
+    me, od = pr.mesh, pr.ords
+    tr = bte.Transport(pr)
+    div = np.zeros(me.nc)
+    wall_net = np.zeros(me.nw)
+    for o, T in fw["T"].items():
+        for a in me.axes:
+            k = od.K[o, a] / me.h[a]
+            for side, sgn in ((0, -1), (1, 1)):
+                kn = k * sgn                     # outward normal component
+                j = me.nbr[:, a, side]
+                f = me.wall[:, a, side]
+                if kn > 0:
+                    up = T
+                else:
+                    up = np.where(j >= 0, T[np.maximum(j, 0)] + me.jump[:, a, side],
+                                  sol.T_w[np.maximum(f, 0)])
+                div += kn * up
+                wf = f >= 0
+                np.add.at(wall_net, f[wf], (kn * up)[wf])
+    scale = np.abs(od.K).sum() / me.h[0]
+    assert np.abs(div).max() < 1e-9 * scale
+    assert np.abs(wall_net).max() < 1e-9 * scale
+
+
+# ---------------------------------------------------------------- p4 thin film
+def _film(nz, n_mu, lam, t, lx=1e-15):
+    mask = np.ones((nz, 2, 2), np.uint8)
+    wl = I.Workload("film", 3, (2, 2, nz), (lx, lx, t), mask, (1, 1, 0), 1.0,
+                    np.array([150.0]), np.array([lam]), I.sphere_quadrature(4, n_mu))
+    return wl
+
+
+def test_film_discrete_recurrence():
+    """Gray film, diffuse walls at z = 0, t: T_o = a x + c_k with the discrete
+    recurrence c_k = (beta_z c_{k-1} - Lambda p_x a) / (1 + beta_z), c_{-1} = 0,
+    solved in closed form (geometric series).  Pins walls (E3), 3D, c14."""
+    lam, t, nz = 40e-9, 30e-9, 12
+    wl = _film(nz, 6, lam, t, lx=20e-9)
+    pr, sol = _solve(wl, rtol=1e-13)
+    od = pr.ords
+    hz = t / nz
+    bz = od.lam * np.abs(od.p[:, 2]) / hz
+    r = bz / (1 + bz)
+    geo = r * (1 - r ** nz) / (1 - r)
+    kx_lp = od.K[:, 0] * od.lam * od.p[:, 0]
+    hx = wl.lengths[0] / 2
+    expect = 0.5 * hx * np.abs(od.K[:, 0]).sum() + kx_lp.sum() - (kx_lp * geo).sum() / nz
+    assert abs(sol.kappa - expect) < 1e-11 * expect
+
+
+def test_film_fuchs_sondheimer_limit():
+    """Fine z grid and polar quadrature approach the Fuchs-Sondheimer result
+    kappa / kappa_b = 1 - 3/(2 delta) int_0^1 mu (1 - mu^2)(1 - exp(-delta/mu)) dmu
+    once the x-direction numerical-diffusion term (h_x/2) sum |K_ox| of the
+    pore-free closed form is taken off."""
+    lam, t = 50e-9, 25e-9
+    delta = t / lam
+    fs = 1 - 1.5 / delta * integrate.quad(lambda m: m * (1 - m * m) * (1 - math.exp(-delta / m)),
+                                          0, 1, limit=200)[0]
+    errs = []
+    for nz, n_mu in ((32, 8), (128, 16)):
+        wl = _film(nz, n_mu, lam, t, lx=1e-10)
+        pr, sol = _solve(wl, rtol=1e-10, maxiter=20)
+        offset = 0.5 * (wl.lengths[0] / 2) * np.abs(pr.ords.K[:, 0]).sum()
+        errs.append(abs((sol.kappa - offset) / 150.0 - fs))
+    assert errs[1] < 0.5 * errs[0] and errs[1] < 5e-3
+
+
+# ---------------------------------------------------------------- p5 small-MFP limit
+def test_small_mfp_tends_to_fourier():
+    """Single bin with Lambda << L and h = Lambda / 2: kappa_eff relative to the
+    discrete bulk value approaches kappa_fourier / kappa_bulk of the same mask,
+    with a gap that shrinks as Lambda / L does (Knudsen layers)."""
+    L = 100e-9
+    gaps = []
+    for ratio, n in ((10, 20), (20, 40)):
+        wl = I.make_2d("x", n, L, [I.circle_pore(L, L, 0.2)], 1, I.circle_quadrature(16))
+        wl.lambda_m = np.array([L / ratio])
+        wl.kappa_m = np.array([150.0])
+        pr, sol = _solve(wl, rtol=1e-10, restart=100, maxiter=50)
+        kF = fourier.solve_fourier(pr.mesh, 150.0)["kappa"] / 150.0
+        gaps.append(abs(sol.kappa / bte.kappa_bulk_discrete(pr) - kF))
+    assert gaps[1] < 0.6 * gaps[0] and gaps[1] < 0.05
+
+
+# ---------------------------------------------------------------- p6 Fourier
+def test_fourier_porefree_exact():
+    wl = I.make_2d("pf", 16, 100e-9, [], 1, I.circle_quadrature(4))
+    me = bte.Mesh(wl.mask, wl.lengths, wl.periodic, 1.0, 2)
+    r = fourier.solve_fourier(me, 150.0)
+    assert abs(r["kappa"] - 150.0) < 1e-10
+    x = (me.coords[:, 0] + 0.5) / 16
+    assert np.abs(r["T"] + (x - x.mean())).max() < 1e-12
+
+
+@pytest.mark.parametrize("phi", [0.05, 0.1, 0.2, 0.25])
+def test_fourier_eucken_maxwell(phi):
+    """Circular pores: kappa_fourier / kappa_bulk -> (1 - phi)/(1 + phi)
+    (Sec. 8 reports < 1 % agreement); the voxel staircase error shrinks with N."""
+    L = 100e-9
+    devs = []
+    for n in (64, 128):
+        wl = I.make_2d("em", n, L, [I.circle_pore(L, L, phi)], 1, I.circle_quadrature(4))
+        me = bte.Mesh(wl.mask, wl.lengths, wl.periodic, 1.0, 2)
+        k = fourier.solve_fourier(me, 150.0)["kappa"] / 150.0
+        ph = wl.porosity
+        devs.append(abs(k / ((1 - ph) / (1 + ph)) - 1))
+    assert devs[1] < devs[0] and devs[1] < 0.01
+
+
+# ---------------------------------------------------------------- p7 symmetries
+def _asym_wl(n=8):
+    L = 100e-9
+    return I.make_2d("asym", n, L, [I.square_pore(L, L, 0.1, x=0.3 * L, y=0.6 * L)], 2,
+                     I.circle_quadrature(8))
+
+
+def test_rotation_symmetry():
+    wl = _asym_wl()
+    pr, sol = _solve(wl)
+    wr = _asym_wl()
+    wr.mask = np.ascontiguousarray(np.transpose(wl.mask, (0, 2, 1)))
+    wr.grad_axis = 1
+    prr, solr = _solve(wr)
+    assert abs(sol.kappa - solr.kappa) < 1e-11 * sol.kappa
+
+
+def test_roll_and_mirror_symmetry():
+    wl = _asym_wl()
+    pr, sol = _solve(wl)
+    for sh in ((2, 0), (0, 3), (5, 1)):
+        w2 = _asym_wl()
+        w2.mask = np.roll(wl.mask, sh, axis=(2, 1))
+        _, s2 = _solve(w2)
+        assert abs(sol.kappa - s2.kappa) < 1e-11 * sol.kappa
+    w3 = _asym_wl()
+    w3.mask = np.ascontiguousarray(wl.mask[:, :, ::-1])
+    p3, s3 = _solve(w3)
+    assert abs(sol.kappa - s3.kappa) < 1e-11 * sol.kappa
+    g = bte.to_grid(pr, sol.T_L)
+    g3 = bte.to_grid(p3, s3.T_L)
+    ok = ~np.isnan(g)
+    assert np.abs(g3[:, :, ::-1][ok] + g[ok]).max() < 1e-11
+
+
+# ---------------------------------------------------------------- p8 folding
+def test_projected_folding():
+    L = 100e-9
+    pores = [I.circle_pore(L, L, 0.2)]
+    a = I.make_2d("f", 8, L, pores, 3, I.projected_quadrature(8, 4, fold=True))
+    b = I.make_2d("u", 8, L, pores, 3, I.projected_quadrature(8, 4, fold=False))
+    pa, sa = _solve(a, rtol=1e-13)
+    pb, sb = _solve(b, rtol=1e-13)
+    assert abs(sa.kappa - sb.kappa) < 1e-12 * sa.kappa
+    assert np.abs(sa.T_L - sb.T_L).max() < 1e-12
+
+
+# ---------------------------------------------------------------- p9 schemes
+def test_mode_a_equals_mode_b():
+    wl = I.small_2d(n=12, porosity=0.2, n_bins=3, n_phi=8)
+    pr = bte.Problem.from_workload(wl)
+    sb = bte.solve_mode_B(pr, rtol=1e-13)
+    sa = bte.solve_mode_A(pr, tol=1e-15, max_iter=2000)
+    assert abs(sa.kappa - sb.kappa) < 1e-11 * sb.kappa
+    assert np.abs(sa.T_L - sb.T_L).max() < 1e-10
