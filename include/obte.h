@@ -1,0 +1,197 @@
+/*
+ * obte.h -- C ABI of libobte, a GB300 (sm_103a) solver for the steady-state
+ * anisotropic-mean-free-path phonon Boltzmann transport equation (aMFP-BTE)
+ * on periodic Cartesian voxel meshes, after OpenBTE (G. Romano, arXiv
+ * 2106.02764).
+ *
+ * What is solved (App. A of the paper, upwind finite volumes, Eq. iter2):
+ * for every ordinate o = (MFP bin m, direction s) and every solid cell i
+ *
+ *   (s_i + sum_a Lambda_m |p_a| / h_a) T_oi
+ *       - sum_{inflow faces} (Lambda_m |p_a| / h_a) u_o  =  s_i T_Li
+ *
+ * where u_o is the upwind value across the face: the neighbour's T_o (plus
+ * the applied jump +dT / -dT across the low / high side of the periodic x
+ * period, the P term of App. A), or the temperature of a diffuse wall face.
+ * The lattice temperature is T_L = sum_o a_o T_o with
+ * a_o = w_s (kappa_m / Lambda_m^2) / sum_m' (kappa_m' / Lambda_m'^2) (Sec. 2),
+ * every wall face thermalises to the flux-weighted mean of the ordinates
+ * leaving into it (Sec. 2, R_mu_nu), with flux weights
+ * K_o = d_ang kappa_m w_s p_s / Lambda_m, and kappa_eff is the upwinded heat
+ * flux through the solid faces of the plane x = 0 (Eq. keff, hot-contact form
+ * of App. A) times L_x / (dT * cross-section).  The system is iterated to its
+ * fixed point as in Algorithm 1 (Sec. 3), starting from a Fourier solution
+ * (App. B).
+ *
+ * Conventions
+ *  - Every function returns an obte_status; obte_last_error() gives a message.
+ *  - The caller owns every host array; the library copies what it needs and
+ *    keeps no caller pointer.
+ *  - Device memory is taken only through obte_device_cfg.alloc/free when they
+ *    are given (cudaMalloc/cudaFree otherwise) and work is enqueued on
+ *    obte_device_cfg.cuda_stream (a cudaStream_t; NULL = a stream the library
+ *    creates).  Functions that return results to host memory synchronise that
+ *    stream.
+ *  - Call order: create -> create_mesh -> set_material -> [set_scattering_scale]
+ *    -> solve -> get_* / kappa_grad_s.  Out of order: OBTE_ESTATE.
+ *  - One context per host thread at a time.
+ *  - Lengths are in metres, conductivities in W/m/K, temperatures in K.
+ */
+#ifndef OBTE_H
+#define OBTE_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct obte_ctx obte_ctx;
+
+typedef enum {
+  OBTE_OK = 0,
+  OBTE_EINVAL = -1,         /* invalid argument (message says which)            */
+  OBTE_ESTATE = -2,         /* call out of order                                */
+  OBTE_ECUDA = -3,          /* a CUDA call failed                               */
+  OBTE_ENOMEM = -4,         /* device allocation failed                         */
+  OBTE_NOT_CONVERGED = -5,  /* max_iter reached; results are readable           */
+  OBTE_ENONFINITE = -6,     /* NaN or Inf in the inputs or in the iterate       */
+  OBTE_ETIMEOUT = -7        /* reserved: a bounded device-side wait expired      */
+} obte_status;
+
+typedef enum { OBTE_FP64 = 0, OBTE_MIXED = 1 } obte_precision;
+
+typedef struct {
+  void* (*alloc)(size_t bytes, void* user); /* NULL: cudaMalloc                  */
+  void (*free)(void* ptr, void* user);      /* NULL: cudaFree                    */
+  void* user;
+  void* cuda_stream;                        /* cudaStream_t, NULL: library stream */
+  int device;                               /* CUDA device ordinal               */
+} obte_device_cfg;
+
+typedef struct {
+  int precision;        /* obte_precision.  FP64: every step in double.  MIXED:
+                           transport sweeps in float; T_L, flux, kappa and
+                           wall sums, the periodic jump term and the
+                           convergence test in double                          */
+  double tol;           /* stop when |kappa_n - kappa_{n-1}| <= tol |kappa_n|
+                           (Algorithm 1); <= 0 disables                        */
+  double tol_TL;        /* and max_i |T_L,n - T_L,n-1| <= tol_TL (K); <= 0 off  */
+  int max_iter;         /* iteration cap; reaching it gives OBTE_NOT_CONVERGED  */
+  int min_iter;         /* never stop before this many iterations              */
+  int check_every;      /* iterations per CUDA-graph launch between host checks */
+  int fourier_max_iter; /* CG iterations for the Fourier first guess (0: auto) */
+  double fourier_tol;   /* relative CG residual (0: auto)                      */
+  int group_size;       /* ordinates per thread block (0: autotuned)           */
+  int rows_per_thread;  /* mesh rows per thread (0: autotuned)                 */
+  int use_graph;        /* 1: capture check_every iterations in a CUDA graph   */
+  int profile;          /* 1: time every sweep / finalize launch with CUDA
+                           events recorded on the solve stream (stats below)   */
+} obte_solve_opts;
+
+#define OBTE_MAX_HISTORY 4096
+
+typedef struct {
+  int iterations;             /* source iterations run                            */
+  int fourier_iterations;     /* CG iterations of the first guess                 */
+  int converged;              /* 1 if the stopping test passed                    */
+  double kappa_eff;           /* W/m/K                                            */
+  double delta_TL;            /* max |T_L,n - T_L,n-1| of the last iteration (K)  */
+  double time_fourier_ms;     /* device time of the first guess                   */
+  double time_iter_ms;        /* device time of the source iterations             */
+  double time_total_ms;       /* device time of obte_solve                        */
+  double updates_per_s;       /* N_solid * N_ordinates * iterations / time_iter   */
+  int group_size, rows_per_thread, threads_per_block, n_groups;
+  int n_sweeps;               /* sweep launches timed when opts.profile = 1       */
+  double time_sweep_ms;       /* summed device time of those sweep launches       */
+  double time_finalize_ms;    /* summed device time of the finalize launches      */
+  int n_history;              /* entries of kappa_history                         */
+  double kappa_history[OBTE_MAX_HISTORY];
+} obte_solve_stats;
+
+/* Fill opts with defaults: FP64, tol 1e-6, max_iter 2000, check_every 8. */
+void obte_default_opts(obte_solve_opts* opts);
+
+/* Create a context on cfg->device.  cfg may be NULL (defaults: device 0). */
+int obte_create(obte_ctx** out, const obte_device_cfg* cfg);
+
+/* Mesh and geometry (Sec. 6; App. A, R_ij, R^P_ij, g_si).
+ *  dim        2 or 3 (2: nz must be 1 and lz is ignored)
+ *  nx,ny,nz   cells per axis; lx,ly,lz domain lengths (m)
+ *  solid_mask host uint8 [nz][ny][nx] (x fastest), nonzero = solid, 0 = pore
+ *  periodic   host int[3]; 1 = periodic axis, 0 = diffuse walls at both ends
+ *  grad_axis  axis of the applied temperature jump (must be periodic)
+ *  delta_T    applied jump across one period (K), nonzero
+ * After mapping grad_axis to the sweep's x axis, a periodic y (z) axis needs
+ * ny (nz) to be a multiple of nx; OBTE_EINVAL otherwise. */
+int obte_create_mesh(obte_ctx* ctx, int dim, int nx, int ny, int nz, double lx, double ly,
+                     double lz, const uint8_t* solid_mask, const int periodic[3],
+                     int grad_axis, double delta_T);
+
+/* Material and angular quadrature (Sec. 5; aMFP interpolation of App. A,
+ * F_ml = Lambda_m s_l).
+ *  kappa_m, lambda_m  host double[n_mfp]: bin conductivity (W/m/K), MFP (m) > 0
+ *  dirs               host double[n_dir][3]: directions; in 2D only x, y are
+ *                     used (projected directions may have |p| < 1)
+ *  w                  host double[n_dir]: weights, sum 1
+ *  angular_dim        2 (in-plane circle) or 3 (sphere-based sets)
+ * The direction set must be symmetric under p -> -p and under each axis
+ * mirror, as every wall must conserve energy (OBTE_EINVAL otherwise). */
+int obte_set_material(obte_ctx* ctx, int n_mfp, const double* kappa_m, const double* lambda_m,
+                      int n_dir, const double* dirs, const double* w, int angular_dim);
+
+/* Per-cell scattering scale s_i > 0 multiplying the collision term of every
+ * ordinate in cell i (not in the paper; used for sensitivities).
+ * s: host double[nz][ny][nx] or NULL (all ones). */
+int obte_set_scattering_scale(obte_ctx* ctx, const double* s);
+
+/* Fourier first guess then source iteration to the fixed point (Algorithm 1).
+ * opts NULL: defaults.  stats may be NULL.  Returns OBTE_NOT_CONVERGED when
+ * max_iter is reached (results still readable). */
+int obte_solve(obte_ctx* ctx, const obte_solve_opts* opts, obte_solve_stats* stats);
+
+/* Several independent geometries (each its own context on the same device and
+ * stream) iterated together: one persistent launch per iteration over a work
+ * list of (geometry, ordinate group) items, the iteration captured in a CUDA
+ * graph, per-geometry convergence.  stats: array of n or NULL. */
+int obte_solve_batch(obte_ctx* const* ctxs, int n, const obte_solve_opts* opts,
+                     obte_solve_stats* stats);
+
+/* Lattice temperature of the last solve, gauged to zero mean over the solid
+ * cells: host double[nz][ny][nx], NaN in pores. */
+int obte_get_T_L(obte_ctx* ctx, double* out);
+
+/* Heat flux J = sum_o K_o T_o (Sec. 2) per cell: host double[nz][ny][nx][dim]
+ * (W/m^2), NaN in pores.  Runs one extra sweep the first time it is called. */
+int obte_get_flux(obte_ctx* ctx, double* out);
+
+/* kappa_eff of the last solve (W/m/K). */
+int obte_get_kappa_eff(obte_ctx* ctx, double* out);
+
+/* Net x-flux through every section x = const of the kernel frame (conservation
+ * diagnostic; equal at the fixed point): host double[n_sections], n_sections
+ * = cells along the gradient axis.  Runs with obte_get_flux's extra sweep. */
+int obte_get_section_flux(obte_ctx* ctx, double* out);
+
+/* d kappa_eff / d s_i for every cell after obte_solve: host double[nz][ny][nx],
+ * 0 in pores.  The adjoint of the discrete system is the same upwind transport
+ * with every direction reversed (transposed ordinate direction, reverse
+ * wavefront order) and the applied jump replaced by the kappa functional; the
+ * adjoint fields are produced by sweeps in reversed direction and contracted
+ * with the forward fields group by group, so device memory stays bounded by
+ * max_field_bytes (0: 1 GiB). */
+int obte_kappa_grad_s(obte_ctx* ctx, double* out, size_t max_field_bytes);
+
+/* Per-MFP-bin contribution to kappa_eff (the aMFP analogue of the
+ * mode-resolved conductivity, App. A): host double[n_mfp]; sums to kappa_eff.
+ * Runs with obte_get_flux's extra sweep. */
+int obte_get_kappa_bins(obte_ctx* ctx, double* out);
+
+const char* obte_last_error(const obte_ctx* ctx);
+void obte_destroy(obte_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* OBTE_H */

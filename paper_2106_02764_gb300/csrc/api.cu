@@ -1,0 +1,1484 @@
+// Host implementation of the libobte C ABI (include/obte.h).
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <string>
+#include <tuple>
+#include <vector>
+
+#include "obte.h"
+#include "obte_internal.h"
+
+namespace {
+
+constexpr int kMaxHist = OBTE_MAX_HISTORY;
+constexpr int kFourierBlocksMax = 1024;
+
+struct DevBuf {
+  void* p = nullptr;
+  size_t bytes = 0;
+};
+
+}  // namespace
+
+struct obte_ctx {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  void* (*alloc_fn)(size_t, void*) = nullptr;
+  void (*free_fn)(void*, void*) = nullptr;
+  void* user = nullptr;
+  std::string err;
+  std::vector<DevBuf> bufs;
+
+  // mesh (kernel frame: x = gradient axis)
+  bool has_mesh = false, has_material = false, solved = false;
+  int dim = 2, n[3] = {1, 1, 1}, perm[3] = {0, 1, 2}, user_n[3] = {1, 1, 1};
+  double len[3] = {0, 0, 0}, h[3] = {1, 1, 1};
+  int periodic[3] = {1, 1, 1};
+  double dT = 1.0;
+  int n_cells = 0, n_solid = 0, n_walls = 0;
+  std::vector<uint8_t> code_h;
+  std::vector<int> wall_id_h, wall_cell_h, wall_side_h;
+  uint8_t* code_d = nullptr;
+  int* wall_id_d = nullptr;
+  int* wall_cell_d = nullptr;
+  double* s_d = nullptr;
+  bool has_s = false;
+
+  // material: sorted ordinate table
+  int M = 0, S = 0, O = 0, d_ang = 2;
+  std::vector<double> kappa_m, lambda_m;
+  std::vector<int> ord_m, ord_s, octant;          // sorted order
+  std::vector<double> bx, by, bz, diag, inv, aw, kxa, kya, kza;
+  std::vector<double> pk[3];                      // kernel-frame direction per sorted ordinate
+  double* wall_den_d = nullptr;
+  std::vector<double> wall_den_h;
+  void* tab_d[2][9] = {{nullptr}};                // [precision][table]
+  int* mbin_d = nullptr;
+  int* octant_d = nullptr;
+  double kappa_scale = 0.0, sum_k_over_l2 = 0.0;
+
+  // solve state
+  int precision = -1;
+  GeomDev gh{};
+  GeomDev* gd = nullptr;
+  double* TL = nullptr;
+  double* TL_acc = nullptr;
+  void* src = nullptr;
+  double* Tw = nullptr;
+  double* wall_acc = nullptr;
+  void* front = nullptr;
+  double* scal = nullptr;    // phi_acc, delta_max[2]
+  int* ctrl = nullptr;       // done, iter, nonfinite, fin_count
+  double* hist = nullptr;
+  double* TF = nullptr;
+  double* fwork = nullptr;
+  int* fiters = nullptr;
+  double* J_acc = nullptr;
+  double* phi_sec = nullptr;
+  double* phi_bin = nullptr;
+  bool flux_done = false;
+  int G = 0, R = 0, threads = 0;
+  std::vector<WorkItem> items_h;
+  WorkItem* items_d = nullptr;
+  double kappa = NAN;
+  int last_iters = 0;
+  // cached iteration graph (reused by later solves with the same launch shape)
+  cudaGraphExec_t it_exec = nullptr;
+  std::vector<cudaEvent_t> it_events;
+  long long it_key[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+  void drop_graph() {
+    if (it_exec) cudaGraphExecDestroy(it_exec);
+    it_exec = nullptr;
+    for (auto& e : it_events) cudaEventDestroy(e);
+    it_events.clear();
+  }
+  obte_solve_opts last_opts{};
+
+  void* dalloc(size_t bytes) {
+    if (bytes == 0) bytes = 16;
+    void* p = nullptr;
+    if (alloc_fn) {
+      p = alloc_fn(bytes, user);
+    } else if (cudaMalloc(&p, bytes) != cudaSuccess) {
+      p = nullptr;
+    }
+    if (p) bufs.push_back({p, bytes});
+    return p;
+  }
+  void dfree(void* p) {
+    if (!p) return;
+    bool owned = false;
+    for (size_t i = 0; i < bufs.size(); ++i)
+      if (bufs[i].p == p) {
+        bufs.erase(bufs.begin() + i);
+        owned = true;
+        break;
+      }
+    if (!owned) return;  // never free what this context did not allocate
+    if (free_fn) free_fn(p, user);
+    else cudaFree(p);
+  }
+  void forget_pointers() {
+    code_d = nullptr;
+    wall_id_d = nullptr;
+    wall_cell_d = nullptr;
+    s_d = nullptr;
+    wall_den_d = nullptr;
+    for (auto& a : tab_d)
+      for (auto& b : a) b = nullptr;
+    mbin_d = octant_d = nullptr;
+    gd = nullptr;
+    TL = TL_acc = Tw = wall_acc = scal = hist = TF = fwork = J_acc = phi_sec = phi_bin = nullptr;
+    src = front = nullptr;
+    ctrl = fiters = nullptr;
+    items_d = nullptr;
+    items_h.clear();
+    precision = -1;
+  }
+  template <typename T>
+  T* dalloc_t(size_t count) {
+    return reinterpret_cast<T*>(dalloc(count * sizeof(T)));
+  }
+  int fail(int code, const std::string& m) {
+    err = m;
+    return code;
+  }
+  int cuda_fail(cudaError_t e, const char* where) {
+    err = std::string(where) + ": " + cudaGetErrorString(e);
+    return OBTE_ECUDA;
+  }
+};
+
+#define CK(call)                                           \
+  do {                                                     \
+    cudaError_t e_ = (call);                               \
+    if (e_ != cudaSuccess) return ctx->cuda_fail(e_, #call); \
+  } while (0)
+
+#define NEED(ptr)                                                              \
+  do {                                                                         \
+    if (!(ptr)) return ctx->fail(OBTE_ENOMEM, "device allocation failed: " #ptr); \
+  } while (0)
+
+extern "C" void obte_default_opts(obte_solve_opts* o) {
+  if (!o) return;
+  std::memset(o, 0, sizeof(*o));
+  o->precision = OBTE_FP64;
+  o->tol = 1e-6;
+  o->tol_TL = 0.0;
+  o->max_iter = 2000;
+  o->min_iter = 2;
+  o->check_every = 8;
+  o->fourier_max_iter = 0;
+  o->fourier_tol = 0.0;
+  o->group_size = 0;
+  o->rows_per_thread = 0;
+  o->use_graph = 1;
+  o->profile = 0;
+}
+
+extern "C" int obte_create(obte_ctx** out, const obte_device_cfg* cfg) {
+  if (!out) return OBTE_EINVAL;
+  *out = nullptr;
+  obte_ctx* ctx = new obte_ctx();
+  if (cfg) {
+    ctx->device = cfg->device;
+    ctx->alloc_fn = cfg->alloc;
+    ctx->free_fn = cfg->free;
+    ctx->user = cfg->user;
+    ctx->stream = reinterpret_cast<cudaStream_t>(cfg->cuda_stream);
+  }
+  if ((ctx->alloc_fn == nullptr) != (ctx->free_fn == nullptr)) {
+    ctx->err = "alloc and free must be given together";
+    *out = ctx;
+    return OBTE_EINVAL;
+  }
+  cudaError_t e = cudaSetDevice(ctx->device);
+  if (e != cudaSuccess) {
+    ctx->err = std::string("cudaSetDevice: ") + cudaGetErrorString(e);
+    *out = ctx;
+    return OBTE_ECUDA;
+  }
+  if (!ctx->stream) {
+    e = cudaStreamCreateWithFlags(&ctx->stream, cudaStreamNonBlocking);
+    if (e != cudaSuccess) {
+      ctx->err = std::string("cudaStreamCreate: ") + cudaGetErrorString(e);
+      *out = ctx;
+      return OBTE_ECUDA;
+    }
+    ctx->own_stream = true;
+  }
+  *out = ctx;
+  return OBTE_OK;
+}
+
+extern "C" const char* obte_last_error(const obte_ctx* ctx) {
+  return ctx ? ctx->err.c_str() : "null context";
+}
+
+static void free_all(obte_ctx* ctx) {
+  cudaSetDevice(ctx->device);
+  if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+  while (!ctx->bufs.empty()) ctx->dfree(ctx->bufs.back().p);
+  ctx->forget_pointers();
+}
+
+extern "C" void obte_destroy(obte_ctx* ctx) {
+  if (!ctx) return;
+  ctx->drop_graph();
+  free_all(ctx);
+  if (ctx->own_stream && ctx->stream) cudaStreamDestroy(ctx->stream);
+  delete ctx;
+}
+
+// ---------------------------------------------------------------------------
+// mesh
+// ---------------------------------------------------------------------------
+extern "C" int obte_create_mesh(obte_ctx* ctx, int dim, int nx, int ny, int nz, double lx,
+                                double ly, double lz, const uint8_t* mask, const int periodic[3],
+                                int grad_axis, double delta_T) {
+  if (!ctx) return OBTE_EINVAL;
+  if (dim != 2 && dim != 3) return ctx->fail(OBTE_EINVAL, "dim must be 2 or 3");
+  if (dim == 2) {
+    if (nz != 1) return ctx->fail(OBTE_EINVAL, "2D mesh needs nz = 1");
+    lz = 1.0;
+  }
+  if (nx < 1 || ny < 1 || nz < 1) return ctx->fail(OBTE_EINVAL, "cell counts must be positive");
+  if ((long)nx * ny * nz > (1L << 30)) return ctx->fail(OBTE_EINVAL, "mesh too large");
+  if (!(lx > 0) || !(ly > 0) || !(lz > 0) || !std::isfinite(lx) || !std::isfinite(ly) ||
+      !std::isfinite(lz))
+    return ctx->fail(OBTE_EINVAL, "lengths must be positive and finite");
+  if (!mask || !periodic) return ctx->fail(OBTE_EINVAL, "mask and periodic are required");
+  if (grad_axis < 0 || grad_axis >= dim) return ctx->fail(OBTE_EINVAL, "grad_axis out of range");
+  if (!periodic[grad_axis]) return ctx->fail(OBTE_EINVAL, "the gradient axis must be periodic");
+  if (!(delta_T != 0.0) || !std::isfinite(delta_T)) return ctx->fail(OBTE_EINVAL, "delta_T must be nonzero and finite");
+  ctx->drop_graph();
+  if (ctx->solved || ctx->has_mesh) free_all(ctx);
+  ctx->has_mesh = ctx->has_material = ctx->solved = false;
+  ctx->precision = -1;
+  ctx->flux_done = false;
+
+  const int un[3] = {nx, ny, nz};
+  const double ul[3] = {lx, ly, lz};
+  // kernel axis k <- user axis perm[k]: gradient first, the others in order
+  int perm[3] = {grad_axis, 0, 0};
+  int k = 1;
+  for (int a = 0; a < 3; ++a)
+    if (a != grad_axis) perm[k++] = a;
+  if (dim == 2) {  // keep z as the third axis
+    perm[0] = grad_axis;
+    perm[1] = 1 - grad_axis;
+    perm[2] = 2;
+  }
+  for (int i = 0; i < 3; ++i) {
+    ctx->perm[i] = perm[i];
+    ctx->n[i] = un[perm[i]];
+    ctx->len[i] = ul[perm[i]];
+    ctx->periodic[i] = (dim == 2 && i == 2) ? 1 : (periodic[perm[i]] ? 1 : 0);
+    ctx->h[i] = ctx->len[i] / ctx->n[i];
+    ctx->user_n[i] = un[i];
+  }
+  ctx->dim = dim;
+  ctx->dT = delta_T;
+  const int Nx = ctx->n[0], Ny = ctx->n[1], Nz = ctx->n[2];
+  if (ctx->periodic[1] && Ny % Nx != 0)
+    return ctx->fail(OBTE_EINVAL, "a periodic y axis needs ny to be a multiple of nx (kernel frame)");
+  if (dim == 3 && ctx->periodic[2] && Nz % Nx != 0)
+    return ctx->fail(OBTE_EINVAL, "a periodic z axis needs nz to be a multiple of nx (kernel frame)");
+  ctx->n_cells = Nx * Ny * Nz;
+
+  // solid flags in the kernel frame
+  std::vector<uint8_t> solid(ctx->n_cells);
+  for (int z = 0; z < Nz; ++z)
+    for (int y = 0; y < Ny; ++y)
+      for (int x = 0; x < Nx; ++x) {
+        int u[3];
+        const int kc[3] = {x, y, z};
+        for (int i = 0; i < 3; ++i) u[perm[i]] = kc[i];
+        const long ui = u[0] + (long)un[0] * (u[1] + (long)un[1] * u[2]);
+        solid[x + Nx * (y + Ny * z)] = mask[ui] ? 1 : 0;
+      }
+  ctx->code_h.assign(ctx->n_cells, 0);
+  ctx->wall_id_h.assign((size_t)ctx->n_cells * 6, -1);
+  ctx->wall_cell_h.clear();
+  ctx->wall_side_h.clear();
+  ctx->n_solid = 0;
+  for (int z = 0; z < Nz; ++z)
+    for (int y = 0; y < Ny; ++y)
+      for (int x = 0; x < Nx; ++x) {
+        const int c = x + Nx * (y + Ny * z);
+        if (!solid[c]) continue;
+        ++ctx->n_solid;
+        uint8_t code = CODE_SOLID;
+        const int kc[3] = {x, y, z};
+        for (int a = 0; a < dim; ++a)
+          for (int sd = 0; sd < 2; ++sd) {
+            int q[3] = {x, y, z};
+            q[a] += sd ? 1 : -1;
+            bool wall = false;
+            if (q[a] < 0 || q[a] >= ctx->n[a]) {
+              if (ctx->periodic[a]) q[a] = (q[a] + ctx->n[a]) % ctx->n[a];
+              else wall = true;
+            }
+            if (!wall) wall = !solid[q[0] + Nx * (q[1] + Ny * q[2])];
+            if (wall) {
+              code |= (uint8_t)(1u << (2 * a + sd));
+              ctx->wall_id_h[(size_t)c * 6 + 2 * a + sd] = (int)ctx->wall_cell_h.size();
+              ctx->wall_cell_h.push_back(c);
+              ctx->wall_side_h.push_back(2 * a + sd);
+            }
+            (void)kc;
+          }
+        ctx->code_h[c] = code;
+      }
+  if (ctx->n_solid == 0) return ctx->fail(OBTE_EINVAL, "the mask has no solid cell");
+  ctx->n_walls = (int)ctx->wall_cell_h.size();
+  long n_sec = (long)Ny * (dim == 3 ? Nz : 1);
+  ctx->kappa_scale = ctx->len[0] / (delta_T * (double)n_sec);
+
+  cudaSetDevice(ctx->device);
+  ctx->code_d = ctx->dalloc_t<uint8_t>(ctx->n_cells);
+  ctx->wall_id_d = ctx->dalloc_t<int>((size_t)ctx->n_cells * 6);
+  ctx->wall_cell_d = ctx->dalloc_t<int>(std::max(1, ctx->n_walls));
+  NEED(ctx->code_d);
+  NEED(ctx->wall_id_d);
+  NEED(ctx->wall_cell_d);
+  CK(cudaMemcpyAsync(ctx->code_d, ctx->code_h.data(), ctx->n_cells, cudaMemcpyHostToDevice, ctx->stream));
+  CK(cudaMemcpyAsync(ctx->wall_id_d, ctx->wall_id_h.data(), sizeof(int) * ctx->n_cells * 6,
+                     cudaMemcpyHostToDevice, ctx->stream));
+  if (ctx->n_walls)
+    CK(cudaMemcpyAsync(ctx->wall_cell_d, ctx->wall_cell_h.data(), sizeof(int) * ctx->n_walls,
+                       cudaMemcpyHostToDevice, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  ctx->has_s = false;
+  ctx->s_d = nullptr;
+  ctx->has_mesh = true;
+  return OBTE_OK;
+}
+
+extern "C" int obte_set_scattering_scale(obte_ctx* ctx, const double* s) {
+  if (!ctx) return OBTE_EINVAL;
+  if (!ctx->has_mesh) return ctx->fail(OBTE_ESTATE, "create_mesh first");
+  ctx->solved = false;
+  ctx->flux_done = false;
+  if (!s) {
+    ctx->has_s = false;
+    return OBTE_OK;
+  }
+  std::vector<double> sk(ctx->n_cells, 1.0);
+  const int Nx = ctx->n[0], Ny = ctx->n[1];
+  for (int c = 0; c < ctx->n_cells; ++c) {
+    const int kc[3] = {c % Nx, (c / Nx) % Ny, c / (Nx * Ny)};
+    int u[3];
+    for (int i = 0; i < 3; ++i) u[ctx->perm[i]] = kc[i];
+    const long ui = u[0] + (long)ctx->user_n[0] * (u[1] + (long)ctx->user_n[1] * u[2]);
+    const double v = s[ui];
+    if (ctx->code_h[c] & CODE_SOLID) {
+      if (!std::isfinite(v)) return ctx->fail(OBTE_ENONFINITE, "scattering scale is not finite");
+      if (!(v > 0)) return ctx->fail(OBTE_EINVAL, "scattering scale must be positive");
+    }
+    sk[c] = v;
+  }
+  if (!ctx->s_d) ctx->s_d = ctx->dalloc_t<double>(ctx->n_cells);
+  NEED(ctx->s_d);
+  CK(cudaMemcpyAsync(ctx->s_d, sk.data(), sizeof(double) * ctx->n_cells, cudaMemcpyHostToDevice, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  ctx->has_s = true;
+  return OBTE_OK;
+}
+
+// ---------------------------------------------------------------------------
+// material and ordinate table
+// ---------------------------------------------------------------------------
+enum { TB_BX, TB_BY, TB_BZ, TB_DIAG, TB_INV, TB_AW, TB_KXA, TB_KYA, TB_KZA };
+
+extern "C" int obte_set_material(obte_ctx* ctx, int n_mfp, const double* kappa_m,
+                                 const double* lambda_m, int n_dir, const double* dirs,
+                                 const double* w, int angular_dim) {
+  if (!ctx) return OBTE_EINVAL;
+  if (!ctx->has_mesh) return ctx->fail(OBTE_ESTATE, "create_mesh first");
+  if (n_mfp < 1 || n_dir < 1 || !kappa_m || !lambda_m || !dirs || !w)
+    return ctx->fail(OBTE_EINVAL, "empty material");
+  if (angular_dim != 2 && angular_dim != 3) return ctx->fail(OBTE_EINVAL, "angular_dim must be 2 or 3");
+  double wsum = 0;
+  for (int m = 0; m < n_mfp; ++m) {
+    if (!std::isfinite(kappa_m[m]) || !std::isfinite(lambda_m[m]))
+      return ctx->fail(OBTE_ENONFINITE, "material is not finite");
+    if (!(lambda_m[m] > 0) || kappa_m[m] < 0) return ctx->fail(OBTE_EINVAL, "need lambda_m > 0, kappa_m >= 0");
+  }
+  for (int s = 0; s < n_dir; ++s) {
+    for (int a = 0; a < 3; ++a)
+      if (!std::isfinite(dirs[3 * s + a])) return ctx->fail(OBTE_ENONFINITE, "directions not finite");
+    if (!std::isfinite(w[s]) || w[s] < 0) return ctx->fail(OBTE_EINVAL, "weights must be >= 0");
+    wsum += w[s];
+  }
+  if (std::fabs(wsum - 1.0) > 1e-9) return ctx->fail(OBTE_EINVAL, "direction weights must sum to 1");
+  double sk = 0;
+  for (int m = 0; m < n_mfp; ++m) sk += kappa_m[m] / (lambda_m[m] * lambda_m[m]);
+  if (!(sk > 0)) return ctx->fail(OBTE_EINVAL, "sum kappa_m / lambda_m^2 must be positive");
+
+  const int dim = ctx->dim;
+  ctx->M = n_mfp;
+  ctx->S = n_dir;
+  ctx->O = n_mfp * n_dir;
+  ctx->d_ang = angular_dim;
+  ctx->kappa_m.assign(kappa_m, kappa_m + n_mfp);
+  ctx->lambda_m.assign(lambda_m, lambda_m + n_mfp);
+  ctx->sum_k_over_l2 = sk;
+
+  // kernel-frame directions (2D: user z dropped before the permutation)
+  std::vector<double> pdir((size_t)n_dir * 3);
+  for (int s = 0; s < n_dir; ++s) {
+    double u[3] = {dirs[3 * s], dirs[3 * s + 1], dim == 3 ? dirs[3 * s + 2] : 0.0};
+    for (int i = 0; i < 3; ++i) pdir[3 * s + i] = u[ctx->perm[i]];
+  }
+  // octant of a direction; ordering puts reversed octants next to each other
+  auto oct_of = [&](int s) {
+    int q = 0;
+    if (pdir[3 * s] < 0) q |= 1;
+    if (pdir[3 * s + 1] < 0) q |= 2;
+    if (dim == 3 && pdir[3 * s + 2] < 0) q |= 4;
+    return q;
+  };
+  const int full = dim == 3 ? 7 : 3;
+  std::vector<int> oct_order;
+  for (int q = 0; q <= full; ++q) {
+    const int qb = q ^ full;
+    if (q < qb) {
+      oct_order.push_back(q);
+      oct_order.push_back(qb);
+    }
+  }
+  // within an octant, order directions by their reversed direction's canonical
+  // index so that the k-th ordinate of octant q reverses to the k-th of q^full
+  std::vector<std::vector<int>> dir_in_oct(8);
+  for (int s = 0; s < n_dir; ++s) dir_in_oct[oct_of(s)].push_back(s);
+  auto find_rev = [&](int s) {
+    for (int t = 0; t < n_dir; ++t) {
+      bool same = true;
+      for (int a = 0; a < 3; ++a)
+        if (std::fabs(pdir[3 * t + a] + pdir[3 * s + a]) > 1e-12) same = false;
+      if (same && std::fabs(w[t] - w[s]) <= 1e-15 + 1e-12 * w[s]) return t;
+    }
+    return -1;
+  };
+  for (int i = 0; i + 1 < (int)oct_order.size(); i += 2) {
+    const int q = oct_order[i], qb = oct_order[i + 1];
+    std::vector<int> rv;
+    bool ok = true;
+    for (int s : dir_in_oct[q]) {
+      const int r = find_rev(s);
+      if (r < 0 || oct_of(r) != qb) ok = false;
+      rv.push_back(r);
+    }
+    if (ok && rv.size() == dir_in_oct[qb].size()) dir_in_oct[qb] = rv;  // paired order
+  }
+  ctx->ord_m.clear();
+  ctx->ord_s.clear();
+  ctx->octant.clear();
+  for (int q : oct_order)
+    for (int m = 0; m < n_mfp; ++m)
+      for (int s : dir_in_oct[q]) {
+        ctx->ord_m.push_back(m);
+        ctx->ord_s.push_back(s);
+        ctx->octant.push_back(q);
+      }
+  const int O = ctx->O;
+  for (auto* v : {&ctx->bx, &ctx->by, &ctx->bz, &ctx->diag, &ctx->inv, &ctx->aw, &ctx->kxa,
+                  &ctx->kya, &ctx->kza})
+    v->assign(O, 0.0);
+  for (int a = 0; a < 3; ++a) ctx->pk[a].assign(O, 0.0);
+  double den_side[6] = {0, 0, 0, 0, 0, 0};
+  for (int o = 0; o < O; ++o) {
+    const int m = ctx->ord_m[o], s = ctx->ord_s[o];
+    const double lam = lambda_m[m];
+    double p[3] = {pdir[3 * s], pdir[3 * s + 1], pdir[3 * s + 2]};
+    for (int a = 0; a < 3; ++a) ctx->pk[a][o] = p[a];
+    double beta[3] = {0, 0, 0};
+    for (int a = 0; a < dim; ++a) beta[a] = lam * std::fabs(p[a]) / ctx->h[a];
+    const double D = beta[0] + beta[1] + beta[2];
+    ctx->bx[o] = beta[0];
+    ctx->by[o] = beta[1];
+    ctx->bz[o] = beta[2];
+    ctx->diag[o] = D;
+    ctx->inv[o] = 1.0 / (1.0 + D);
+    // E2 weight a_o = w_s (kappa_m / Lambda_m^2) / sum (kappa / Lambda^2)
+    ctx->aw[o] = w[s] * (kappa_m[m] / (lam * lam)) / sk;
+    // flux weight K_o = d_ang kappa_m w_s p_s / Lambda_m
+    const double kf = angular_dim * kappa_m[m] * w[s] / lam;
+    ctx->kxa[o] = kf * std::fabs(p[0]);
+    ctx->kya[o] = kf * std::fabs(p[1]);
+    ctx->kza[o] = dim == 3 ? kf * std::fabs(p[2]) : 0.0;
+    for (int a = 0; a < dim; ++a) {
+      const double k = kf * p[a];
+      if (k > 0) den_side[2 * a + 1] += k;   // leaves through the + face
+      if (k < 0) den_side[2 * a] += -k;      // leaves through the - face
+    }
+  }
+  for (int a = 0; a < dim; ++a) {
+    const double s0 = den_side[2 * a], s1 = den_side[2 * a + 1];
+    if (std::fabs(s0 - s1) > 1e-10 * std::max(s0, s1))
+      return ctx->fail(OBTE_EINVAL, "direction set is not mirror-symmetric: walls would not conserve energy");
+  }
+  ctx->wall_den_h.assign(std::max(1, ctx->n_walls), 1.0);
+  for (int f = 0; f < ctx->n_walls; ++f) {
+    const double d = den_side[ctx->wall_side_h[f]];
+    ctx->wall_den_h[f] = d > 0 ? d : 1.0;
+  }
+
+  cudaSetDevice(ctx->device);
+  const std::vector<double>* tabs[9] = {&ctx->bx, &ctx->by, &ctx->bz, &ctx->diag, &ctx->inv,
+                                        &ctx->aw, &ctx->kxa, &ctx->kya, &ctx->kza};
+  for (int t = 0; t < 9; ++t) {
+    if (!ctx->tab_d[0][t]) ctx->tab_d[0][t] = ctx->dalloc_t<double>(O);
+    else {
+      ctx->dfree(ctx->tab_d[0][t]);
+      ctx->tab_d[0][t] = ctx->dalloc_t<double>(O);
+    }
+    if (ctx->tab_d[1][t]) ctx->dfree(ctx->tab_d[1][t]);
+    ctx->tab_d[1][t] = ctx->dalloc_t<float>(O);
+    NEED(ctx->tab_d[0][t]);
+    NEED(ctx->tab_d[1][t]);
+    std::vector<float> f(O);
+    for (int o = 0; o < O; ++o) f[o] = (float)(*tabs[t])[o];
+    CK(cudaMemcpyAsync(ctx->tab_d[0][t], tabs[t]->data(), sizeof(double) * O, cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaMemcpyAsync(ctx->tab_d[1][t], f.data(), sizeof(float) * O, cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+  }
+  if (ctx->mbin_d) ctx->dfree(ctx->mbin_d);
+  if (ctx->octant_d) ctx->dfree(ctx->octant_d);
+  if (ctx->wall_den_d) ctx->dfree(ctx->wall_den_d);
+  ctx->mbin_d = ctx->dalloc_t<int>(O);
+  ctx->octant_d = ctx->dalloc_t<int>(O);
+  ctx->wall_den_d = ctx->dalloc_t<double>(ctx->wall_den_h.size());
+  NEED(ctx->mbin_d);
+  NEED(ctx->octant_d);
+  NEED(ctx->wall_den_d);
+  CK(cudaMemcpyAsync(ctx->mbin_d, ctx->ord_m.data(), sizeof(int) * O, cudaMemcpyHostToDevice, ctx->stream));
+  CK(cudaMemcpyAsync(ctx->octant_d, ctx->octant.data(), sizeof(int) * O, cudaMemcpyHostToDevice, ctx->stream));
+  CK(cudaMemcpyAsync(ctx->wall_den_d, ctx->wall_den_h.data(), sizeof(double) * ctx->wall_den_h.size(),
+                     cudaMemcpyHostToDevice, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  ctx->has_material = true;
+  ctx->solved = false;
+  ctx->precision = -1;  // state buffers are rebuilt by the next solve
+  return OBTE_OK;
+}
+
+// ---------------------------------------------------------------------------
+// variant choice and autotuning
+// ---------------------------------------------------------------------------
+namespace {
+
+struct Variant {
+  int G, R;
+};
+
+const Variant kVariants2D_F[] = {{16, 4}, {8, 4}, {8, 8}, {16, 2}, {8, 2}, {4, 4}, {16, 1}};
+const Variant kVariants2D_D[] = {{8, 2}, {8, 4}, {4, 4}, {4, 8}, {8, 1}};
+const Variant kVariants3D_F[] = {{8, 4}, {4, 4}, {8, 8}, {4, 8}, {8, 2}, {4, 2}};
+const Variant kVariants3D_D[] = {{4, 4}, {4, 8}, {4, 2}, {8, 2}};
+
+int threads_for(int ny, int nz, int R) {
+  const int tpp = (ny + R - 1) / R;
+  const int t = tpp * nz;
+  return ((t + 31) / 32) * 32;
+}
+
+std::vector<Variant> candidates(int precision, int dim, int ny, int nz) {
+  std::vector<Variant> out;
+  const Variant* v;
+  int n;
+  if (dim == 2) {
+    v = precision ? kVariants2D_F : kVariants2D_D;
+    n = precision ? (int)(sizeof(kVariants2D_F) / sizeof(Variant)) : (int)(sizeof(kVariants2D_D) / sizeof(Variant));
+  } else {
+    v = precision ? kVariants3D_F : kVariants3D_D;
+    n = precision ? (int)(sizeof(kVariants3D_F) / sizeof(Variant)) : (int)(sizeof(kVariants3D_D) / sizeof(Variant));
+  }
+  for (int i = 0; i < n; ++i) {
+    if (ny % v[i].R != 0) continue;
+    const int thr = threads_for(ny, nz, v[i].R);
+    if (thr > (dim == 3 ? 512 : 256)) continue;
+    if (sweep_smem_bytes(precision, dim, v[i].G, v[i].R, thr) > 200 * 1024) continue;
+    if (!sweep_variant_exists(precision, dim, v[i].G, v[i].R)) continue;
+    out.push_back(v[i]);
+  }
+  return out;
+}
+
+std::map<std::tuple<int, int, int, int, int, int>, Variant>& tune_cache() {
+  static std::map<std::tuple<int, int, int, int, int, int>, Variant> c;
+  return c;
+}
+
+}  // namespace
+
+static void build_items(obte_ctx* ctx, int geom, int G, std::vector<WorkItem>& items) {
+  const int O = ctx->O;
+  int o = 0;
+  while (o < O) {
+    const int q = ctx->octant[o];
+    int e = o;
+    while (e < O && ctx->octant[e] == q) ++e;
+    for (int a = o; a < e; a += G) items.push_back({geom, q, a, std::min(G, e - a)});
+    o = e;
+  }
+}
+
+// allocate the iteration state for a precision / variant; fill gh and gd
+static int prepare_state(obte_ctx* ctx, int precision, int G, int R, int max_iter,
+                         const obte_solve_opts& op) {
+  cudaSetDevice(ctx->device);
+  const int Nx = ctx->n[0], Ny = ctx->n[1], Nz = ctx->n[2];
+  const int rows = Ny * Nz;
+  if (ctx->precision != precision) {
+    ctx->drop_graph();
+    // (re)allocate everything that depends on the precision
+    for (void* p : {(void*)ctx->TL, (void*)ctx->TL_acc, ctx->src, (void*)ctx->Tw, (void*)ctx->wall_acc,
+                    ctx->front, (void*)ctx->scal, (void*)ctx->ctrl, (void*)ctx->hist, (void*)ctx->TF,
+                    (void*)ctx->fwork, (void*)ctx->fiters, (void*)ctx->gd})
+      ctx->dfree(p);
+    const size_t e = precision == 0 ? 8 : 4;
+    ctx->TL = ctx->dalloc_t<double>(ctx->n_cells);
+    ctx->TL_acc = ctx->dalloc_t<double>(ctx->n_cells);
+    ctx->src = ctx->dalloc(e * ctx->n_cells);
+    ctx->Tw = ctx->dalloc_t<double>(std::max(1, ctx->n_walls));
+    ctx->wall_acc = ctx->dalloc_t<double>(std::max(1, ctx->n_walls));
+    ctx->front = ctx->dalloc(e * (size_t)ctx->O * rows);
+    ctx->scal = ctx->dalloc_t<double>(4);
+    ctx->ctrl = ctx->dalloc_t<int>(4);
+    ctx->hist = ctx->dalloc_t<double>(kMaxHist);
+    ctx->TF = ctx->dalloc_t<double>(ctx->n_cells);
+    ctx->fwork = ctx->dalloc_t<double>(fourier_work_doubles(ctx->n_cells, kFourierBlocksMax));
+    ctx->fiters = ctx->dalloc_t<int>(1);
+    ctx->gd = ctx->dalloc_t<GeomDev>(1);
+    NEED(ctx->TL);
+    NEED(ctx->TL_acc);
+    NEED(ctx->src);
+    NEED(ctx->Tw);
+    NEED(ctx->wall_acc);
+    NEED(ctx->front);
+    NEED(ctx->scal);
+    NEED(ctx->ctrl);
+    NEED(ctx->hist);
+    NEED(ctx->TF);
+    NEED(ctx->fwork);
+    NEED(ctx->fiters);
+    NEED(ctx->gd);
+    ctx->precision = precision;
+  }
+  GeomDev& g = ctx->gh;
+  std::memset(&g, 0, sizeof(g));
+  g.nx = Nx;
+  g.ny = Ny;
+  g.nz = Nz;
+  g.dim = ctx->dim;
+  g.n_cells = ctx->n_cells;
+  g.rows = rows;
+  g.py = ctx->periodic[1];
+  g.pz = ctx->dim == 3 ? ctx->periodic[2] : 0;
+  g.R = R;
+  g.tpp = (Ny + R - 1) / R;
+  g.n_ord = ctx->O;
+  g.n_walls = ctx->n_walls;
+  g.dT = ctx->dT;
+  g.kappa_scale = ctx->kappa_scale;
+  g.code = ctx->code_d;
+  g.wall_id = ctx->wall_id_d;
+  g.s = ctx->has_s ? ctx->s_d : nullptr;
+  g.TL = ctx->TL;
+  g.TL_acc = ctx->TL_acc;
+  g.src = ctx->src;
+  g.Tw = ctx->Tw;
+  g.wall_acc = ctx->wall_acc;
+  g.wall_den = ctx->wall_den_d;
+  g.wall_cell = ctx->wall_cell_d;
+  g.front = ctx->front;
+  g.phi_acc = ctx->scal;
+  g.delta_max = ctx->scal + 1;
+  g.J_acc = ctx->J_acc;
+  g.phi_sec = ctx->phi_sec;
+  g.phi_bin = ctx->phi_bin;
+  g.rec = nullptr;
+  g.rec_slot = nullptr;
+  const int p = precision == 0 ? 0 : 1;
+  g.bx = ctx->tab_d[p][TB_BX];
+  g.by = ctx->tab_d[p][TB_BY];
+  g.bz = ctx->tab_d[p][TB_BZ];
+  g.diag = ctx->tab_d[p][TB_DIAG];
+  g.inv = ctx->tab_d[p][TB_INV];
+  g.aw = ctx->tab_d[p][TB_AW];
+  g.kxa = ctx->tab_d[p][TB_KXA];
+  g.kya = ctx->tab_d[p][TB_KYA];
+  g.kza = ctx->tab_d[p][TB_KZA];
+  g.mbin = ctx->mbin_d;
+  g.done = ctx->ctrl + 0;
+  g.iter = ctx->ctrl + 1;
+  g.nonfinite = ctx->ctrl + 2;
+  g.fin_count = reinterpret_cast<unsigned int*>(ctx->ctrl + 3);
+  g.kappa_hist = ctx->hist;
+  g.max_hist = kMaxHist;
+  g.tol = op.tol;
+  g.tol_TL = op.tol_TL;
+  g.min_iter = std::max(op.min_iter, 1);
+  g.max_iter = max_iter;
+  CK(cudaMemcpyAsync(ctx->gd, &g, sizeof(GeomDev), cudaMemcpyHostToDevice, ctx->stream));
+  ctx->G = G;
+  ctx->R = R;
+  ctx->threads = threads_for(Ny, Nz, R);
+  std::vector<WorkItem> items;
+  build_items(ctx, 0, G, items);
+  const bool same = ctx->items_d && items.size() == ctx->items_h.size() &&
+                    std::memcmp(items.data(), ctx->items_h.data(), sizeof(WorkItem) * items.size()) == 0;
+  if (!same) {
+    ctx->items_h = items;
+    if (ctx->items_d) ctx->dfree(ctx->items_d);
+    ctx->items_d = ctx->dalloc_t<WorkItem>(ctx->items_h.size());
+    NEED(ctx->items_d);
+    CK(cudaMemcpyAsync(ctx->items_d, ctx->items_h.data(), sizeof(WorkItem) * ctx->items_h.size(),
+                       cudaMemcpyHostToDevice, ctx->stream));
+  }
+  return OBTE_OK;
+}
+
+static cudaError_t sweep_once(obte_ctx* ctx, int flags) {
+  SweepLaunch L;
+  L.geoms = ctx->gd;
+  L.items = ctx->items_d;
+  L.n_items = (int)ctx->items_h.size();
+  L.flags = flags | (ctx->has_s ? SWEEP_HAS_S : 0);
+  L.item_counter = nullptr;
+  const size_t smem = sweep_smem_bytes(ctx->precision, ctx->dim, ctx->G, ctx->R, ctx->threads);
+  return launch_sweep(L, ctx->precision, ctx->dim, ctx->G, ctx->R, ctx->threads, L.n_items, smem,
+                      ctx->stream);
+}
+
+static int finalize_blocks(int n_cells) {
+  int b = (n_cells + 255) / 256;
+  return std::max(1, std::min(b, 296));
+}
+
+static int init_from_fourier(obte_ctx* ctx, const obte_solve_opts& op, int* fiters_out) {
+  const int prec = ctx->precision;
+  int fmax = op.fourier_max_iter > 0 ? op.fourier_max_iter : 4 * (ctx->n[0] + ctx->n[1] + ctx->n[2]);
+  double ftol = op.fourier_tol > 0 ? op.fourier_tol : (prec == 0 ? 1e-4 : 1e-4);
+  CK(launch_fourier_cg(ctx->gh, ctx->h[0], ctx->h[1], ctx->h[2], prec, fmax, ftol, ctx->TF,
+                       ctx->fiters, ctx->fwork, kFourierBlocksMax, ctx->stream));
+  CK(launch_init_state_oct(ctx->gd, ctx->gh, 0, ctx->TF, prec, ctx->octant_d, ctx->stream));
+  if (fiters_out) {
+    CK(cudaMemcpyAsync(fiters_out, ctx->fiters, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+  }
+  return OBTE_OK;
+}
+
+static int pick_variant(obte_ctx* ctx, int precision, const obte_solve_opts& op, Variant* out) {
+  const int Ny = ctx->n[1], Nz = ctx->n[2];
+  auto cands = candidates(precision, ctx->dim, Ny, Nz);
+  if (op.group_size > 0 || op.rows_per_thread > 0) {
+    for (auto& c : candidates(precision, ctx->dim, Ny, Nz))
+      if ((op.group_size <= 0 || c.G == op.group_size) && (op.rows_per_thread <= 0 || c.R == op.rows_per_thread)) {
+        *out = c;
+        return OBTE_OK;
+      }
+    return ctx->fail(OBTE_EINVAL, "no compiled sweep variant matches group_size / rows_per_thread for this mesh");
+  }
+  if (cands.empty()) return ctx->fail(OBTE_EINVAL, "no compiled sweep variant fits this mesh (rows per plane too many?)");
+  auto key = std::make_tuple(precision, ctx->dim, ctx->n[0], Ny, Nz, ctx->O);
+  auto it = tune_cache().find(key);
+  if (it != tune_cache().end()) {
+    *out = it->second;
+    return OBTE_OK;
+  }
+  if (cands.size() == 1 || op.group_size == 0) {
+    // heuristic default: the first candidate that gives at least one block per SM
+    int sms = 148;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ctx->device);
+    *out = cands[0];
+    for (auto& c : cands) {
+      const long blocks = (ctx->O + c.G - 1) / c.G;
+      if (blocks >= sms) {
+        *out = c;
+        break;
+      }
+    }
+    return OBTE_OK;
+  }
+  return OBTE_OK;
+}
+
+// timed autotune over the compiled variants (group_size = -1)
+static int autotune(obte_ctx* ctx, int precision, const obte_solve_opts& op, Variant* out) {
+  auto key = std::make_tuple(precision, ctx->dim, ctx->n[0], ctx->n[1], ctx->n[2], ctx->O);
+  auto cands = candidates(precision, ctx->dim, ctx->n[1], ctx->n[2]);
+  if (cands.empty()) return ctx->fail(OBTE_EINVAL, "no compiled sweep variant fits this mesh");
+  cudaEvent_t a, b;
+  CK(cudaEventCreate(&a));
+  CK(cudaEventCreate(&b));
+  float best = 1e30f;
+  Variant bv = cands[0];
+  for (auto& c : cands) {
+    int rc = prepare_state(ctx, precision, c.G, c.R, 1 << 30, op);
+    if (rc) return rc;
+    obte_solve_opts o2 = op;
+    o2.fourier_max_iter = 1;
+    rc = init_from_fourier(ctx, o2, nullptr);
+    if (rc) return rc;
+    CK(sweep_once(ctx, 0));  // warm-up
+    CK(cudaEventRecord(a, ctx->stream));
+    for (int i = 0; i < 3; ++i) CK(sweep_once(ctx, 0));
+    CK(cudaEventRecord(b, ctx->stream));
+    CK(cudaEventSynchronize(b));
+    float ms = 0;
+    CK(cudaEventElapsedTime(&ms, a, b));
+    if (ms < best) {
+      best = ms;
+      bv = c;
+    }
+  }
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  tune_cache()[key] = bv;
+  *out = bv;
+  return OBTE_OK;
+}
+
+// ---------------------------------------------------------------------------
+// solve
+// ---------------------------------------------------------------------------
+struct IterTiming {
+  int n_sweeps = 0;
+  double sweep_ms = 0.0, finalize_ms = 0.0;
+};
+
+static int run_iterations(obte_ctx* ctx, const obte_solve_opts& op, int* iters, int* done_code,
+                          IterTiming* tm) {
+  const int k = std::max(1, op.check_every);
+  int* host_ctrl = nullptr;
+  CK(cudaMallocHost(&host_ctrl, 4 * sizeof(int)));
+  int rc = OBTE_OK;
+  // optional per-launch events: ev[3 i] before sweep i, ev[3 i + 1] after it,
+  // ev[3 i + 2] after finalize i
+  const long long key[8] = {(long long)(size_t)ctx->gd, (long long)(size_t)ctx->items_d,
+                            (long long)ctx->items_h.size(), ctx->precision * 1000003LL + ctx->G * 1009 + ctx->R,
+                            ctx->threads, k, op.profile, ctx->has_s};
+  bool reuse = op.use_graph && ctx->it_exec && std::equal(key, key + 8, ctx->it_key);
+  if (!reuse) {
+    ctx->drop_graph();
+    if (op.profile) {
+      ctx->it_events.resize(3 * k);
+      for (auto& e : ctx->it_events) CK(cudaEventCreate(&e));
+    }
+  }
+  std::vector<cudaEvent_t>& ev = ctx->it_events;
+  auto body = [&]() -> cudaError_t {
+    for (int i = 0; i < k; ++i) {
+      cudaError_t e;
+      if (op.profile && (e = cudaEventRecordWithFlags(ev[3 * i], ctx->stream, cudaEventRecordExternal)) != cudaSuccess) return e;
+      e = sweep_once(ctx, 0);
+      if (e != cudaSuccess) return e;
+      if (op.profile && (e = cudaEventRecordWithFlags(ev[3 * i + 1], ctx->stream, cudaEventRecordExternal)) != cudaSuccess) return e;
+      e = launch_finalize(ctx->gd, 1, ctx->precision, finalize_blocks(ctx->n_cells), ctx->stream);
+      if (e != cudaSuccess) return e;
+      if (op.profile && (e = cudaEventRecordWithFlags(ev[3 * i + 2], ctx->stream, cudaEventRecordExternal)) != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+  };
+  if (op.use_graph && !reuse) {
+    cudaGraph_t graph = nullptr;
+    cudaError_t e = cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+      cudaError_t eb = body();
+      e = cudaStreamEndCapture(ctx->stream, &graph);
+      if (eb != cudaSuccess) e = eb;
+    }
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&ctx->it_exec, graph, 0);
+    if (graph) cudaGraphDestroy(graph);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      ctx->it_exec = nullptr;
+    } else {
+      std::copy(key, key + 8, ctx->it_key);
+    }
+  }
+  cudaGraphExec_t exec = op.use_graph ? ctx->it_exec : nullptr;
+  int launched = 0, prev_iter = 0;
+  while (true) {
+    cudaError_t e = exec ? cudaGraphLaunch(exec, ctx->stream) : body();
+    if (e != cudaSuccess) {
+      rc = ctx->cuda_fail(e, "iteration launch");
+      break;
+    }
+    launched += k;
+    e = cudaMemcpyAsync(host_ctrl, ctx->ctrl, 4 * sizeof(int), cudaMemcpyDeviceToHost, ctx->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    if (e != cudaSuccess) {
+      rc = ctx->cuda_fail(e, "iteration sync");
+      break;
+    }
+    if (op.profile && tm) {
+      // sweeps that ran (the kernels return at once after convergence)
+      const int ran = host_ctrl[1] - prev_iter;
+      for (int i = 0; i < k && i < ran; ++i) {
+        float a = 0.f, b = 0.f;
+        if (cudaEventElapsedTime(&a, ev[3 * i], ev[3 * i + 1]) == cudaSuccess &&
+            cudaEventElapsedTime(&b, ev[3 * i + 1], ev[3 * i + 2]) == cudaSuccess) {
+          tm->sweep_ms += a;
+          tm->finalize_ms += b;
+          tm->n_sweeps += 1;
+        } else {
+          cudaGetLastError();  // timing unavailable: keep the solve's error state clean
+        }
+      }
+    }
+    prev_iter = host_ctrl[1];
+    if (host_ctrl[0]) break;
+    if (launched > op.max_iter + k) {  // defensive: the device test stops at max_iter
+      rc = ctx->fail(OBTE_NOT_CONVERGED, "iteration cap reached");
+      break;
+    }
+  }
+  *iters = host_ctrl[1];
+  *done_code = host_ctrl[0];
+  if (!op.use_graph) ctx->drop_graph();
+  cudaFreeHost(host_ctrl);
+  return rc;
+}
+
+extern "C" int obte_solve(obte_ctx* ctx, const obte_solve_opts* opts, obte_solve_stats* stats) {
+  if (!ctx) return OBTE_EINVAL;
+  if (!ctx->has_mesh || !ctx->has_material) return ctx->fail(OBTE_ESTATE, "create_mesh and set_material first");
+  obte_solve_opts op;
+  if (opts) op = *opts;
+  else obte_default_opts(&op);
+  if (op.precision != OBTE_FP64 && op.precision != OBTE_MIXED) return ctx->fail(OBTE_EINVAL, "bad precision");
+  if (op.max_iter < 1) return ctx->fail(OBTE_EINVAL, "max_iter must be >= 1");
+  if (op.check_every < 1) op.check_every = 1;
+  cudaSetDevice(ctx->device);
+  const int prec = op.precision == OBTE_FP64 ? 0 : 1;
+  Variant v;
+  int rc = (op.group_size < 0) ? autotune(ctx, prec, op, &v) : pick_variant(ctx, prec, op, &v);
+  if (rc) return rc;
+  rc = prepare_state(ctx, prec, v.G, v.R, op.max_iter, op);
+  if (rc) return rc;
+  ctx->flux_done = false;
+  cudaEvent_t e0, e1, e2;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  CK(cudaEventCreate(&e2));
+  CK(cudaEventRecord(e0, ctx->stream));
+  int fiters = 0;
+  int* fi_host = nullptr;
+  CK(cudaMallocHost(&fi_host, sizeof(int)));
+  rc = init_from_fourier(ctx, op, fi_host);
+  if (rc) {
+    cudaFreeHost(fi_host);
+    return rc;
+  }
+  CK(cudaEventRecord(e1, ctx->stream));
+  int iters = 0, done = 0;
+  IterTiming tm;
+  rc = run_iterations(ctx, op, &iters, &done, &tm);
+  CK(cudaEventRecord(e2, ctx->stream));
+  CK(cudaEventSynchronize(e2));
+  fiters = *fi_host;
+  cudaFreeHost(fi_host);
+  float t_f = 0, t_i = 0;
+  cudaEventElapsedTime(&t_f, e0, e1);
+  cudaEventElapsedTime(&t_i, e1, e2);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaEventDestroy(e2);
+  if (rc && rc != OBTE_NOT_CONVERGED) return rc;
+  std::vector<double> hist(std::min(iters, kMaxHist));
+  double scal[4];
+  if (!hist.empty())
+    CK(cudaMemcpy(hist.data(), ctx->hist, sizeof(double) * hist.size(), cudaMemcpyDeviceToHost));
+  CK(cudaMemcpy(scal, ctx->scal, sizeof(double) * 4, cudaMemcpyDeviceToHost));
+  ctx->kappa = hist.empty() ? NAN : hist.back();
+  ctx->last_iters = iters;
+  ctx->last_opts = op;
+  ctx->solved = true;
+  if (stats) {
+    std::memset(stats, 0, sizeof(*stats));
+    stats->iterations = iters;
+    stats->fourier_iterations = fiters;
+    stats->converged = done == 1;
+    stats->kappa_eff = ctx->kappa;
+    stats->delta_TL = scal[2];
+    stats->time_fourier_ms = t_f;
+    stats->time_iter_ms = t_i;
+    stats->time_total_ms = t_f + t_i;
+    stats->updates_per_s = t_i > 0 ? (double)ctx->n_solid * ctx->O * iters / (t_i * 1e-3) : 0.0;
+    stats->group_size = ctx->G;
+    stats->rows_per_thread = ctx->R;
+    stats->threads_per_block = ctx->threads;
+    stats->n_groups = (int)ctx->items_h.size();
+    stats->n_history = (int)hist.size();
+    for (size_t i = 0; i < hist.size(); ++i) stats->kappa_history[i] = hist[i];
+    stats->n_sweeps = tm.n_sweeps;
+    stats->time_sweep_ms = tm.sweep_ms;
+    stats->time_finalize_ms = tm.finalize_ms;
+  }
+  if (done == 3) return ctx->fail(OBTE_ENONFINITE, "non-finite value in the iterate");
+  if (done != 1) return ctx->fail(OBTE_NOT_CONVERGED, "stopping test not met within max_iter");
+  return OBTE_OK;
+}
+
+// ---------------------------------------------------------------------------
+// outputs
+// ---------------------------------------------------------------------------
+template <typename F>
+static void to_user(const obte_ctx* ctx, F&& per_cell) {
+  const int Nx = ctx->n[0], Ny = ctx->n[1];
+  for (int c = 0; c < ctx->n_cells; ++c) {
+    const int kc[3] = {c % Nx, (c / Nx) % Ny, c / (Nx * Ny)};
+    int u[3];
+    for (int i = 0; i < 3; ++i) u[ctx->perm[i]] = kc[i];
+    const long ui = u[0] + (long)ctx->user_n[0] * (u[1] + (long)ctx->user_n[1] * u[2]);
+    per_cell(c, ui);
+  }
+}
+
+extern "C" int obte_get_kappa_eff(obte_ctx* ctx, double* out) {
+  if (!ctx || !out) return OBTE_EINVAL;
+  if (!ctx->solved) return ctx->fail(OBTE_ESTATE, "solve first");
+  *out = ctx->kappa;
+  return OBTE_OK;
+}
+
+extern "C" int obte_get_T_L(obte_ctx* ctx, double* out) {
+  if (!ctx || !out) return OBTE_EINVAL;
+  if (!ctx->solved) return ctx->fail(OBTE_ESTATE, "solve first");
+  cudaSetDevice(ctx->device);
+  double* tmp = ctx->dalloc_t<double>(ctx->n_cells);
+  NEED(tmp);
+  CK(launch_gauge(ctx->code_d, ctx->TL, ctx->n_cells, tmp, nullptr, ctx->stream));
+  std::vector<double> k(ctx->n_cells);
+  CK(cudaMemcpyAsync(k.data(), tmp, sizeof(double) * ctx->n_cells, cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  ctx->dfree(tmp);
+  to_user(ctx, [&](int c, long ui) { out[ui] = k[c]; });
+  return OBTE_OK;
+}
+
+static int run_flux_pass(obte_ctx* ctx) {
+  if (ctx->flux_done) return OBTE_OK;
+  cudaSetDevice(ctx->device);
+  if (!ctx->J_acc) ctx->J_acc = ctx->dalloc_t<double>((size_t)ctx->n_cells * 3);
+  if (!ctx->phi_sec) ctx->phi_sec = ctx->dalloc_t<double>(ctx->n[0]);
+  if (!ctx->phi_bin) ctx->phi_bin = ctx->dalloc_t<double>(ctx->M);
+  NEED(ctx->J_acc);
+  NEED(ctx->phi_sec);
+  NEED(ctx->phi_bin);
+  CK(cudaMemsetAsync(ctx->J_acc, 0, sizeof(double) * ctx->n_cells * 3, ctx->stream));
+  CK(cudaMemsetAsync(ctx->phi_sec, 0, sizeof(double) * ctx->n[0], ctx->stream));
+  CK(cudaMemsetAsync(ctx->phi_bin, 0, sizeof(double) * ctx->M, ctx->stream));
+  ctx->gh.J_acc = ctx->J_acc;
+  ctx->gh.phi_sec = ctx->phi_sec;
+  ctx->gh.phi_bin = ctx->phi_bin;
+  int zero = 0;
+  CK(cudaMemcpyAsync(ctx->gd, &ctx->gh, sizeof(GeomDev), cudaMemcpyHostToDevice, ctx->stream));
+  CK(cudaMemcpyAsync(ctx->ctrl, &zero, sizeof(int), cudaMemcpyHostToDevice, ctx->stream));  // done = 0
+  CK(sweep_once(ctx, SWEEP_FLUX));
+  // the pass does not advance the iterate: drop its moment accumulations
+  CK(cudaMemsetAsync(ctx->TL_acc, 0, sizeof(double) * ctx->n_cells, ctx->stream));
+  CK(cudaMemsetAsync(ctx->wall_acc, 0, sizeof(double) * std::max(1, ctx->n_walls), ctx->stream));
+  CK(cudaMemsetAsync(ctx->scal, 0, sizeof(double), ctx->stream));
+  int one = 1;
+  CK(cudaMemcpyAsync(ctx->ctrl, &one, sizeof(int), cudaMemcpyHostToDevice, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  ctx->flux_done = true;
+  return OBTE_OK;
+}
+
+extern "C" int obte_get_flux(obte_ctx* ctx, double* out) {
+  if (!ctx || !out) return OBTE_EINVAL;
+  if (!ctx->solved) return ctx->fail(OBTE_ESTATE, "solve first");
+  int rc = run_flux_pass(ctx);
+  if (rc) return rc;
+  std::vector<double> J((size_t)ctx->n_cells * 3);
+  CK(cudaMemcpy(J.data(), ctx->J_acc, sizeof(double) * J.size(), cudaMemcpyDeviceToHost));
+  const int dim = ctx->dim;
+  to_user(ctx, [&](int c, long ui) {
+    const bool solid = ctx->code_h[c] & CODE_SOLID;
+    for (int i = 0; i < dim; ++i) {
+      const int ua = ctx->perm[i];
+      out[ui * dim + ua] = solid ? J[3 * (size_t)c + i] : NAN;
+    }
+  });
+  return OBTE_OK;
+}
+
+extern "C" int obte_get_section_flux(obte_ctx* ctx, double* out) {
+  if (!ctx || !out) return OBTE_EINVAL;
+  if (!ctx->solved) return ctx->fail(OBTE_ESTATE, "solve first");
+  int rc = run_flux_pass(ctx);
+  if (rc) return rc;
+  std::vector<double> p(ctx->n[0]);
+  CK(cudaMemcpy(p.data(), ctx->phi_sec, sizeof(double) * p.size(), cudaMemcpyDeviceToHost));
+  for (int i = 0; i < ctx->n[0]; ++i) out[i] = ctx->kappa_scale * p[i];
+  return OBTE_OK;
+}
+
+extern "C" int obte_get_kappa_bins(obte_ctx* ctx, double* out) {
+  if (!ctx || !out) return OBTE_EINVAL;
+  if (!ctx->solved) return ctx->fail(OBTE_ESTATE, "solve first");
+  int rc = run_flux_pass(ctx);
+  if (rc) return rc;
+  std::vector<double> p(ctx->M);
+  CK(cudaMemcpy(p.data(), ctx->phi_bin, sizeof(double) * p.size(), cudaMemcpyDeviceToHost));
+  for (int m = 0; m < ctx->M; ++m) out[m] = ctx->kappa_scale * p[m];
+  return OBTE_OK;
+}
+
+// ---------------------------------------------------------------------------
+// d kappa / d s
+// ---------------------------------------------------------------------------
+extern "C" int obte_kappa_grad_s(obte_ctx* ctx, double* out, size_t max_field_bytes) {
+  if (!ctx || !out) return OBTE_EINVAL;
+  if (!ctx->solved) return ctx->fail(OBTE_ESTATE, "solve first");
+  cudaSetDevice(ctx->device);
+  const int O = ctx->O;
+  // reversed ordinate of every sorted ordinate (same bin, opposite direction)
+  std::vector<int> rev(O, -1);
+  {
+    std::map<std::tuple<int, long long, long long, long long>, int> idx;
+    auto keyf = [&](int o, double sgn) {
+      return std::make_tuple(ctx->ord_m[o], llround(sgn * ctx->pk[0][o] * 1e12),
+                             llround(sgn * ctx->pk[1][o] * 1e12), llround(sgn * ctx->pk[2][o] * 1e12));
+    };
+    for (int o = 0; o < O; ++o) idx[keyf(o, 1.0)] = o;
+    for (int o = 0; o < O; ++o) {
+      auto it = idx.find(keyf(o, -1.0));
+      if (it == idx.end()) return ctx->fail(OBTE_EINVAL, "direction set is not symmetric under p -> -p");
+      rev[o] = it->second;
+    }
+  }
+  if (max_field_bytes == 0) max_field_bytes = (size_t)1 << 30;
+  const size_t e = ctx->precision == 0 ? 8 : 4;
+  const size_t per_ord = e * (size_t)ctx->n_cells;
+  // batches: whole reversed octant pairs when they fit, else matching slices
+  std::vector<std::vector<int>> batches;
+  {
+    int o = 0;
+    while (o < O) {
+      const int q = ctx->octant[o];
+      int e1 = o;
+      while (e1 < O && ctx->octant[e1] == q) ++e1;
+      int e2 = e1;
+      while (e2 < O && ctx->octant[e2] == ctx->octant[e1]) ++e2;
+      const int half = e1 - o;  // ordinates per octant
+      const size_t cap = std::max<size_t>(1, max_field_bytes / (2 * per_ord));
+      for (int a = 0; a < half; a += (int)cap) {
+        std::vector<int> b;
+        for (int k2 = a; k2 < std::min(half, a + (int)cap); ++k2) {
+          b.push_back(o + k2);
+          b.push_back(rev[o + k2]);
+        }
+        batches.push_back(b);
+      }
+      o = e2;
+    }
+  }
+  size_t max_b = 0;
+  for (auto& b : batches) max_b = std::max(max_b, b.size());
+  void* rec = ctx->dalloc(per_ord * max_b);
+  int* slot_d = ctx->dalloc_t<int>(O);
+  int* revl_d = ctx->dalloc_t<int>(max_b);
+  double* a_d = ctx->dalloc_t<double>(max_b);
+  double* grad_d = ctx->dalloc_t<double>(ctx->n_cells);
+  NEED(rec);
+  NEED(slot_d);
+  NEED(revl_d);
+  NEED(a_d);
+  NEED(grad_d);
+  CK(cudaMemsetAsync(grad_d, 0, sizeof(double) * ctx->n_cells, ctx->stream));
+  // adjoint jump: -(L_x / (dT N_sec)) d_ang h_x sum kappa_m / Lambda_m^2; the
+  // adjoint field of o is jscale * T_rev(o) (up to a constant that cancels)
+  const double jadj = -ctx->kappa_scale * ctx->d_ang * ctx->h[0] * ctx->sum_k_over_l2;
+  const double jscale = jadj / ctx->dT;
+  std::vector<int> slot(O);
+  std::vector<WorkItem> all_items = ctx->items_h;
+  int one = 1, zero = 0;
+  for (auto& b : batches) {
+    std::fill(slot.begin(), slot.end(), -1);
+    for (size_t k2 = 0; k2 < b.size(); ++k2) slot[b[k2]] = (int)k2;
+    std::vector<int> revl(b.size());
+    std::vector<double> ab(b.size());
+    for (size_t k2 = 0; k2 < b.size(); ++k2) {
+      revl[k2] = slot[rev[b[k2]]];
+      ab[k2] = ctx->aw[b[k2]];
+    }
+    // work items that hold a recorded ordinate
+    std::vector<WorkItem> its;
+    for (auto& it : all_items) {
+      bool any = false;
+      for (int o = it.o0; o < it.o0 + it.count; ++o)
+        if (slot[o] >= 0) any = true;
+      if (any) its.push_back(it);
+    }
+    WorkItem* its_d = ctx->dalloc_t<WorkItem>(its.size());
+    NEED(its_d);
+    CK(cudaMemcpyAsync(its_d, its.data(), sizeof(WorkItem) * its.size(), cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaMemcpyAsync(slot_d, slot.data(), sizeof(int) * O, cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaMemcpyAsync(revl_d, revl.data(), sizeof(int) * b.size(), cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaMemcpyAsync(a_d, ab.data(), sizeof(double) * b.size(), cudaMemcpyHostToDevice, ctx->stream));
+    GeomDev g = ctx->gh;
+    g.rec = rec;
+    g.rec_slot = slot_d;
+    CK(cudaMemcpyAsync(ctx->gd, &g, sizeof(GeomDev), cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaMemcpyAsync(ctx->ctrl, &zero, sizeof(int), cudaMemcpyHostToDevice, ctx->stream));
+    SweepLaunch L;
+    L.geoms = ctx->gd;
+    L.items = its_d;
+    L.n_items = (int)its.size();
+    L.flags = SWEEP_RECORD | (ctx->has_s ? SWEEP_HAS_S : 0);
+    L.item_counter = nullptr;
+    const size_t smem = sweep_smem_bytes(ctx->precision, ctx->dim, ctx->G, ctx->R, ctx->threads);
+    CK(launch_sweep(L, ctx->precision, ctx->dim, ctx->G, ctx->R, ctx->threads, L.n_items, smem, ctx->stream));
+    CK(launch_grad_contract2(ctx->code_d, ctx->TL, ctx->n_cells, rec, (int)b.size(), revl_d, a_d,
+                             jscale, grad_d, ctx->precision, ctx->stream));
+    CK(cudaMemsetAsync(ctx->TL_acc, 0, sizeof(double) * ctx->n_cells, ctx->stream));
+    CK(cudaMemsetAsync(ctx->wall_acc, 0, sizeof(double) * std::max(1, ctx->n_walls), ctx->stream));
+    CK(cudaMemsetAsync(ctx->scal, 0, sizeof(double), ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    ctx->dfree(its_d);
+  }
+  CK(cudaMemcpyAsync(ctx->gd, &ctx->gh, sizeof(GeomDev), cudaMemcpyHostToDevice, ctx->stream));
+  CK(cudaMemcpyAsync(ctx->ctrl, &one, sizeof(int), cudaMemcpyHostToDevice, ctx->stream));
+  std::vector<double> gk(ctx->n_cells);
+  CK(cudaMemcpyAsync(gk.data(), grad_d, sizeof(double) * ctx->n_cells, cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  for (void* p : {rec, (void*)slot_d, (void*)revl_d, (void*)a_d, (void*)grad_d}) ctx->dfree(p);
+  to_user(ctx, [&](int c, long ui) { out[ui] = (ctx->code_h[c] & CODE_SOLID) ? gk[c] : 0.0; });
+  return OBTE_OK;
+}
+
+// ---------------------------------------------------------------------------
+// batched solve: many geometries, one persistent sweep launch per iteration
+// ---------------------------------------------------------------------------
+extern "C" int obte_solve_batch(obte_ctx* const* ctxs, int n, const obte_solve_opts* opts,
+                                obte_solve_stats* stats) {
+  if (!ctxs || n < 1 || !ctxs[0]) return OBTE_EINVAL;
+  obte_ctx* ctx = ctxs[0];  // owns the batch buffers and the stream
+  for (int i = 0; i < n; ++i) {
+    if (!ctxs[i]) return ctx->fail(OBTE_EINVAL, "null context in batch");
+    if (!ctxs[i]->has_mesh || !ctxs[i]->has_material)
+      return ctx->fail(OBTE_ESTATE, "every context needs create_mesh and set_material");
+    if (ctxs[i]->device != ctx->device || ctxs[i]->dim != ctx->dim)
+      return ctx->fail(OBTE_EINVAL, "batch contexts must share device and dimension");
+  }
+  obte_solve_opts op;
+  if (opts) op = *opts;
+  else obte_default_opts(&op);
+  if (op.precision != OBTE_FP64 && op.precision != OBTE_MIXED) return ctx->fail(OBTE_EINVAL, "bad precision");
+  if (op.max_iter < 1) return ctx->fail(OBTE_EINVAL, "max_iter must be >= 1");
+  const int prec = op.precision == OBTE_FP64 ? 0 : 1;
+  cudaSetDevice(ctx->device);
+  // a variant every geometry accepts; the block covers the largest geometry
+  std::vector<Variant> common;
+  int max_ny = 0, max_nz = 0;
+  for (int i = 0; i < n; ++i) {
+    max_ny = std::max(max_ny, ctxs[i]->n[1]);
+    max_nz = std::max(max_nz, ctxs[i]->n[2]);
+  }
+  for (auto& c : candidates(prec, ctx->dim, max_ny, max_nz)) {
+    bool ok = true;
+    for (int i = 0; i < n; ++i)
+      if (ctxs[i]->n[1] % c.R != 0) ok = false;
+    if ((op.group_size > 0 && c.G != op.group_size) || (op.rows_per_thread > 0 && c.R != op.rows_per_thread))
+      ok = false;
+    if (ok) common.push_back(c);
+  }
+  if (common.empty()) return ctx->fail(OBTE_EINVAL, "no compiled sweep variant fits every geometry");
+  Variant v = common[0];
+  if (op.group_size == 0 && op.rows_per_thread == 0) {
+    // prefer the variant whose rows per thread keep the largest mesh at <= 256 threads
+    // with the fewest idle threads on small meshes
+    long best = -1;
+    for (auto& c : common) {
+      long busy = 0;
+      const int thr = threads_for(max_ny, max_nz, c.R);
+      for (int i = 0; i < n; ++i) busy += (long)threads_for(ctxs[i]->n[1], ctxs[i]->n[2], c.R) * 1000 / thr;
+      if (busy > best) {
+        best = busy;
+        v = c;
+      }
+    }
+  }
+  for (int i = 0; i < n; ++i) {
+    int rc = prepare_state(ctxs[i], prec, v.G, v.R, op.max_iter, op);
+    if (rc) return ctx->fail(rc, std::string("batch member: ") + ctxs[i]->err);
+    ctxs[i]->flux_done = false;
+  }
+  const int threads = threads_for(max_ny, max_nz, v.R);
+  const size_t smem = sweep_smem_bytes(prec, ctx->dim, v.G, v.R, threads);
+  // contiguous geometry table and a work list sorted by cost (largest first)
+  GeomDev* gds = ctx->dalloc_t<GeomDev>(n);
+  NEED(gds);
+  std::vector<GeomDev> gh(n);
+  std::vector<WorkItem> items;
+  for (int i = 0; i < n; ++i) {
+    gh[i] = ctxs[i]->gh;
+    build_items(ctxs[i], i, v.G, items);
+  }
+  std::stable_sort(items.begin(), items.end(), [&](const WorkItem& a, const WorkItem& b) {
+    return (long)gh[a.geom].n_cells * a.count > (long)gh[b.geom].n_cells * b.count;
+  });
+  WorkItem* items_d = ctx->dalloc_t<WorkItem>(items.size());
+  int* counter = ctx->dalloc_t<int>(1);
+  NEED(items_d);
+  NEED(counter);
+  CK(cudaMemcpyAsync(gds, gh.data(), sizeof(GeomDev) * n, cudaMemcpyHostToDevice, ctx->stream));
+  CK(cudaMemcpyAsync(items_d, items.data(), sizeof(WorkItem) * items.size(), cudaMemcpyHostToDevice,
+                     ctx->stream));
+  int sms = 148;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ctx->device);
+  const int per_sm = std::max(1, sweep_blocks_per_sm(prec, ctx->dim, v.G, v.R, threads, smem));
+  const int blocks = (int)std::min<long>((long)items.size(), (long)sms * per_sm);
+  int max_cells = 0;
+  for (int i = 0; i < n; ++i) max_cells = std::max(max_cells, ctxs[i]->n_cells);
+
+  cudaEvent_t e0, e1, e2;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  CK(cudaEventCreate(&e2));
+  CK(cudaEventRecord(e0, ctx->stream));
+  // Fourier first guess and initial state per geometry (on the batch stream)
+  std::vector<int> fiters(n, 0);
+  for (int i = 0; i < n; ++i) {
+    obte_ctx* c = ctxs[i];
+    cudaStream_t keep = c->stream;
+    c->stream = ctx->stream;
+    int fmax = op.fourier_max_iter > 0 ? op.fourier_max_iter : 4 * (c->n[0] + c->n[1] + c->n[2]);
+    double ftol = op.fourier_tol > 0 ? op.fourier_tol : 1e-4;
+    cudaError_t e = launch_fourier_cg(c->gh, c->h[0], c->h[1], c->h[2], prec, fmax, ftol, c->TF,
+                                      c->fiters, c->fwork, kFourierBlocksMax, ctx->stream);
+    if (e == cudaSuccess) e = launch_init_state_oct(gds, gh[i], i, c->TF, prec, c->octant_d, ctx->stream);
+    c->stream = keep;
+    if (e != cudaSuccess) return ctx->cuda_fail(e, "batch init");
+  }
+  CK(cudaEventRecord(e1, ctx->stream));
+  const int k = std::max(1, op.check_every);
+  auto body = [&]() -> cudaError_t {
+    for (int it = 0; it < k; ++it) {
+      cudaError_t e = cudaMemsetAsync(counter, 0, sizeof(int), ctx->stream);
+      if (e != cudaSuccess) return e;
+      SweepLaunch L;
+      L.geoms = gds;
+      L.items = items_d;
+      L.n_items = (int)items.size();
+      L.flags = 0;
+      for (int i = 0; i < n; ++i)
+        if (ctxs[i]->has_s) L.flags |= SWEEP_HAS_S;
+      L.item_counter = counter;
+      e = launch_sweep(L, prec, ctx->dim, v.G, v.R, threads, blocks, smem, ctx->stream);
+      if (e != cudaSuccess) return e;
+      e = launch_finalize(gds, n, prec, finalize_blocks(max_cells), ctx->stream);
+      if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+  };
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  if (op.use_graph) {
+    cudaError_t e = cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+      cudaError_t eb = body();
+      e = cudaStreamEndCapture(ctx->stream, &graph);
+      if (eb != cudaSuccess) e = eb;
+    }
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&exec, graph, 0);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      if (graph) cudaGraphDestroy(graph);
+      graph = nullptr;
+      exec = nullptr;
+    }
+  }
+  int* hc = nullptr;
+  CK(cudaMallocHost(&hc, sizeof(int) * 4 * n));
+  int rc = OBTE_OK;
+  int launched = 0;
+  while (true) {
+    cudaError_t e = exec ? cudaGraphLaunch(exec, ctx->stream) : body();
+    if (e != cudaSuccess) {
+      rc = ctx->cuda_fail(e, "batch iteration");
+      break;
+    }
+    launched += k;
+    for (int i = 0; i < n && e == cudaSuccess; ++i)
+      e = cudaMemcpyAsync(hc + 4 * i, ctxs[i]->ctrl, 4 * sizeof(int), cudaMemcpyDeviceToHost, ctx->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    if (e != cudaSuccess) {
+      rc = ctx->cuda_fail(e, "batch sync");
+      break;
+    }
+    bool all = true;
+    for (int i = 0; i < n; ++i)
+      if (!hc[4 * i]) all = false;
+    if (all) break;
+    if (launched > op.max_iter + k) break;
+  }
+  CK(cudaEventRecord(e2, ctx->stream));
+  CK(cudaEventSynchronize(e2));
+  float t_f = 0, t_i = 0;
+  cudaEventElapsedTime(&t_f, e0, e1);
+  cudaEventElapsedTime(&t_i, e1, e2);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaEventDestroy(e2);
+  if (exec) cudaGraphExecDestroy(exec);
+  if (graph) cudaGraphDestroy(graph);
+  int worst = OBTE_OK;
+  long total_updates = 0;
+  for (int i = 0; i < n; ++i) total_updates += (long)ctxs[i]->n_solid * ctxs[i]->O * hc[4 * i + 1];
+  for (int i = 0; i < n; ++i) {
+    obte_ctx* c = ctxs[i];
+    const int iters = hc[4 * i + 1], done = hc[4 * i];
+    std::vector<double> hist(std::min(iters, kMaxHist));
+    if (!hist.empty())
+      CK(cudaMemcpy(hist.data(), c->hist, sizeof(double) * hist.size(), cudaMemcpyDeviceToHost));
+    double scal[4];
+    CK(cudaMemcpy(scal, c->scal, sizeof(double) * 4, cudaMemcpyDeviceToHost));
+    c->kappa = hist.empty() ? NAN : hist.back();
+    c->last_iters = iters;
+    c->last_opts = op;
+    c->solved = true;
+    c->gh.kappa_hist = c->hist;
+    CK(cudaMemcpy(c->gd, &c->gh, sizeof(GeomDev), cudaMemcpyHostToDevice));
+    if (stats) {
+      obte_solve_stats* s = stats + i;
+      std::memset(s, 0, sizeof(*s));
+      s->iterations = iters;
+      s->converged = done == 1;
+      s->kappa_eff = c->kappa;
+      s->delta_TL = scal[2];
+      s->time_fourier_ms = t_f;
+      s->time_iter_ms = t_i;
+      s->time_total_ms = t_f + t_i;
+      s->updates_per_s = t_i > 0 ? (double)total_updates / (t_i * 1e-3) : 0.0;
+      s->group_size = v.G;
+      s->rows_per_thread = v.R;
+      s->threads_per_block = threads;
+      s->n_groups = (int)items.size();
+      s->n_history = (int)hist.size();
+      for (size_t j = 0; j < hist.size(); ++j) s->kappa_history[j] = hist[j];
+    }
+    if (done == 3) worst = OBTE_ENONFINITE;
+    else if (done != 1 && worst == OBTE_OK) worst = OBTE_NOT_CONVERGED;
+  }
+  cudaFreeHost(hc);
+  ctx->dfree(gds);
+  ctx->dfree(items_d);
+  ctx->dfree(counter);
+  if (rc) return rc;
+  if (worst == OBTE_ENONFINITE) return ctx->fail(worst, "non-finite value in a batch member");
+  if (worst == OBTE_NOT_CONVERGED) return ctx->fail(worst, "a batch member did not converge");
+  return OBTE_OK;
+}

@@ -1,0 +1,230 @@
+// Per-iteration finalisation (FP64): new lattice and wall temperatures,
+// kappa_eff, convergence test; state initialisation from the Fourier guess;
+// gauge and gradient contraction for the outputs.
+#include <math.h>
+
+#include <algorithm>
+
+#include "obte_internal.h"
+
+namespace {
+
+__device__ __forceinline__ void atomic_max_nonneg(double* addr, double v) {
+  // non-negative doubles order like their bit patterns
+  atomicMax(reinterpret_cast<unsigned long long*>(addr), (unsigned long long)__double_as_longlong(v));
+}
+
+// T_L <- sum_o a_o T_o (E2), T_w <- wall numerator / denominator (E3),
+// kappa from the hot-face flux, then the stopping test of Algorithm 1 in the
+// last block of each geometry.  Grid: x = blocks per geometry, y = geometry.
+template <typename T>
+__global__ void finalize_kernel(const GeomDev* geoms) {
+  const GeomDev& g = geoms[blockIdx.y];
+  if (*(volatile int*)g.done) return;
+  __shared__ double red[32];
+  __shared__ int s_nonfin;
+  __shared__ bool s_last;
+  if (threadIdx.x == 0) s_nonfin = 0;
+  __syncthreads();
+  double dmax = 0.0;
+  int nonfin = 0;
+  T* src = reinterpret_cast<T*>(g.src);
+  const int stride = gridDim.x * blockDim.x;
+  for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < g.n_cells; c += stride) {
+    if (!(g.code[c] & CODE_SOLID)) continue;
+    const double t = g.TL_acc[c];
+    g.TL_acc[c] = 0.0;
+    if (!isfinite(t)) nonfin = 1;
+    dmax = fmax(dmax, fabs(t - g.TL[c]));
+    g.TL[c] = t;
+    src[c] = (T)(g.s ? g.s[c] * t : t);
+  }
+  for (int f = blockIdx.x * blockDim.x + threadIdx.x; f < g.n_walls; f += stride) {
+    const double w = g.wall_acc[f] / g.wall_den[f];
+    g.wall_acc[f] = 0.0;
+    if (!isfinite(w)) nonfin = 1;
+    g.Tw[f] = w;
+  }
+  for (int o = 16; o > 0; o >>= 1) dmax = fmax(dmax, __shfl_xor_sync(0xffffffffu, dmax, o));
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = dmax;
+  if (nonfin) atomicOr(&s_nonfin, 1);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double m = 0.0;
+    for (int w = 0; w < (int)((blockDim.x + 31) >> 5); ++w) m = fmax(m, red[w]);
+    atomic_max_nonneg(g.delta_max, m);
+    if (s_nonfin) atomicOr(g.nonfinite, 1);
+    __threadfence();
+    const unsigned prev = atomicAdd(g.fin_count, 1u);
+    s_last = (prev == gridDim.x - 1);
+  }
+  __syncthreads();
+  if (!s_last || threadIdx.x != 0) return;
+  __threadfence();
+  // last block of this geometry: kappa and the stopping test
+  volatile double* phi = g.phi_acc;
+  const double kappa = g.kappa_scale * (*phi);
+  *phi = 0.0;
+  const int n = *g.iter + 1;
+  *g.iter = n;
+  if (n - 1 < g.max_hist) g.kappa_hist[n - 1] = kappa;
+  const double prevk = (n >= 2 && n - 2 < g.max_hist) ? g.kappa_hist[n - 2] : NAN;
+  volatile double* dm = g.delta_max;
+  const double delta = *dm;
+  g.delta_max[1] = delta;   // last iteration's max |dT_L|, for the host
+  *dm = 0.0;
+  *g.fin_count = 0u;
+  bool conv = n >= 2 && n >= g.min_iter;
+  if (g.tol > 0.0) conv = conv && fabs(kappa - prevk) <= g.tol * fabs(kappa);
+  if (g.tol_TL > 0.0) conv = conv && delta <= g.tol_TL;
+  if (g.tol <= 0.0 && g.tol_TL <= 0.0) conv = false;
+  int done = 0;
+  if (*(volatile int*)g.nonfinite || !isfinite(kappa)) done = 3;
+  else if (conv) done = 1;
+  else if (n >= g.max_iter) done = 2;
+  if (done) *(volatile int*)g.done = done;
+}
+
+// State at iteration 0 from a full-grid temperature T0 (the Fourier guess):
+// T_L, the sweep source, wall temperatures (their cell's value) and the row
+// values carried into the first sweep (the value of the cell each row visits
+// last, for every ordinate's octant).
+template <typename T>
+__global__ void init_state_kernel(const GeomDev* geoms, int gi, const double* T0,
+                                  const int* octant_of) {
+  const GeomDev& g = geoms[gi];
+  const int tid = blockIdx.x * blockDim.x + threadIdx.x;
+  const int stride = gridDim.x * blockDim.x;
+  T* src = reinterpret_cast<T*>(g.src);
+  for (int c = tid; c < g.n_cells; c += stride) {
+    const bool solid = g.code[c] & CODE_SOLID;
+    const double t = solid ? T0[c] : 0.0;
+    g.TL[c] = t;
+    g.TL_acc[c] = 0.0;
+    src[c] = (T)(g.s ? g.s[c] * t : t);
+  }
+  for (int f = tid; f < g.n_walls; f += stride) {
+    g.Tw[f] = T0[g.wall_cell[f]];
+    g.wall_acc[f] = 0.0;
+  }
+  T* front = reinterpret_cast<T*>(g.front);
+  const long total = (long)g.n_ord * g.rows;
+  for (long i = tid; i < total; i += stride) {
+    const int o = (int)(i / g.rows);
+    const int row = (int)(i % g.rows);
+    const int jp = row % g.ny, kp = row / g.ny;
+    const int oc = octant_of[o];
+    const int ip = ((g.nx - 1 - jp - (g.dim == 3 ? kp : 0)) % g.nx + g.nx) % g.nx;
+    const int x = (oc & 1) ? g.nx - 1 - ip : ip;
+    const int y = (oc & 2) ? g.ny - 1 - jp : jp;
+    const int z = (g.dim == 3) ? ((oc & 4) ? g.nz - 1 - kp : kp) : 0;
+    const int c = x + g.nx * (y + g.ny * z);
+    front[i] = (T)((g.code[c] & CODE_SOLID) ? T0[c] : 0.0);
+  }
+  if (tid == 0) {
+    *g.phi_acc = 0.0;
+    g.delta_max[0] = 0.0;
+    g.delta_max[1] = 0.0;
+    *g.iter = 0;
+    *g.done = 0;
+    *g.nonfinite = 0;
+    *g.fin_count = 0u;
+  }
+}
+
+// out[c] = T_L[c] - mean over solid cells (NaN in pores); one block.
+__global__ void gauge_kernel(const uint8_t* code, const double* TL, int n, double* out,
+                             double* mean_out) {
+  __shared__ double red[64];
+  __shared__ double s_mean;
+  double s = 0.0, k = 0.0;
+  for (int c = threadIdx.x; c < n; c += blockDim.x)
+    if (code[c] & CODE_SOLID) {
+      s += TL[c];
+      k += 1.0;
+    }
+  for (int o = 16; o > 0; o >>= 1) {
+    s += __shfl_xor_sync(0xffffffffu, s, o);
+    k += __shfl_xor_sync(0xffffffffu, k, o);
+  }
+  const int w = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+  if ((threadIdx.x & 31) == 0) {
+    red[w] = s;
+    red[32 + w] = k;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double a = 0.0, b = 0.0;
+    for (int i = 0; i < nw; ++i) {
+      a += red[i];
+      b += red[32 + i];
+    }
+    s_mean = b > 0 ? a / b : 0.0;
+    if (mean_out) *mean_out = s_mean;
+  }
+  __syncthreads();
+  for (int c = threadIdx.x; c < n; c += blockDim.x)
+    out[c] = (code[c] & CODE_SOLID) ? TL[c] - s_mean : NAN;
+}
+
+// grad[c] -= jscale * sum_{o in [o0, o1)} a_o T_rev(o)[c] (T_o[c] - T_L[c])
+// over recorded fields rec[(o - o0) * n + c]; rev_local maps o - o0 to the
+// record slot of the reversed ordinate.  The reversed field is the adjoint
+// field of o (see obte_kappa_grad_s).
+template <typename T>
+__global__ void grad_contract_kernel(const uint8_t* code, const double* TL, int n, const T* rec,
+                                     int n_rec, const int* rev_local, const double* a_rec,
+                                     double jscale, double* grad) {
+  for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < n; c += gridDim.x * blockDim.x) {
+    if (!(code[c] & CODE_SOLID)) continue;
+    const double tl = TL[c];
+    double acc = 0.0;
+    for (int k = 0; k < n_rec; ++k) {
+      const double f = (double)rec[(size_t)k * n + c];
+      const double b = (double)rec[(size_t)rev_local[k] * n + c];
+      acc += a_rec[k] * b * (f - tl);
+    }
+    grad[c] -= jscale * acc;
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_finalize(const GeomDev* geoms_dev, int n_geoms, int precision, int blocks,
+                            cudaStream_t st) {
+  dim3 grid(blocks, n_geoms);
+  if (precision == 0) finalize_kernel<double><<<grid, 256, 0, st>>>(geoms_dev);
+  else finalize_kernel<float><<<grid, 256, 0, st>>>(geoms_dev);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_init_state_oct(const GeomDev* geoms_dev, const GeomDev& gh, int gi,
+                                  const double* T0, int precision, const int* octant_of,
+                                  cudaStream_t st) {
+  const long work = std::max((long)gh.n_cells, (long)gh.n_ord * gh.rows);
+  int blocks = (int)std::min<long>((work + 255) / 256, 4096);
+  if (blocks < 1) blocks = 1;
+  if (precision == 0) init_state_kernel<double><<<blocks, 256, 0, st>>>(geoms_dev, gi, T0, octant_of);
+  else init_state_kernel<float><<<blocks, 256, 0, st>>>(geoms_dev, gi, T0, octant_of);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_gauge(const uint8_t* code, const double* TL, int n, double* out,
+                         double* mean_out, cudaStream_t st) {
+  gauge_kernel<<<1, 1024, 0, st>>>(code, TL, n, out, mean_out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_grad_contract2(const uint8_t* code, const double* TL, int n, const void* rec,
+                                  int n_rec, const int* rev_local, const double* a_rec,
+                                  double jscale, double* grad, int precision, cudaStream_t st) {
+  int blocks = (n + 255) / 256;
+  if (blocks > 2048) blocks = 2048;
+  if (precision == 0)
+    grad_contract_kernel<double><<<blocks, 256, 0, st>>>(code, TL, n, (const double*)rec, n_rec,
+                                                         rev_local, a_rec, jscale, grad);
+  else
+    grad_contract_kernel<float><<<blocks, 256, 0, st>>>(code, TL, n, (const float*)rec, n_rec,
+                                                        rev_local, a_rec, jscale, grad);
+  return cudaGetLastError();
+}

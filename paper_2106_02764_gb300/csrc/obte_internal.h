@@ -1,0 +1,115 @@
+// Internal declarations shared by the libobte translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+// ---------------------------------------------------------------------------
+// per-cell face codes (kernel frame): a wall bit means that side of a solid
+// cell has no solid neighbour (pore or non-periodic boundary)
+// ---------------------------------------------------------------------------
+enum : uint8_t {
+  CODE_WALL_XM = 1u << 0,
+  CODE_WALL_XP = 1u << 1,
+  CODE_WALL_YM = 1u << 2,
+  CODE_WALL_YP = 1u << 3,
+  CODE_WALL_ZM = 1u << 4,
+  CODE_WALL_ZP = 1u << 5,
+  CODE_SOLID = 1u << 6,
+};
+
+// sweep flags (runtime, uniform)
+enum : int {
+  SWEEP_HAS_S = 1 << 0,   // per-cell scattering scale: divide per update
+  SWEEP_FLUX = 1 << 1,    // also accumulate J per cell, section fluxes, bin fluxes
+  SWEEP_RECORD = 1 << 2,  // write every ordinate field to the record buffer
+};
+
+// One geometry as seen by the device kernels (kernel frame: x = gradient axis).
+struct GeomDev {
+  int nx, ny, nz, dim;
+  int n_cells;            // nx * ny * nz
+  int rows;               // ny * nz
+  int py, pz;             // periodic flags of y and z
+  int R;                  // rows (along y) per thread
+  int tpp;                // threads per z-plane = ceil(ny / R)
+  int n_ord;              // ordinates
+  int n_walls;
+  double dT;              // applied jump across the x period
+  double kappa_scale;     // L_x / (dT * cells per cross-section)
+  const uint8_t* code;    // [n_cells]
+  const int* wall_id;     // [n_cells * 6], side order -x +x -y +y -z +z; -1 none
+  const double* s;        // [n_cells] scattering scale (nullptr: 1)
+  // iteration state
+  double* TL;             // [n_cells] lattice temperature (FP64)
+  double* TL_acc;         // [n_cells] sum_o a_o T_o of the running sweep
+  void* src;              // [n_cells] s_i T_L,i in the sweep precision
+  double* Tw;             // [n_walls]
+  double* wall_acc;       // [n_walls]
+  const double* wall_den; // [n_walls]
+  const int* wall_cell;   // [n_walls]
+  void* front;            // [n_ord][rows] row values carried between iterations
+  double* phi_acc;        // [1] hot-face flux of the running sweep
+  // flux pass outputs
+  double* J_acc;          // [n_cells * 3]
+  double* phi_sec;        // [nx] flux through every x-section
+  double* phi_bin;        // [n_mfp] hot-face flux per MFP bin
+  // record pass output: rec[rec_slot[o] * n_cells + cell] for rec_slot[o] >= 0
+  void* rec;
+  const int* rec_slot;
+  // ordinate table (sorted by octant), precision of the sweep
+  const void* bx; const void* by; const void* bz; const void* diag; const void* inv;
+  const void* aw; const void* kxa; const void* kya; const void* kza; const void* kx;
+  const int* mbin;        // [n_ord] MFP bin of each sorted ordinate
+  // control
+  int* done;              // [1] converged flag
+  int* iter;              // [1] iterations run
+  double* kappa_hist;     // [max_hist]
+  int max_hist;
+  double* delta_max;      // [1] max |dT_L| (as FP64 bits, via atomicMax on u64)
+  double tol, tol_TL;
+  int min_iter, max_iter;
+  unsigned int* fin_count;  // [1] blocks done in finalize (last-block pattern)
+  int* nonfinite;         // [1]
+};
+
+// A unit of sweep work: ordinates [o0, o0 + count) of one octant of one geometry.
+struct WorkItem {
+  int geom;
+  int octant;   // bit0: p_x < 0, bit1: p_y < 0, bit2: p_z < 0
+  int o0;
+  int count;
+};
+
+struct SweepLaunch {
+  const GeomDev* geoms;
+  const WorkItem* items;
+  int n_items;
+  int flags;
+  int* item_counter;  // persistent work queue (nullptr: one item per block)
+};
+
+// sweep.cu
+cudaError_t launch_sweep(const SweepLaunch& L, int precision, int dim, int G, int RMAX,
+                         int threads, int blocks, size_t smem, cudaStream_t st);
+size_t sweep_smem_bytes(int precision, int dim, int G, int RMAX, int threads);
+bool sweep_variant_exists(int precision, int dim, int G, int RMAX);
+int sweep_blocks_per_sm(int precision, int dim, int G, int RMAX, int threads, size_t smem);
+
+// finalize.cu
+cudaError_t launch_finalize(const GeomDev* geoms_dev, int n_geoms, int precision, int blocks,
+                            cudaStream_t st);
+cudaError_t launch_init_state_oct(const GeomDev* geoms_dev, const GeomDev& gh, int gi,
+                                  const double* T0, int precision, const int* octant_of,
+                                  cudaStream_t st);
+cudaError_t launch_gauge(const uint8_t* code, const double* TL, int n, double* out,
+                         double* mean_out, cudaStream_t st);
+cudaError_t launch_grad_contract2(const uint8_t* code, const double* TL, int n, const void* rec,
+                                  int n_rec, const int* rev_local, const double* a_rec,
+                                  double jscale, double* grad, int precision, cudaStream_t st);
+
+// fourier.cu
+cudaError_t launch_fourier_cg(const GeomDev& g, double hx, double hy, double hz, int precision,
+                              int max_iter, double tol, double* T_out, int* iters_out,
+                              double* work, int blocks_max, cudaStream_t st);
+size_t fourier_work_doubles(int n_cells, int blocks_max);

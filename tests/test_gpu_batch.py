@@ -1,0 +1,59 @@
+"""Batched solve: several geometries of uneven size in one persistent launch
+per iteration (GPU)."""
+import numpy as np
+import pytest
+
+from paper_2106_02764_gb300 import inputs as I
+from gpu_common import KAPPA_RTOL, TL_ATOL, oracle, solid_vector
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    from paper_2106_02764_gb300 import build
+    build.build()
+
+
+def _geoms():
+    L = 100e-9
+    q = I.circle_quadrature(8)
+    return [
+        I.make_2d("b0", 8, L, [I.circle_pore(L, L, 0.2)], 3, q),
+        I.make_2d("b1", 16, L, [I.square_pore(L, L, 0.1, x=0.3 * L, y=0.6 * L)], 3, q),
+        I.make_2d("b2", 16, L, [I.circle_pore(L, L, 0.05, x=0.2 * L, y=0.2 * L),
+                                I.square_pore(L, L, 0.05, x=0.7 * L, y=0.7 * L)], 3, q),
+        I.make_2d("b3", 12, L, [], 3, q),
+    ]
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_batch_matches_oracle(precision):
+    from paper_2106_02764_gb300.binding import Solver, solve_batch
+    geoms = _geoms()
+    solvers = [Solver.from_workload(w) for w in geoms]
+    if precision == "fp64":
+        opts = dict(tol=1e-12, tol_TL=1e-13, max_iter=200000, check_every=32)
+    else:
+        opts = dict(tol=0.0, tol_TL=0.0, max_iter=4000, check_every=50)
+    stats = solve_batch(solvers, precision=precision, allow_not_converged=True, **opts)
+    for w, s, st in zip(geoms, solvers, stats):
+        pr, ref = oracle(w)
+        assert abs(s.kappa_eff - ref.kappa) <= KAPPA_RTOL[precision] * ref.kappa
+        assert np.abs(solid_vector(pr, s.T_L()) - ref.T_L).max() <= TL_ATOL
+    if precision == "fp64":
+        # per-geometry stopping: iteration counts differ between geometries
+        its = [st["iterations"] for st in stats]
+        assert len(set(its)) > 1
+
+
+def test_batch_equals_single():
+    from paper_2106_02764_gb300.binding import Solver, solve_batch
+    geoms = _geoms()
+    solvers = [Solver.from_workload(w) for w in geoms]
+    solve_batch(solvers, precision="fp64", tol=1e-12, tol_TL=1e-13, max_iter=200000,
+                allow_not_converged=True)
+    for w, s in zip(geoms, solvers):
+        one = Solver.from_workload(w)
+        one.solve(precision="fp64", tol=1e-12, tol_TL=1e-13, max_iter=200000, allow_not_converged=True)
+        assert abs(one.kappa_eff - s.kappa_eff) < 1e-10 * one.kappa_eff
