@@ -59,6 +59,7 @@ struct obte_ctx {
   void* tab_d[2][9] = {{nullptr}};                // [precision][table]
   int* mbin_d = nullptr;
   int* octant_d = nullptr;
+  int* ord_d0_d = nullptr;
   double kappa_scale = 0.0, sum_k_over_l2 = 0.0;
 
   // solve state
@@ -130,7 +131,7 @@ struct obte_ctx {
     wall_den_d = nullptr;
     for (auto& a : tab_d)
       for (auto& b : a) b = nullptr;
-    mbin_d = octant_d = nullptr;
+    mbin_d = octant_d = ord_d0_d = nullptr;
     gd = nullptr;
     TL = TL_acc = Tw = wall_acc = scal = hist = TF = fwork = J_acc = phi_sec = phi_bin = nullptr;
     src = front = nullptr;
@@ -589,7 +590,7 @@ int threads_for(int ny, int nz, int R) {
   return ((t + 31) / 32) * 32;
 }
 
-std::vector<Variant> candidates(int precision, int dim, int ny, int nz) {
+std::vector<Variant> candidates(int precision, int dim, int ny, int nz, bool has_s) {
   std::vector<Variant> out;
   const Variant* v;
   int n;
@@ -603,9 +604,9 @@ std::vector<Variant> candidates(int precision, int dim, int ny, int nz) {
   for (int i = 0; i < n; ++i) {
     if (ny % v[i].R != 0) continue;
     const int thr = threads_for(ny, nz, v[i].R);
-    if (thr > (dim == 3 ? 512 : 256)) continue;
+    if (thr > ((dim == 3 && v[i].R < 8) ? 512 : 256)) continue;  // the kernel's launch bound
     if (sweep_smem_bytes(precision, dim, v[i].G, v[i].R, thr) > 200 * 1024) continue;
-    if (!sweep_variant_exists(precision, dim, v[i].G, v[i].R)) continue;
+    if (!sweep_variant_exists(precision, dim, v[i].G, v[i].R, has_s)) continue;
     out.push_back(v[i]);
   }
   return out;
@@ -618,14 +619,27 @@ std::map<std::tuple<int, int, int, int, int, int>, Variant>& tune_cache() {
 
 }  // namespace
 
-static void build_items(obte_ctx* ctx, int geom, int G, std::vector<WorkItem>& items) {
+// Work items: runs of at most G ordinates of one octant.  Items of one octant
+// start their wavefront at evenly spaced columns (d0) so that, at a given
+// step, they update different cells.
+static void build_items(obte_ctx* ctx, int geom, int G, std::vector<WorkItem>& items,
+                        std::vector<int>* ord_d0 = nullptr) {
   const int O = ctx->O;
+  const int nx = ctx->n[0];
+  if (ord_d0) ord_d0->assign(O, 0);
   int o = 0;
   while (o < O) {
     const int q = ctx->octant[o];
     int e = o;
     while (e < O && ctx->octant[e] == q) ++e;
-    for (int a = o; a < e; a += G) items.push_back({geom, q, a, std::min(G, e - a)});
+    const int n_it = (e - o + G - 1) / G;
+    int k = 0;
+    for (int a = o; a < e; a += G, ++k) {
+      const int d0 = (int)(((long)k * nx) / std::max(1, n_it)) % nx;
+      items.push_back({geom, q, a, std::min(G, e - a), d0});
+      if (ord_d0)
+        for (int b = a; b < std::min(e, a + G); ++b) (*ord_d0)[b] = d0;
+    }
     o = e;
   }
 }
@@ -717,6 +731,7 @@ static int prepare_state(obte_ctx* ctx, int precision, int G, int R, int max_ite
   g.kya = ctx->tab_d[p][TB_KYA];
   g.kza = ctx->tab_d[p][TB_KZA];
   g.mbin = ctx->mbin_d;
+  g.ord_d0 = nullptr;  // set below once the work items are known
   g.done = ctx->ctrl + 0;
   g.iter = ctx->ctrl + 1;
   g.nonfinite = ctx->ctrl + 2;
@@ -727,22 +742,29 @@ static int prepare_state(obte_ctx* ctx, int precision, int G, int R, int max_ite
   g.tol_TL = op.tol_TL;
   g.min_iter = std::max(op.min_iter, 1);
   g.max_iter = max_iter;
-  CK(cudaMemcpyAsync(ctx->gd, &g, sizeof(GeomDev), cudaMemcpyHostToDevice, ctx->stream));
   ctx->G = G;
   ctx->R = R;
   ctx->threads = threads_for(Ny, Nz, R);
   std::vector<WorkItem> items;
-  build_items(ctx, 0, G, items);
+  std::vector<int> ord_d0;
+  build_items(ctx, 0, G, items, &ord_d0);
   const bool same = ctx->items_d && items.size() == ctx->items_h.size() &&
                     std::memcmp(items.data(), ctx->items_h.data(), sizeof(WorkItem) * items.size()) == 0;
   if (!same) {
     ctx->items_h = items;
+    if (ctx->ord_d0_d) ctx->dfree(ctx->ord_d0_d);
+    ctx->ord_d0_d = ctx->dalloc_t<int>(ctx->O);
+    NEED(ctx->ord_d0_d);
+    CK(cudaMemcpyAsync(ctx->ord_d0_d, ord_d0.data(), sizeof(int) * ctx->O, cudaMemcpyHostToDevice,
+                       ctx->stream));
     if (ctx->items_d) ctx->dfree(ctx->items_d);
     ctx->items_d = ctx->dalloc_t<WorkItem>(ctx->items_h.size());
     NEED(ctx->items_d);
     CK(cudaMemcpyAsync(ctx->items_d, ctx->items_h.data(), sizeof(WorkItem) * ctx->items_h.size(),
                        cudaMemcpyHostToDevice, ctx->stream));
   }
+  g.ord_d0 = ctx->ord_d0_d;
+  CK(cudaMemcpyAsync(ctx->gd, &g, sizeof(GeomDev), cudaMemcpyHostToDevice, ctx->stream));
   return OBTE_OK;
 }
 
@@ -751,11 +773,11 @@ static cudaError_t sweep_once(obte_ctx* ctx, int flags) {
   L.geoms = ctx->gd;
   L.items = ctx->items_d;
   L.n_items = (int)ctx->items_h.size();
-  L.flags = flags | (ctx->has_s ? SWEEP_HAS_S : 0);
+  L.flags = flags;
   L.item_counter = nullptr;
   const size_t smem = sweep_smem_bytes(ctx->precision, ctx->dim, ctx->G, ctx->R, ctx->threads);
-  return launch_sweep(L, ctx->precision, ctx->dim, ctx->G, ctx->R, ctx->threads, L.n_items, smem,
-                      ctx->stream);
+  return launch_sweep(L, ctx->precision, ctx->dim, ctx->G, ctx->R, ctx->has_s, ctx->threads,
+                      L.n_items, smem, ctx->stream);
 }
 
 static int finalize_blocks(int n_cells) {
@@ -778,9 +800,9 @@ static int init_from_fourier(obte_ctx* ctx, const obte_solve_opts& op, int* fite
 
 static int pick_variant(obte_ctx* ctx, int precision, const obte_solve_opts& op, Variant* out) {
   const int Ny = ctx->n[1], Nz = ctx->n[2];
-  auto cands = candidates(precision, ctx->dim, Ny, Nz);
+  auto cands = candidates(precision, ctx->dim, Ny, Nz, ctx->has_s);
   if (op.group_size > 0 || op.rows_per_thread > 0) {
-    for (auto& c : candidates(precision, ctx->dim, Ny, Nz))
+    for (auto& c : candidates(precision, ctx->dim, Ny, Nz, ctx->has_s))
       if ((op.group_size <= 0 || c.G == op.group_size) && (op.rows_per_thread <= 0 || c.R == op.rows_per_thread)) {
         *out = c;
         return OBTE_OK;
@@ -788,7 +810,7 @@ static int pick_variant(obte_ctx* ctx, int precision, const obte_solve_opts& op,
     return ctx->fail(OBTE_EINVAL, "no compiled sweep variant matches group_size / rows_per_thread for this mesh");
   }
   if (cands.empty()) return ctx->fail(OBTE_EINVAL, "no compiled sweep variant fits this mesh (rows per plane too many?)");
-  auto key = std::make_tuple(precision, ctx->dim, ctx->n[0], Ny, Nz, ctx->O);
+  auto key = std::make_tuple(precision * 2 + (ctx->has_s ? 1 : 0), ctx->dim, ctx->n[0], Ny, Nz, ctx->O);
   auto it = tune_cache().find(key);
   if (it != tune_cache().end()) {
     *out = it->second;
@@ -813,8 +835,8 @@ static int pick_variant(obte_ctx* ctx, int precision, const obte_solve_opts& op,
 
 // timed autotune over the compiled variants (group_size = -1)
 static int autotune(obte_ctx* ctx, int precision, const obte_solve_opts& op, Variant* out) {
-  auto key = std::make_tuple(precision, ctx->dim, ctx->n[0], ctx->n[1], ctx->n[2], ctx->O);
-  auto cands = candidates(precision, ctx->dim, ctx->n[1], ctx->n[2]);
+  auto key = std::make_tuple(precision * 2 + (ctx->has_s ? 1 : 0), ctx->dim, ctx->n[0], ctx->n[1], ctx->n[2], ctx->O);
+  auto cands = candidates(precision, ctx->dim, ctx->n[1], ctx->n[2], ctx->has_s);
   if (cands.empty()) return ctx->fail(OBTE_EINVAL, "no compiled sweep variant fits this mesh");
   cudaEvent_t a, b;
   CK(cudaEventCreate(&a));
@@ -1237,10 +1259,11 @@ extern "C" int obte_kappa_grad_s(obte_ctx* ctx, double* out, size_t max_field_by
     L.geoms = ctx->gd;
     L.items = its_d;
     L.n_items = (int)its.size();
-    L.flags = SWEEP_RECORD | (ctx->has_s ? SWEEP_HAS_S : 0);
+    L.flags = SWEEP_RECORD;
     L.item_counter = nullptr;
     const size_t smem = sweep_smem_bytes(ctx->precision, ctx->dim, ctx->G, ctx->R, ctx->threads);
-    CK(launch_sweep(L, ctx->precision, ctx->dim, ctx->G, ctx->R, ctx->threads, L.n_items, smem, ctx->stream));
+    CK(launch_sweep(L, ctx->precision, ctx->dim, ctx->G, ctx->R, ctx->has_s, ctx->threads, L.n_items,
+                    smem, ctx->stream));
     CK(launch_grad_contract2(ctx->code_d, ctx->TL, ctx->n_cells, rec, (int)b.size(), revl_d, a_d,
                              jscale, grad_d, ctx->precision, ctx->stream));
     CK(cudaMemsetAsync(ctx->TL_acc, 0, sizeof(double) * ctx->n_cells, ctx->stream));
@@ -1287,7 +1310,9 @@ extern "C" int obte_solve_batch(obte_ctx* const* ctxs, int n, const obte_solve_o
     max_ny = std::max(max_ny, ctxs[i]->n[1]);
     max_nz = std::max(max_nz, ctxs[i]->n[2]);
   }
-  for (auto& c : candidates(prec, ctx->dim, max_ny, max_nz)) {
+  bool any_s = false;
+  for (int i = 0; i < n; ++i) any_s = any_s || ctxs[i]->has_s;
+  for (auto& c : candidates(prec, ctx->dim, max_ny, max_nz, any_s)) {
     bool ok = true;
     for (int i = 0; i < n; ++i)
       if (ctxs[i]->n[1] % c.R != 0) ok = false;
@@ -1339,7 +1364,7 @@ extern "C" int obte_solve_batch(obte_ctx* const* ctxs, int n, const obte_solve_o
                      ctx->stream));
   int sms = 148;
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ctx->device);
-  const int per_sm = std::max(1, sweep_blocks_per_sm(prec, ctx->dim, v.G, v.R, threads, smem));
+  const int per_sm = std::max(1, sweep_blocks_per_sm(prec, ctx->dim, v.G, v.R, any_s, threads, smem));
   const int blocks = (int)std::min<long>((long)items.size(), (long)sms * per_sm);
   int max_cells = 0;
   for (int i = 0; i < n; ++i) max_cells = std::max(max_cells, ctxs[i]->n_cells);
@@ -1374,10 +1399,8 @@ extern "C" int obte_solve_batch(obte_ctx* const* ctxs, int n, const obte_solve_o
       L.items = items_d;
       L.n_items = (int)items.size();
       L.flags = 0;
-      for (int i = 0; i < n; ++i)
-        if (ctxs[i]->has_s) L.flags |= SWEEP_HAS_S;
       L.item_counter = counter;
-      e = launch_sweep(L, prec, ctx->dim, v.G, v.R, threads, blocks, smem, ctx->stream);
+      e = launch_sweep(L, prec, ctx->dim, v.G, v.R, any_s, threads, blocks, smem, ctx->stream);
       if (e != cudaSuccess) return e;
       e = launch_finalize(gds, n, prec, finalize_blocks(max_cells), ctx->stream);
       if (e != cudaSuccess) return e;

@@ -114,7 +114,8 @@ __global__ void init_state_kernel(const GeomDev* geoms, int gi, const double* T0
     const int row = (int)(i % g.rows);
     const int jp = row % g.ny, kp = row / g.ny;
     const int oc = octant_of[o];
-    const int ip = ((g.nx - 1 - jp - (g.dim == 3 ? kp : 0)) % g.nx + g.nx) % g.nx;
+    // the column the row visits last: step nx-1 of the group's wavefront
+    const int ip = ((g.nx - 1 + g.ord_d0[o] - jp - (g.dim == 3 ? kp : 0)) % g.nx + g.nx) % g.nx;
     const int x = (oc & 1) ? g.nx - 1 - ip : ip;
     const int y = (oc & 2) ? g.ny - 1 - jp : jp;
     const int z = (g.dim == 3) ? ((oc & 4) ? g.nz - 1 - kp : kp) : 0;

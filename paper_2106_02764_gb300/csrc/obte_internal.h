@@ -61,6 +61,7 @@ struct GeomDev {
   const void* bx; const void* by; const void* bz; const void* diag; const void* inv;
   const void* aw; const void* kxa; const void* kya; const void* kza; const void* kx;
   const int* mbin;        // [n_ord] MFP bin of each sorted ordinate
+  const int* ord_d0;      // [n_ord] start step of the group holding each ordinate
   // control
   int* done;              // [1] converged flag
   int* iter;              // [1] iterations run
@@ -79,6 +80,7 @@ struct WorkItem {
   int octant;   // bit0: p_x < 0, bit1: p_y < 0, bit2: p_z < 0
   int o0;
   int count;
+  int d0;       // start step: row j' visits column (d + d0 - j' - k') mod nx
 };
 
 struct SweepLaunch {
@@ -91,17 +93,18 @@ struct SweepLaunch {
 
 // sweep.cu
 cudaError_t launch_sweep(const SweepLaunch& L, int precision, int dim, int G, int RMAX,
-                         int threads, int blocks, size_t smem, cudaStream_t st);
+                         bool has_s, int threads, int blocks, size_t smem, cudaStream_t st);
 size_t sweep_smem_bytes(int precision, int dim, int G, int RMAX, int threads);
-bool sweep_variant_exists(int precision, int dim, int G, int RMAX);
-int sweep_blocks_per_sm(int precision, int dim, int G, int RMAX, int threads, size_t smem);
+bool sweep_variant_exists(int precision, int dim, int G, int RMAX, bool has_s);
+int sweep_blocks_per_sm(int precision, int dim, int G, int RMAX, bool has_s, int threads,
+                        size_t smem);
 
 // finalize.cu
 cudaError_t launch_finalize(const GeomDev* geoms_dev, int n_geoms, int precision, int blocks,
                             cudaStream_t st);
 cudaError_t launch_init_state_oct(const GeomDev* geoms_dev, const GeomDev& gh, int gi,
                                   const double* T0, int precision, const int* octant_of,
-                                  cudaStream_t st);
+                                  cudaStream_t st);  // uses gh.ord_d0
 cudaError_t launch_gauge(const uint8_t* code, const double* TL, int n, double* out,
                          double* mean_out, cudaStream_t st);
 cudaError_t launch_grad_contract2(const uint8_t* code, const double* TL, int n, const void* rec,

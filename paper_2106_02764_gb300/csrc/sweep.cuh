@@ -7,35 +7,39 @@
 // upwind neighbours of cell (i', j', k') are always (i'-1, j', k'),
 // (i', j'-1, k') and (i', j', k'-1).
 //
-// Wavefront.  Row (j', k') -- the line of cells along x -- processes column
-//     i'(d) = (d - j' - k') mod nx        at step d = 0 .. nx-1.
-// The x neighbour of a cell was processed by the same row one step earlier
-// (or, for the first column visited, in the previous iteration), and the y
-// and z neighbours were processed by the rows below one step earlier (or in
-// the previous iteration at d = 0).  The periodic wrap in x is therefore
-// immediate everywhere except on one skewed cut per row, and the wrap in y
-// (z) is immediate when ny (nz) is a multiple of nx.  Values that cross the
-// cut come from the previous iteration: they are the row values left in
-// `front` by the previous sweep.  Like the walls and T_L of Eq. iter2 they are
-// lagged; the fixed point is unchanged.  Every thread is busy at every step
-// (no wavefront fill or drain).
+// Wavefront.  Row (j', k') -- the line of cells along x -- visits column
+//     i'(d) = (d + d0 - j' - k') mod nx        at step d = 0 .. nx-1,
+// d0 being a per-group start offset.  The x neighbour of a cell was visited by
+// the same row one step earlier (or, for the row's first column, in the
+// previous iteration), and the y and z neighbours were visited by the rows
+// below one step earlier (or in the previous iteration at d = 0).  The
+// periodic wrap in x is therefore immediate except on one skewed cut per row,
+// and the wrap in y (z) is immediate when ny (nz) is a multiple of nx.  Values
+// that cross the cut come from the previous iteration: they are the row values
+// left in `front` by the previous sweep.  Like the walls and T_L of Eq. iter2
+// they are lagged; the fixed point is unchanged.  Every thread is busy at every
+// step (no wavefront fill or drain), and groups of one octant start at
+// different columns, so their moment atomics land on different cells.
 //
-// Threads.  Thread t owns R consecutive rows (R divides ny) j' = jb R .. jb R + R-1 of plane
-// k' (jb = t mod tpp, k' = t / tpp) and keeps their values for all G
-// ordinates of the group in registers.  Rows are updated top-down inside a
-// step, so the row below still holds the previous step's value; only the
-// lowest row needs the value of the thread below, exchanged through shared
-// memory (2D), and in 3D every row needs the row of the plane below.  One
+// Threads.  Thread t owns R consecutive rows (R divides ny) j' = jb R ..
+// jb R + R-1 of plane k' (jb = t mod tpp, k' = t / tpp) and keeps their values
+// for all G ordinates of the group in registers.  Rows are updated top-down
+// inside a step, so the row below still holds the previous step's value; only
+// the lowest row needs the value of the thread below, exchanged through shared
+// memory (2D); in 3D every row also needs the row of the plane below.  One
 // barrier per step; the exchange buffers are double-buffered by step parity.
 //
-// Epilogue per solid cell (Eq. iter2 right-hand side of the next iteration,
-// hot-contact flux of App. A):
+// Epilogue per solid cell (right-hand side of the next iteration, hot-contact
+// flux of App. A):
 //   T_L numerator   sum_g a_g T_g               -> FP64 atomic per cell
 //   wall numerator  sum_g |K_g . n| T_g  (out-of-cell faces that are walls)
 //   hot-face flux   sum_g K_gx (T_g + [p_x > 0] dT)  at the x = 0 plane
 // The within-group sums run in the sweep precision (float in mixed mode) and
-// are promoted to double once per cell per group.
+// are promoted to double once per cell per group.  The periodic jump term
+// beta_x dT / (1 + D) is formed in double once per ordinate.
 #pragma once
+
+#include <stdint.h>
 
 #include "obte_internal.h"
 
@@ -51,6 +55,28 @@ __device__ __forceinline__ int pmod(int a, int n) {
   return r < 0 ? r + n : r;
 }
 
+// Exact binary32 -> binary64 conversion by re-encoding the IEEE 754 fields on
+// the integer pipe (sign kept, exponent re-biased by 1023 - 127, mantissa
+// shifted into the wider field).  Subnormal inputs flush to a signed zero (their
+// magnitude is below 1.2e-38); Inf / NaN keep their class.
+__device__ __forceinline__ double widen(float f) {
+  const uint32_t u = __float_as_uint(f);
+  const uint32_t sign = u & 0x80000000u;
+  const uint32_t e = (u >> 23) & 0xffu;
+  const uint32_t m = u & 0x7fffffu;
+  uint32_t hi, lo;
+  if (e == 0u) {
+    hi = sign;
+    lo = 0u;
+  } else {
+    const uint32_t ed = (e == 0xffu) ? 0x7ffu : e + 896u;
+    hi = sign | (ed << 20) | (m >> 3);
+    lo = m << 29;
+  }
+  return __hiloint2double((int)hi, (int)lo);
+}
+__device__ __forceinline__ double widen(double d) { return d; }
+
 __device__ __forceinline__ double block_sum(double v, double* red) {
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
@@ -65,18 +91,74 @@ __device__ __forceinline__ double block_sum(double v, double* red) {
   return s;  // valid in thread 0
 }
 
-template <typename T, int DIM, int G, int RMAX>
-__global__ void __launch_bounds__(DIM == 3 ? 512 : 256) sweep_kernel(const SweepLaunch L) {
+// Rare per-cell work, kept out of the unrolled update so that the hot loop
+// stays small: wall numerators, hot-face flux, and the flux / record passes.
+// The cell's G values are read from the thread's scratch row in shared memory.
+// Returns the hot-face flux contribution (added to the thread's phi).
+template <typename T, int DIM, int G>
+__device__ __noinline__ double cell_epilogue(const GeomDev& gm, const T* __restrict__ val,
+                                             int cell, uint8_t code, int x, int ip, int o0,
+                                             int cnt, int sx, int sy, int sz, int flags,
+                                             double kx_sum) {
+  const int nx = gm.nx;
+  const double dT = gm.dT;
+  const uint8_t out_x_bit = sx > 0 ? CODE_WALL_XP : CODE_WALL_XM;
+  const uint8_t out_y_bit = sy > 0 ? CODE_WALL_YP : CODE_WALL_YM;
+  const uint8_t out_z_bit = sz > 0 ? CODE_WALL_ZP : CODE_WALL_ZM;
+  const int out_x_side = sx > 0 ? 1 : 0;
+  const int out_y_side = sy > 0 ? 3 : 2;
+  const int out_z_side = sz > 0 ? 5 : 4;
+  double sxk = 0.0, syk = 0.0, szk = 0.0;  // sum_g |K_ga| T_g
+  for (int g = 0; g < cnt; ++g) {
+    const double v = (double)val[g];
+    sxk += (double)ld<T>(gm.kxa, o0 + g) * v;
+    syk += (double)ld<T>(gm.kya, o0 + g) * v;
+    if (DIM == 3) szk += (double)ld<T>(gm.kza, o0 + g) * v;
+  }
+  if (code & out_x_bit) atomicAdd(gm.wall_acc + gm.wall_id[cell * 6 + out_x_side], sxk);
+  if (code & out_y_bit) atomicAdd(gm.wall_acc + gm.wall_id[cell * 6 + out_y_side], syk);
+  if (DIM == 3 && (code & out_z_bit)) atomicAdd(gm.wall_acc + gm.wall_id[cell * 6 + out_z_side], szk);
+  // the x = 0 plane is the out-of-cell x face of the last column i' = nx-1
+  const bool hot = (ip == nx - 1) && !(code & out_x_bit);
+  double phi = 0.0;
+  if (hot) phi = (double)sx * sxk + (sx > 0 ? dT * kx_sum : 0.0);
+  if (flags & SWEEP_FLUX) {
+    atomicAdd(gm.J_acc + 3 * cell + 0, (double)sx * sxk);
+    atomicAdd(gm.J_acc + 3 * cell + 1, (double)sy * syk);
+    if (DIM == 3) atomicAdd(gm.J_acc + 3 * cell + 2, (double)sz * szk);
+    if (!(code & out_x_bit)) {
+      const int sec = sx > 0 ? (x + 1) % nx : x;
+      const bool jmp = sx > 0 && x == nx - 1;
+      atomicAdd(gm.phi_sec + sec, (double)sx * sxk + (jmp ? dT * kx_sum : 0.0));
+    }
+    if (hot)
+      for (int g = 0; g < cnt; ++g) {
+        const double k = (double)sx * (double)ld<T>(gm.kxa, o0 + g);
+        atomicAdd(gm.phi_bin + gm.mbin[o0 + g], k * ((double)val[g] + (sx > 0 ? dT : 0.0)));
+      }
+  }
+  if (flags & SWEEP_RECORD) {
+    T* rec = reinterpret_cast<T*>(gm.rec);
+    for (int g = 0; g < cnt; ++g) {
+      const int sl = gm.rec_slot[o0 + g];
+      if (sl >= 0) rec[(size_t)sl * gm.n_cells + cell] = val[g];
+    }
+  }
+  return phi;
+}
+
+template <typename T, int DIM, int G, int RMAX, bool HAS_S>
+__global__ void __launch_bounds__((DIM == 3 && RMAX < 8) ? 512 : 256, 1) sweep_kernel(const SweepLaunch L) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ double red[32];
   __shared__ int s_item;
   const int nthr = blockDim.x;
   const int t = threadIdx.x;
-  T* xtop = reinterpret_cast<T*>(smem_raw);  // [2][nthr][G]
-  T* xall = xtop + 2 * nthr * G;             // [2][nthr][RMAX][G]   (DIM == 3)
-  const bool has_s = (L.flags & SWEEP_HAS_S) != 0;
-  const bool flux = (L.flags & SWEEP_FLUX) != 0;
-  const bool record = (L.flags & SWEEP_RECORD) != 0;
+  T* xtop = reinterpret_cast<T*>(smem_raw);               // [2][nthr][G]
+  T* scratch = xtop + 2 * nthr * G;                        // [nthr][G]
+  T* xall = scratch + nthr * G;                            // [2][nthr][RMAX][G]  (DIM == 3)
+  const int flags = L.flags;
+  const bool rare_pass = (flags & (SWEEP_FLUX | SWEEP_RECORD)) != 0;
 
   int item = blockIdx.x;
   for (;;) {
@@ -98,35 +180,45 @@ __global__ void __launch_bounds__(DIM == 3 ? 512 : 256) sweep_kernel(const Sweep
     const int sx = (wi.octant & 1) ? -1 : 1;
     const int sy = (wi.octant & 2) ? -1 : 1;
     const int sz = (wi.octant & 4) ? -1 : 1;
-    const int o0 = wi.o0, cnt = wi.count;
+    const int o0 = wi.o0, cnt = wi.count, d0 = wi.d0;
     const double dT = gm.dT;
     const int jb = t % tpp, kp = t / tpp;
     const int j0 = jb * R;
     // the host picks R = RMAX dividing ny: a thread owns all RMAX rows or none
     const int nr = (kp < nz && j0 < ny) ? RMAX : 0;
+    const uint8_t* __restrict__ codev = gm.code;
+    const T* __restrict__ srcv = reinterpret_cast<const T*>(gm.src);
+    const double* __restrict__ Twv = gm.Tw;
+    const int* __restrict__ widv = gm.wall_id;
+    const double* __restrict__ sv_ptr = gm.s;
+    double* TLacc = gm.TL_acc;
 
-    // per-ordinate coefficients.  no s: A0 = 1/(1+D), AX = beta_x/(1+D), ...
-    // with s: A0 = D, AX = beta_x, ...  (premultiplied tables vs raw tables)
-    T A0[G], AX[G], AY[G], AZ[G], AW[G];
+    // per-ordinate coefficients.  HAS_S: A0 = D, AX = beta_x, ...; otherwise
+    // premultiplied by 1/(1+D): A0 = 1/(1+D), AX = beta_x/(1+D), ...
+    // JX = AX * (+-dT): the periodic jump term, formed in double.
+    T A0[G], AX[G], AY[G], AZ[G], AW[G], JX[G];
+    double kx_sum = 0.0;  // sum_g K_gx (signed), jump part of the hot-face flux
 #pragma unroll
     for (int g = 0; g < G; ++g) {
       const bool ok = g < cnt;
       const int o = o0 + (ok ? g : 0);
-      A0[g] = ok ? ld<T>(has_s ? gm.diag : gm.inv, o) : T(0);
-      AX[g] = ok ? ld<T>(gm.bx, o) : T(0);
-      AY[g] = ok ? ld<T>(gm.by, o) : T(0);
-      AZ[g] = (DIM == 3 && ok) ? ld<T>(gm.bz, o) : T(0);
-      AW[g] = ok ? ld<T>(gm.aw, o) : T(0);
-      if (ok && !has_s) {  // premultiply by 1 / (1 + D)
-        AX[g] *= A0[g];
-        AY[g] *= A0[g];
-        AZ[g] *= A0[g];
+      const double a0 = ok ? (double)ld<T>(HAS_S ? gm.diag : gm.inv, o) : 0.0;
+      double ax = ok ? (double)ld<T>(gm.bx, o) : 0.0;
+      double ay = ok ? (double)ld<T>(gm.by, o) : 0.0;
+      double az = (DIM == 3 && ok) ? (double)ld<T>(gm.bz, o) : 0.0;
+      if (!HAS_S) {
+        ax *= a0;
+        ay *= a0;
+        az *= a0;
       }
+      A0[g] = (T)a0;
+      AX[g] = (T)ax;
+      AY[g] = (T)ay;
+      AZ[g] = (T)az;
+      AW[g] = ok ? ld<T>(gm.aw, o) : T(0);
+      JX[g] = (T)(ax * (double)sx * dT);
+      if (ok) kx_sum += (double)sx * (double)ld<T>(gm.kxa, o);
     }
-    double kx_sum = 0.0;  // sum_g K_gx (signed), for the jump part of the hot-face flux
-#pragma unroll
-    for (int g = 0; g < G; ++g)
-      if (g < cnt) kx_sum += (double)sx * (double)ld<T>(gm.kxa, o0 + g);
 
     // row values carried from the previous iteration
     T v[RMAX][G];
@@ -164,15 +256,14 @@ __global__ void __launch_bounds__(DIM == 3 ? 512 : 256) sweep_kernel(const Sweep
 
     double phi = 0.0;
     const uint8_t in_x_bit = sx > 0 ? CODE_WALL_XM : CODE_WALL_XP;
-    const uint8_t out_x_bit = sx > 0 ? CODE_WALL_XP : CODE_WALL_XM;
     const uint8_t in_y_bit = sy > 0 ? CODE_WALL_YM : CODE_WALL_YP;
-    const uint8_t out_y_bit = sy > 0 ? CODE_WALL_YP : CODE_WALL_YM;
     const uint8_t in_z_bit = sz > 0 ? CODE_WALL_ZM : CODE_WALL_ZP;
-    const uint8_t out_z_bit = sz > 0 ? CODE_WALL_ZP : CODE_WALL_ZM;
-    const int in_x_side = sx > 0 ? 0 : 1, out_x_side = 1 - in_x_side;
-    const int in_y_side = sy > 0 ? 2 : 3, out_y_side = 5 - in_y_side;
-    const int in_z_side = sz > 0 ? 4 : 5, out_z_side = 9 - in_z_side;
-    const T* srcv = reinterpret_cast<const T*>(gm.src);
+    const uint8_t out_wall_bits = (uint8_t)((sx > 0 ? CODE_WALL_XP : CODE_WALL_XM) |
+                                            (sy > 0 ? CODE_WALL_YP : CODE_WALL_YM) |
+                                            (DIM == 3 ? (sz > 0 ? CODE_WALL_ZP : CODE_WALL_ZM) : 0));
+    const int in_x_side = sx > 0 ? 0 : 1;
+    const int in_y_side = sy > 0 ? 2 : 3;
+    const int in_z_side = sz > 0 ? 4 : 5;
 
     for (int d = 0; d < nx; ++d) {
       const int cur = d & 1, prv = cur ^ 1;
@@ -183,117 +274,64 @@ __global__ void __launch_bounds__(DIM == 3 ? 512 : 256) sweep_kernel(const Sweep
       for (int rr = 0; rr < RMAX; ++rr) {
         const int r = RMAX - 1 - rr;
         if (r < nr) {
-        const int jp = j0 + r;
-        const int ip = pmod(d - jp - (DIM == 3 ? kp : 0), nx);
-        const int x = sx > 0 ? ip : nx - 1 - ip;
-        const int y = sy > 0 ? jp : ny - 1 - jp;
-        const int z = (DIM == 3) ? (sz > 0 ? kp : nz - 1 - kp) : 0;
-        const int cell = x + nx * (y + ny * z);
-        const uint8_t code = __ldg(gm.code + cell);
-        if (code & CODE_SOLID) {
-        const T src = srcv[cell];
-        const bool wx = code & in_x_bit, wy = code & in_y_bit;
-        const bool wz = (DIM == 3) && (code & in_z_bit);
-        const T uxw = wx ? (T)gm.Tw[gm.wall_id[cell * 6 + in_x_side]] : T(0);
-        const T uyw = wy ? (T)gm.Tw[gm.wall_id[cell * 6 + in_y_side]] : T(0);
-        const T uzw = wz ? (T)gm.Tw[gm.wall_id[cell * 6 + in_z_side]] : T(0);
-        const bool jump = (ip == 0) && !wx;
-        const double jdt = (double)sx * dT;
-        const T sv = has_s ? (T)__ldg(gm.s + cell) : T(1);
-        T tl = T(0);
+          const int jp = j0 + r;
+          const int ip = pmod(d + d0 - jp - (DIM == 3 ? kp : 0), nx);
+          const int x = sx > 0 ? ip : nx - 1 - ip;
+          const int y = sy > 0 ? jp : ny - 1 - jp;
+          const int z = (DIM == 3) ? (sz > 0 ? kp : nz - 1 - kp) : 0;
+          const int cell = x + nx * (y + ny * z);
+          const uint8_t code = __ldg(codev + cell);
+          if (code & CODE_SOLID) {
+            const T src = srcv[cell];
+            // a wall upstream in x replaces the row's carried value
+            if (code & in_x_bit) {
+              const T w = (T)Twv[widv[cell * 6 + in_x_side]];
 #pragma unroll
-        for (int g = 0; g < G; ++g) {
-          const T ux = wx ? uxw : v[r][g];
-          T uy;
-          if (wy) uy = uyw;
-          else if (r > 0) uy = v[r > 0 ? r - 1 : 0][g];
-          else uy = dn0[g];
-          T base;
-          if (!has_s) {
-            base = jump ? (T)((double)src * (double)A0[g] + (double)AX[g] * jdt) : src * A0[g];
-          } else {
-            base = jump ? (T)((double)src + (double)AX[g] * jdt) : src;
-          }
-          T acc = fma(AX[g], ux, fma(AY[g], uy, base));
-          if (DIM == 3) {
-            const T uz = wz ? uzw : ((tz >= 0) ? xall[((prv * nthr + tz) * RMAX + r) * G + g] : T(0));
-            acc = fma(AZ[g], uz, acc);
-          }
-          const T val = has_s ? acc / (sv + A0[g]) : acc;
-          v[r][g] = val;
-          tl = fma(AW[g], val, tl);
-        }
-        atomicAdd(gm.TL_acc + cell, (double)tl);
-
-        // walls the group's ordinates leave into
-        if (code & out_x_bit) {
-          T s = T(0);
-#pragma unroll
-          for (int g = 0; g < G; ++g)
-            if (g < cnt) s = fma(ld<T>(gm.kxa, o0 + g), v[r][g], s);
-          atomicAdd(gm.wall_acc + gm.wall_id[cell * 6 + out_x_side], (double)s);
-        }
-        if (code & out_y_bit) {
-          T s = T(0);
-#pragma unroll
-          for (int g = 0; g < G; ++g)
-            if (g < cnt) s = fma(ld<T>(gm.kya, o0 + g), v[r][g], s);
-          atomicAdd(gm.wall_acc + gm.wall_id[cell * 6 + out_y_side], (double)s);
-        }
-        if (DIM == 3 && (code & out_z_bit)) {
-          T s = T(0);
-#pragma unroll
-          for (int g = 0; g < G; ++g)
-            if (g < cnt) s = fma(ld<T>(gm.kza, o0 + g), v[r][g], s);
-          atomicAdd(gm.wall_acc + gm.wall_id[cell * 6 + out_z_side], (double)s);
-        }
-        // hot-contact face: the x = 0 plane is the out-of-cell x face of i' = nx-1
-        const bool hot = (ip == nx - 1) && !(code & out_x_bit);
-        if (hot) {
-          T s = T(0);
-#pragma unroll
-          for (int g = 0; g < G; ++g)
-            if (g < cnt) s = fma(ld<T>(gm.kxa, o0 + g), v[r][g], s);
-          phi += (double)sx * (double)s + (sx > 0 ? dT * kx_sum : 0.0);
-        }
-        if (flux) {
-          T jx = T(0), jy = T(0), jz = T(0);
-#pragma unroll
-          for (int g = 0; g < G; ++g) {
-            if (g < cnt) {
-              jx = fma(ld<T>(gm.kxa, o0 + g), v[r][g], jx);
-              jy = fma(ld<T>(gm.kya, o0 + g), v[r][g], jy);
-              if (DIM == 3) jz = fma(ld<T>(gm.kza, o0 + g), v[r][g], jz);
+              for (int g = 0; g < G; ++g) v[r][g] = w;
             }
-          }
-          atomicAdd(gm.J_acc + 3 * cell + 0, (double)sx * (double)jx);
-          atomicAdd(gm.J_acc + 3 * cell + 1, (double)sy * (double)jy);
-          if (DIM == 3) atomicAdd(gm.J_acc + 3 * cell + 2, (double)sz * (double)jz);
-          if (!(code & out_x_bit)) {
-            const int sec = sx > 0 ? (x + 1) % nx : x;
-            const bool jmp = sx > 0 && x == nx - 1;
-            atomicAdd(gm.phi_sec + sec, (double)sx * (double)jx + (jmp ? dT * kx_sum : 0.0));
-          }
-          if (hot) {
+            const bool wy = code & in_y_bit;
+            const T uyw = wy ? (T)Twv[widv[cell * 6 + in_y_side]] : T(0);
+            bool wz = false;
+            T uzw = T(0);
+            if (DIM == 3) {
+              wz = code & in_z_bit;
+              if (wz) uzw = (T)Twv[widv[cell * 6 + in_z_side]];
+            }
+            const bool jump = (ip == 0) && !(code & in_x_bit);
+            T sval = T(1);
+            if (HAS_S) sval = (T)__ldg(sv_ptr + cell);
+            T tl = T(0);
 #pragma unroll
             for (int g = 0; g < G; ++g) {
-              if (g < cnt) {
-                const double k = (double)sx * (double)ld<T>(gm.kxa, o0 + g);
-                atomicAdd(gm.phi_bin + gm.mbin[o0 + g], k * ((double)v[r][g] + (sx > 0 ? dT : 0.0)));
+              const T uy = wy ? uyw : (r > 0 ? v[r > 0 ? r - 1 : 0][g] : dn0[g]);
+              const T jx = jump ? JX[g] : T(0);
+              T acc;
+              if (HAS_S) acc = fma(AY[g], uy, src + jx);
+              else acc = fma(AY[g], uy, fma(src, A0[g], jx));
+              acc = fma(AX[g], v[r][g], acc);
+              if (DIM == 3) {
+                const T uz = wz ? uzw : ((tz >= 0) ? xall[((prv * nthr + tz) * RMAX + r) * G + g] : T(0));
+                acc = fma(AZ[g], uz, acc);
               }
+              T val;
+              if (HAS_S) {
+                if (sizeof(T) == 4) val = (T)__fdividef((float)acc, (float)(sval + A0[g]));
+                else val = acc / (sval + A0[g]);
+              } else {
+                val = acc;
+              }
+              v[r][g] = val;
+              tl = fma(AW[g], val, tl);
+            }
+            atomicAdd(TLacc + cell, widen(tl));
+            if ((code & out_wall_bits) || ip == nx - 1 || rare_pass) {
+#pragma unroll
+              for (int g = 0; g < G; ++g) scratch[t * G + g] = v[r][g];
+              phi += cell_epilogue<T, DIM, G>(gm, scratch + t * G, cell, code, x, ip, o0, cnt, sx,
+                                              sy, sz, flags, kx_sum);
             }
           }
         }
-        if (record) {
-          T* rec = reinterpret_cast<T*>(gm.rec);
-#pragma unroll
-          for (int g = 0; g < G; ++g) {
-            const int sl = (g < cnt) ? __ldg(gm.rec_slot + o0 + g) : -1;
-            if (sl >= 0) rec[(size_t)sl * gm.n_cells + cell] = v[r][g];
-          }
-        }
-        }  // solid
-        }  // r < nr
       }
       // publish this step's values
       if (nr > 0) {
@@ -302,9 +340,8 @@ __global__ void __launch_bounds__(DIM == 3 ? 512 : 256) sweep_kernel(const Sweep
         if (DIM == 3) {
 #pragma unroll
           for (int r = 0; r < RMAX; ++r)
-            if (r < nr)
 #pragma unroll
-              for (int g = 0; g < G; ++g) xall[((cur * nthr + t) * RMAX + r) * G + g] = v[r][g];
+            for (int g = 0; g < G; ++g) xall[((cur * nthr + t) * RMAX + r) * G + g] = v[r][g];
         }
       }
       __syncthreads();

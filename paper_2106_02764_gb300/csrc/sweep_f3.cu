@@ -1,0 +1,5 @@
+// Sweep kernel variants: list OBTE_SWEEP_F3 of sweep_variants.h.
+#include "sweep.cuh"
+#include "sweep_variants.h"
+
+OBTE_SWEEP_F3(OBTE_SWEEP_DEFINE)
