@@ -88,6 +88,8 @@ typedef struct {
   int use_graph;        /* 1: capture check_every iterations in a CUDA graph   */
   int profile;          /* 1: time every sweep / finalize launch with CUDA
                            events recorded on the solve stream (stats below)   */
+  int kernel;           /* 0: automatic, 1: block kernel (every dimension),
+                           2: 2D warp-per-group kernel                          */
 } obte_solve_opts;
 
 #define OBTE_MAX_HISTORY 4096
@@ -103,6 +105,7 @@ typedef struct {
   double time_total_ms;       /* device time of obte_solve                        */
   double updates_per_s;       /* N_solid * N_ordinates * iterations / time_iter   */
   int group_size, rows_per_thread, threads_per_block, n_groups;
+  int kernel;                 /* 1: block kernel, 2: 2D warp-per-group kernel       */
   int n_sweeps;               /* sweep launches timed when opts.profile = 1       */
   double time_sweep_ms;       /* summed device time of those sweep launches       */
   double time_finalize_ms;    /* summed device time of the finalize launches      */

@@ -45,6 +45,7 @@ struct obte_ctx {
   uint8_t* code_d = nullptr;
   int* wall_id_d = nullptr;
   int* wall_cell_d = nullptr;
+  int* wall_side_d = nullptr;
   double* s_d = nullptr;
   bool has_s = false;
 
@@ -69,6 +70,7 @@ struct obte_ctx {
   double* TL = nullptr;
   double* TL_acc = nullptr;
   void* src = nullptr;
+  void* twc = nullptr;
   double* Tw = nullptr;
   double* wall_acc = nullptr;
   void* front = nullptr;
@@ -83,6 +85,7 @@ struct obte_ctx {
   double* phi_bin = nullptr;
   bool flux_done = false;
   int G = 0, R = 0, threads = 0;
+  bool warp = false;
   std::vector<WorkItem> items_h;
   WorkItem* items_d = nullptr;
   double kappa = NAN;
@@ -127,6 +130,8 @@ struct obte_ctx {
     code_d = nullptr;
     wall_id_d = nullptr;
     wall_cell_d = nullptr;
+    wall_side_d = nullptr;
+    twc = nullptr;
     s_d = nullptr;
     wall_den_d = nullptr;
     for (auto& a : tab_d)
@@ -345,15 +350,20 @@ extern "C" int obte_create_mesh(obte_ctx* ctx, int dim, int nx, int ny, int nz, 
   ctx->code_d = ctx->dalloc_t<uint8_t>(ctx->n_cells);
   ctx->wall_id_d = ctx->dalloc_t<int>((size_t)ctx->n_cells * 6);
   ctx->wall_cell_d = ctx->dalloc_t<int>(std::max(1, ctx->n_walls));
+  ctx->wall_side_d = ctx->dalloc_t<int>(std::max(1, ctx->n_walls));
+  NEED(ctx->wall_side_d);
   NEED(ctx->code_d);
   NEED(ctx->wall_id_d);
   NEED(ctx->wall_cell_d);
   CK(cudaMemcpyAsync(ctx->code_d, ctx->code_h.data(), ctx->n_cells, cudaMemcpyHostToDevice, ctx->stream));
   CK(cudaMemcpyAsync(ctx->wall_id_d, ctx->wall_id_h.data(), sizeof(int) * ctx->n_cells * 6,
                      cudaMemcpyHostToDevice, ctx->stream));
-  if (ctx->n_walls)
+  if (ctx->n_walls) {
     CK(cudaMemcpyAsync(ctx->wall_cell_d, ctx->wall_cell_h.data(), sizeof(int) * ctx->n_walls,
                        cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaMemcpyAsync(ctx->wall_side_d, ctx->wall_side_h.data(), sizeof(int) * ctx->n_walls,
+                       cudaMemcpyHostToDevice, ctx->stream));
+  }
   CK(cudaStreamSynchronize(ctx->stream));
   ctx->has_s = false;
   ctx->s_d = nullptr;
@@ -382,7 +392,7 @@ extern "C" int obte_set_scattering_scale(obte_ctx* ctx, const double* s) {
       if (!std::isfinite(v)) return ctx->fail(OBTE_ENONFINITE, "scattering scale is not finite");
       if (!(v > 0)) return ctx->fail(OBTE_EINVAL, "scattering scale must be positive");
     }
-    sk[c] = v;
+    sk[c] = (ctx->code_h[c] & CODE_SOLID) ? v : 1.0;  // pores: never used, kept finite
   }
   if (!ctx->s_d) ctx->s_d = ctx->dalloc_t<double>(ctx->n_cells);
   NEED(ctx->s_d);
@@ -577,12 +587,19 @@ namespace {
 
 struct Variant {
   int G, R;
+  bool warp;  // 2D warp-per-group kernel (sweep2d.cuh) instead of the block kernel
 };
 
-const Variant kVariants2D_F[] = {{16, 4}, {8, 4}, {8, 8}, {16, 2}, {8, 2}, {4, 4}, {16, 1}};
-const Variant kVariants2D_D[] = {{8, 2}, {8, 4}, {4, 4}, {4, 8}, {8, 1}};
-const Variant kVariants3D_F[] = {{8, 4}, {4, 4}, {8, 8}, {4, 8}, {8, 2}, {4, 2}};
-const Variant kVariants3D_D[] = {{4, 4}, {4, 8}, {4, 2}, {8, 2}};
+const Variant kWarp2D_F[] = {{8, 8, true}, {8, 4, true}, {16, 4, true},
+                             {16, 2, true}, {16, 1, true}, {8, 1, true}};
+const Variant kWarp2D_D[] = {{4, 8, true}, {8, 4, true}, {8, 2, true}, {8, 1, true}};
+const Variant kVariants2D_F[] = {{16, 4, false}, {8, 4, false}, {8, 8, false}, {16, 2, false},
+                                 {8, 2, false}, {4, 4, false}, {16, 1, false}};
+const Variant kVariants2D_D[] = {{8, 2, false}, {8, 4, false}, {4, 4, false}, {4, 8, false},
+                                 {8, 1, false}};
+const Variant kVariants3D_F[] = {{8, 8, false}, {4, 8, false}, {8, 4, false}, {4, 4, false},
+                                 {8, 2, false}, {4, 2, false}};
+const Variant kVariants3D_D[] = {{4, 8, false}, {4, 4, false}, {4, 2, false}, {8, 2, false}};
 
 int threads_for(int ny, int nz, int R) {
   const int tpp = (ny + R - 1) / R;
@@ -590,24 +607,37 @@ int threads_for(int ny, int nz, int R) {
   return ((t + 31) / 32) * 32;
 }
 
+template <size_t N>
+void push_fitting(std::vector<Variant>& out, const Variant (&v)[N], int precision, int dim, int ny,
+                  int nz, bool has_s) {
+  for (size_t i = 0; i < N; ++i) {
+    if (ny % v[i].R != 0) continue;
+    if (v[i].warp) {
+      if (dim != 2 || ny / v[i].R > 32) continue;
+      if (!sweep2d_warp_exists(precision, v[i].G, v[i].R, has_s, true)) continue;
+    } else {
+      const int thr = threads_for(ny, nz, v[i].R);
+      if (thr > ((dim == 3 && v[i].R < 8) ? 512 : 256)) continue;  // the kernel's launch bound
+      if (sweep_smem_bytes(precision, dim, v[i].G, v[i].R, thr) > 200 * 1024) continue;
+      if (!sweep_variant_exists(precision, dim, v[i].G, v[i].R, has_s)) continue;
+    }
+    out.push_back(v[i]);
+  }
+}
+
 std::vector<Variant> candidates(int precision, int dim, int ny, int nz, bool has_s) {
   std::vector<Variant> out;
-  const Variant* v;
-  int n;
   if (dim == 2) {
-    v = precision ? kVariants2D_F : kVariants2D_D;
-    n = precision ? (int)(sizeof(kVariants2D_F) / sizeof(Variant)) : (int)(sizeof(kVariants2D_D) / sizeof(Variant));
+    if (precision) {
+      push_fitting(out, kWarp2D_F, precision, dim, ny, nz, has_s);
+      push_fitting(out, kVariants2D_F, precision, dim, ny, nz, has_s);
+    } else {
+      push_fitting(out, kWarp2D_D, precision, dim, ny, nz, has_s);
+      push_fitting(out, kVariants2D_D, precision, dim, ny, nz, has_s);
+    }
   } else {
-    v = precision ? kVariants3D_F : kVariants3D_D;
-    n = precision ? (int)(sizeof(kVariants3D_F) / sizeof(Variant)) : (int)(sizeof(kVariants3D_D) / sizeof(Variant));
-  }
-  for (int i = 0; i < n; ++i) {
-    if (ny % v[i].R != 0) continue;
-    const int thr = threads_for(ny, nz, v[i].R);
-    if (thr > ((dim == 3 && v[i].R < 8) ? 512 : 256)) continue;  // the kernel's launch bound
-    if (sweep_smem_bytes(precision, dim, v[i].G, v[i].R, thr) > 200 * 1024) continue;
-    if (!sweep_variant_exists(precision, dim, v[i].G, v[i].R, has_s)) continue;
-    out.push_back(v[i]);
+    if (precision) push_fitting(out, kVariants3D_F, precision, dim, ny, nz, has_s);
+    else push_fitting(out, kVariants3D_D, precision, dim, ny, nz, has_s);
   }
   return out;
 }
@@ -645,7 +675,7 @@ static void build_items(obte_ctx* ctx, int geom, int G, std::vector<WorkItem>& i
 }
 
 // allocate the iteration state for a precision / variant; fill gh and gd
-static int prepare_state(obte_ctx* ctx, int precision, int G, int R, int max_iter,
+static int prepare_state(obte_ctx* ctx, int precision, int G, int R, bool warp, int max_iter,
                          const obte_solve_opts& op) {
   cudaSetDevice(ctx->device);
   const int Nx = ctx->n[0], Ny = ctx->n[1], Nz = ctx->n[2];
@@ -653,7 +683,7 @@ static int prepare_state(obte_ctx* ctx, int precision, int G, int R, int max_ite
   if (ctx->precision != precision) {
     ctx->drop_graph();
     // (re)allocate everything that depends on the precision
-    for (void* p : {(void*)ctx->TL, (void*)ctx->TL_acc, ctx->src, (void*)ctx->Tw, (void*)ctx->wall_acc,
+    for (void* p : {(void*)ctx->TL, (void*)ctx->TL_acc, ctx->src, ctx->twc, (void*)ctx->Tw, (void*)ctx->wall_acc,
                     ctx->front, (void*)ctx->scal, (void*)ctx->ctrl, (void*)ctx->hist, (void*)ctx->TF,
                     (void*)ctx->fwork, (void*)ctx->fiters, (void*)ctx->gd})
       ctx->dfree(p);
@@ -661,6 +691,8 @@ static int prepare_state(obte_ctx* ctx, int precision, int G, int R, int max_ite
     ctx->TL = ctx->dalloc_t<double>(ctx->n_cells);
     ctx->TL_acc = ctx->dalloc_t<double>(ctx->n_cells);
     ctx->src = ctx->dalloc(e * ctx->n_cells);
+    ctx->twc = ctx->dalloc(e * (size_t)ctx->n_cells * 6);
+    NEED(ctx->twc);
     ctx->Tw = ctx->dalloc_t<double>(std::max(1, ctx->n_walls));
     ctx->wall_acc = ctx->dalloc_t<double>(std::max(1, ctx->n_walls));
     ctx->front = ctx->dalloc(e * (size_t)ctx->O * rows);
@@ -712,6 +744,8 @@ static int prepare_state(obte_ctx* ctx, int precision, int G, int R, int max_ite
   g.wall_acc = ctx->wall_acc;
   g.wall_den = ctx->wall_den_d;
   g.wall_cell = ctx->wall_cell_d;
+  g.wall_side = ctx->wall_side_d;
+  g.twc = ctx->twc;
   g.front = ctx->front;
   g.phi_acc = ctx->scal;
   g.delta_max = ctx->scal + 1;
@@ -744,7 +778,8 @@ static int prepare_state(obte_ctx* ctx, int precision, int G, int R, int max_ite
   g.max_iter = max_iter;
   ctx->G = G;
   ctx->R = R;
-  ctx->threads = threads_for(Ny, Nz, R);
+  ctx->warp = warp;
+  ctx->threads = warp ? 32 * kWarpsPerBlock : threads_for(Ny, Nz, R);
   std::vector<WorkItem> items;
   std::vector<int> ord_d0;
   build_items(ctx, 0, G, items, &ord_d0);
@@ -775,6 +810,9 @@ static cudaError_t sweep_once(obte_ctx* ctx, int flags) {
   L.n_items = (int)ctx->items_h.size();
   L.flags = flags;
   L.item_counter = nullptr;
+  if (ctx->warp)
+    return launch_sweep2d_warp(L, ctx->precision, ctx->G, ctx->R, ctx->has_s, true,
+                               (L.n_items + kWarpsPerBlock - 1) / kWarpsPerBlock, ctx->stream);
   const size_t smem = sweep_smem_bytes(ctx->precision, ctx->dim, ctx->G, ctx->R, ctx->threads);
   return launch_sweep(L, ctx->precision, ctx->dim, ctx->G, ctx->R, ctx->has_s, ctx->threads,
                       L.n_items, smem, ctx->stream);
@@ -798,37 +836,42 @@ static int init_from_fourier(obte_ctx* ctx, const obte_solve_opts& op, int* fite
   return OBTE_OK;
 }
 
-static int pick_variant(obte_ctx* ctx, int precision, const obte_solve_opts& op, Variant* out) {
-  const int Ny = ctx->n[1], Nz = ctx->n[2];
-  auto cands = candidates(precision, ctx->dim, Ny, Nz, ctx->has_s);
-  if (op.group_size > 0 || op.rows_per_thread > 0) {
-    for (auto& c : candidates(precision, ctx->dim, Ny, Nz, ctx->has_s))
-      if ((op.group_size <= 0 || c.G == op.group_size) && (op.rows_per_thread <= 0 || c.R == op.rows_per_thread)) {
-        *out = c;
-        return OBTE_OK;
-      }
-    return ctx->fail(OBTE_EINVAL, "no compiled sweep variant matches group_size / rows_per_thread for this mesh");
+static std::vector<Variant> filtered_candidates(obte_ctx* ctx, int precision,
+                                                const obte_solve_opts& op) {
+  std::vector<Variant> out;
+  for (auto& c : candidates(precision, ctx->dim, ctx->n[1], ctx->n[2], ctx->has_s)) {
+    if (op.kernel == 1 && c.warp) continue;
+    if (op.kernel == 2 && !c.warp) continue;
+    if (op.group_size > 0 && c.G != op.group_size) continue;
+    if (op.rows_per_thread > 0 && c.R != op.rows_per_thread) continue;
+    out.push_back(c);
   }
-  if (cands.empty()) return ctx->fail(OBTE_EINVAL, "no compiled sweep variant fits this mesh (rows per plane too many?)");
-  auto key = std::make_tuple(precision * 2 + (ctx->has_s ? 1 : 0), ctx->dim, ctx->n[0], Ny, Nz, ctx->O);
+  return out;
+}
+
+static int pick_variant(obte_ctx* ctx, int precision, const obte_solve_opts& op, Variant* out) {
+  auto cands = filtered_candidates(ctx, precision, op);
+  if (cands.empty())
+    return ctx->fail(OBTE_EINVAL, "no compiled sweep variant matches kernel / group_size / "
+                                  "rows_per_thread for this mesh");
+  auto key = std::make_tuple(precision * 2 + (ctx->has_s ? 1 : 0), ctx->dim, ctx->n[0], ctx->n[1],
+                             ctx->n[2], ctx->O);
   auto it = tune_cache().find(key);
-  if (it != tune_cache().end()) {
+  if (op.group_size == 0 && op.rows_per_thread == 0 && op.kernel == 0 && it != tune_cache().end()) {
     *out = it->second;
     return OBTE_OK;
   }
-  if (cands.size() == 1 || op.group_size == 0) {
-    // heuristic default: the first candidate that gives at least one block per SM
-    int sms = 148;
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ctx->device);
-    *out = cands[0];
-    for (auto& c : cands) {
-      const long blocks = (ctx->O + c.G - 1) / c.G;
-      if (blocks >= sms) {
-        *out = c;
-        break;
-      }
+  // default: the first listed candidate that gives every SM at least one warp
+  // of work; the lists are ordered by measured preference
+  int sms = 148;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ctx->device);
+  *out = cands[0];
+  for (auto& c : cands) {
+    const long units = (ctx->O + c.G - 1) / c.G;
+    if (units >= sms) {
+      *out = c;
+      break;
     }
-    return OBTE_OK;
   }
   return OBTE_OK;
 }
@@ -836,7 +879,7 @@ static int pick_variant(obte_ctx* ctx, int precision, const obte_solve_opts& op,
 // timed autotune over the compiled variants (group_size = -1)
 static int autotune(obte_ctx* ctx, int precision, const obte_solve_opts& op, Variant* out) {
   auto key = std::make_tuple(precision * 2 + (ctx->has_s ? 1 : 0), ctx->dim, ctx->n[0], ctx->n[1], ctx->n[2], ctx->O);
-  auto cands = candidates(precision, ctx->dim, ctx->n[1], ctx->n[2], ctx->has_s);
+  auto cands = filtered_candidates(ctx, precision, op);
   if (cands.empty()) return ctx->fail(OBTE_EINVAL, "no compiled sweep variant fits this mesh");
   cudaEvent_t a, b;
   CK(cudaEventCreate(&a));
@@ -844,7 +887,7 @@ static int autotune(obte_ctx* ctx, int precision, const obte_solve_opts& op, Var
   float best = 1e30f;
   Variant bv = cands[0];
   for (auto& c : cands) {
-    int rc = prepare_state(ctx, precision, c.G, c.R, 1 << 30, op);
+    int rc = prepare_state(ctx, precision, c.G, c.R, c.warp, 1 << 30, op);
     if (rc) return rc;
     obte_solve_opts o2 = op;
     o2.fourier_max_iter = 1;
@@ -985,7 +1028,7 @@ extern "C" int obte_solve(obte_ctx* ctx, const obte_solve_opts* opts, obte_solve
   Variant v;
   int rc = (op.group_size < 0) ? autotune(ctx, prec, op, &v) : pick_variant(ctx, prec, op, &v);
   if (rc) return rc;
-  rc = prepare_state(ctx, prec, v.G, v.R, op.max_iter, op);
+  rc = prepare_state(ctx, prec, v.G, v.R, v.warp, op.max_iter, op);
   if (rc) return rc;
   ctx->flux_done = false;
   cudaEvent_t e0, e1, e2;
@@ -1039,6 +1082,7 @@ extern "C" int obte_solve(obte_ctx* ctx, const obte_solve_opts* opts, obte_solve
     stats->group_size = ctx->G;
     stats->rows_per_thread = ctx->R;
     stats->threads_per_block = ctx->threads;
+    stats->kernel = ctx->warp ? 2 : 1;
     stats->n_groups = (int)ctx->items_h.size();
     stats->n_history = (int)hist.size();
     for (size_t i = 0; i < hist.size(); ++i) stats->kappa_history[i] = hist[i];
@@ -1261,9 +1305,14 @@ extern "C" int obte_kappa_grad_s(obte_ctx* ctx, double* out, size_t max_field_by
     L.n_items = (int)its.size();
     L.flags = SWEEP_RECORD;
     L.item_counter = nullptr;
-    const size_t smem = sweep_smem_bytes(ctx->precision, ctx->dim, ctx->G, ctx->R, ctx->threads);
-    CK(launch_sweep(L, ctx->precision, ctx->dim, ctx->G, ctx->R, ctx->has_s, ctx->threads, L.n_items,
-                    smem, ctx->stream));
+    if (ctx->warp) {
+      CK(launch_sweep2d_warp(L, ctx->precision, ctx->G, ctx->R, ctx->has_s, true,
+                             (L.n_items + kWarpsPerBlock - 1) / kWarpsPerBlock, ctx->stream));
+    } else {
+      const size_t smem = sweep_smem_bytes(ctx->precision, ctx->dim, ctx->G, ctx->R, ctx->threads);
+      CK(launch_sweep(L, ctx->precision, ctx->dim, ctx->G, ctx->R, ctx->has_s, ctx->threads,
+                      L.n_items, smem, ctx->stream));
+    }
     CK(launch_grad_contract2(ctx->code_d, ctx->TL, ctx->n_cells, rec, (int)b.size(), revl_d, a_d,
                              jscale, grad_d, ctx->precision, ctx->stream));
     CK(cudaMemsetAsync(ctx->TL_acc, 0, sizeof(double) * ctx->n_cells, ctx->stream));
@@ -1303,46 +1352,52 @@ extern "C" int obte_solve_batch(obte_ctx* const* ctxs, int n, const obte_solve_o
   if (op.max_iter < 1) return ctx->fail(OBTE_EINVAL, "max_iter must be >= 1");
   const int prec = op.precision == OBTE_FP64 ? 0 : 1;
   cudaSetDevice(ctx->device);
-  // a variant every geometry accepts; the block covers the largest geometry
-  std::vector<Variant> common;
+  // 2D: the warp kernel with per-geometry rows per lane (R <= 8 dividing ny,
+  // ny / R <= 32 lanes); otherwise a block-kernel variant every geometry accepts
+  bool any_s = false;
+  for (int i = 0; i < n; ++i) any_s = any_s || ctxs[i]->has_s;
   int max_ny = 0, max_nz = 0;
   for (int i = 0; i < n; ++i) {
     max_ny = std::max(max_ny, ctxs[i]->n[1]);
     max_nz = std::max(max_nz, ctxs[i]->n[2]);
   }
-  bool any_s = false;
-  for (int i = 0; i < n; ++i) any_s = any_s || ctxs[i]->has_s;
-  for (auto& c : candidates(prec, ctx->dim, max_ny, max_nz, any_s)) {
-    bool ok = true;
-    for (int i = 0; i < n; ++i)
-      if (ctxs[i]->n[1] % c.R != 0) ok = false;
-    if ((op.group_size > 0 && c.G != op.group_size) || (op.rows_per_thread > 0 && c.R != op.rows_per_thread))
-      ok = false;
-    if (ok) common.push_back(c);
-  }
-  if (common.empty()) return ctx->fail(OBTE_EINVAL, "no compiled sweep variant fits every geometry");
-  Variant v = common[0];
-  if (op.group_size == 0 && op.rows_per_thread == 0) {
-    // prefer the variant whose rows per thread keep the largest mesh at <= 256 threads
-    // with the fewest idle threads on small meshes
-    long best = -1;
-    for (auto& c : common) {
-      long busy = 0;
-      const int thr = threads_for(max_ny, max_nz, c.R);
-      for (int i = 0; i < n; ++i) busy += (long)threads_for(ctxs[i]->n[1], ctxs[i]->n[2], c.R) * 1000 / thr;
-      if (busy > best) {
-        best = busy;
-        v = c;
+  const int wG = prec ? 8 : 4, wR = 8;
+  std::vector<int> r_eff(n, 0);
+  bool use_warp = ctx->dim == 2 && op.kernel != 1 && sweep2d_warp_exists(prec, wG, wR, any_s, false) &&
+                  (op.group_size <= 0 || op.group_size == wG);
+  for (int i = 0; use_warp && i < n; ++i) {
+    const int ny = ctxs[i]->n[1];
+    for (int R = 1; R <= wR; ++R)
+      if (ny % R == 0 && ny / R <= 32) {
+        r_eff[i] = R;
+        break;
       }
+    if (!r_eff[i]) use_warp = false;
+  }
+  Variant v{0, 0, false};
+  if (!use_warp) {
+    std::vector<Variant> common;
+    for (auto& c : candidates(prec, ctx->dim, max_ny, max_nz, any_s)) {
+      if (c.warp) continue;
+      bool ok = true;
+      for (int i = 0; i < n; ++i)
+        if (ctxs[i]->n[1] % c.R != 0) ok = false;
+      if ((op.group_size > 0 && c.G != op.group_size) || (op.rows_per_thread > 0 && c.R != op.rows_per_thread))
+        ok = false;
+      if (ok) common.push_back(c);
     }
+    if (common.empty()) return ctx->fail(OBTE_EINVAL, "no compiled sweep variant fits every geometry");
+    v = common[0];
+  } else {
+    v = Variant{wG, wR, true};
   }
   for (int i = 0; i < n; ++i) {
-    int rc = prepare_state(ctxs[i], prec, v.G, v.R, op.max_iter, op);
+    int rc = prepare_state(ctxs[i], prec, v.G, use_warp ? r_eff[i] : v.R, v.warp, op.max_iter, op);
     if (rc) return ctx->fail(rc, std::string("batch member: ") + ctxs[i]->err);
     ctxs[i]->flux_done = false;
   }
-  const int threads = threads_for(max_ny, max_nz, v.R);
-  const size_t smem = sweep_smem_bytes(prec, ctx->dim, v.G, v.R, threads);
+  const int threads = v.warp ? 32 * kWarpsPerBlock : threads_for(max_ny, max_nz, v.R);
+  const size_t smem = v.warp ? 0 : sweep_smem_bytes(prec, ctx->dim, v.G, v.R, threads);
   // contiguous geometry table and a work list sorted by cost (largest first)
   GeomDev* gds = ctx->dalloc_t<GeomDev>(n);
   NEED(gds);
@@ -1364,8 +1419,10 @@ extern "C" int obte_solve_batch(obte_ctx* const* ctxs, int n, const obte_solve_o
                      ctx->stream));
   int sms = 148;
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ctx->device);
-  const int per_sm = std::max(1, sweep_blocks_per_sm(prec, ctx->dim, v.G, v.R, any_s, threads, smem));
-  const int blocks = (int)std::min<long>((long)items.size(), (long)sms * per_sm);
+  const int per_sm = v.warp ? 4 : std::max(1, sweep_blocks_per_sm(prec, ctx->dim, v.G, v.R, any_s, threads, smem));
+  const int blocks = v.warp ? (int)std::min<long>(((long)items.size() + kWarpsPerBlock - 1) / kWarpsPerBlock,
+                                                  (long)sms * per_sm)
+                            : (int)std::min<long>((long)items.size(), (long)sms * per_sm);
   int max_cells = 0;
   for (int i = 0; i < n; ++i) max_cells = std::max(max_cells, ctxs[i]->n_cells);
 
@@ -1400,7 +1457,8 @@ extern "C" int obte_solve_batch(obte_ctx* const* ctxs, int n, const obte_solve_o
       L.n_items = (int)items.size();
       L.flags = 0;
       L.item_counter = counter;
-      e = launch_sweep(L, prec, ctx->dim, v.G, v.R, any_s, threads, blocks, smem, ctx->stream);
+      e = v.warp ? launch_sweep2d_warp(L, prec, v.G, v.R, any_s, false, blocks, ctx->stream)
+                 : launch_sweep(L, prec, ctx->dim, v.G, v.R, any_s, threads, blocks, smem, ctx->stream);
       if (e != cudaSuccess) return e;
       e = launch_finalize(gds, n, prec, finalize_blocks(max_cells), ctx->stream);
       if (e != cudaSuccess) return e;
@@ -1487,7 +1545,8 @@ extern "C" int obte_solve_batch(obte_ctx* const* ctxs, int n, const obte_solve_o
       s->time_total_ms = t_f + t_i;
       s->updates_per_s = t_i > 0 ? (double)total_updates / (t_i * 1e-3) : 0.0;
       s->group_size = v.G;
-      s->rows_per_thread = v.R;
+      s->rows_per_thread = c->R;
+      s->kernel = v.warp ? 2 : 1;
       s->threads_per_block = threads;
       s->n_groups = (int)items.size();
       s->n_history = (int)hist.size();

@@ -39,11 +39,13 @@ __global__ void finalize_kernel(const GeomDev* geoms) {
     g.TL[c] = t;
     src[c] = (T)(g.s ? g.s[c] * t : t);
   }
+  T* twc = reinterpret_cast<T*>(g.twc);
   for (int f = blockIdx.x * blockDim.x + threadIdx.x; f < g.n_walls; f += stride) {
     const double w = g.wall_acc[f] / g.wall_den[f];
     g.wall_acc[f] = 0.0;
     if (!isfinite(w)) nonfin = 1;
     g.Tw[f] = w;
+    twc[(size_t)g.wall_cell[f] * 6 + g.wall_side[f]] = (T)w;
   }
   for (int o = 16; o > 0; o >>= 1) dmax = fmax(dmax, __shfl_xor_sync(0xffffffffu, dmax, o));
   if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = dmax;
@@ -103,6 +105,8 @@ __global__ void init_state_kernel(const GeomDev* geoms, int gi, const double* T0
     g.TL_acc[c] = 0.0;
     src[c] = (T)(g.s ? g.s[c] * t : t);
   }
+  T* twc = reinterpret_cast<T*>(g.twc);
+  for (long i = tid; i < (long)g.n_cells * 6; i += stride) twc[i] = T(0);
   for (int f = tid; f < g.n_walls; f += stride) {
     g.Tw[f] = T0[g.wall_cell[f]];
     g.wall_acc[f] = 0.0;
@@ -199,14 +203,28 @@ cudaError_t launch_finalize(const GeomDev* geoms_dev, int n_geoms, int precision
   return cudaGetLastError();
 }
 
+template <typename T>
+__global__ void init_twc_kernel(const GeomDev* geoms, int gi) {
+  const GeomDev& g = geoms[gi];
+  T* twc = reinterpret_cast<T*>(g.twc);
+  for (int f = blockIdx.x * blockDim.x + threadIdx.x; f < g.n_walls; f += gridDim.x * blockDim.x)
+    twc[(size_t)g.wall_cell[f] * 6 + g.wall_side[f]] = (T)g.Tw[f];
+}
+
 cudaError_t launch_init_state_oct(const GeomDev* geoms_dev, const GeomDev& gh, int gi,
                                   const double* T0, int precision, const int* octant_of,
                                   cudaStream_t st) {
-  const long work = std::max((long)gh.n_cells, (long)gh.n_ord * gh.rows);
+  const long work = std::max((long)gh.n_cells * 6, (long)gh.n_ord * gh.rows);
   int blocks = (int)std::min<long>((work + 255) / 256, 4096);
   if (blocks < 1) blocks = 1;
-  if (precision == 0) init_state_kernel<double><<<blocks, 256, 0, st>>>(geoms_dev, gi, T0, octant_of);
-  else init_state_kernel<float><<<blocks, 256, 0, st>>>(geoms_dev, gi, T0, octant_of);
+  const int wb = std::max(1, std::min((gh.n_walls + 255) / 256, 1024));
+  if (precision == 0) {
+    init_state_kernel<double><<<blocks, 256, 0, st>>>(geoms_dev, gi, T0, octant_of);
+    init_twc_kernel<double><<<wb, 256, 0, st>>>(geoms_dev, gi);
+  } else {
+    init_state_kernel<float><<<blocks, 256, 0, st>>>(geoms_dev, gi, T0, octant_of);
+    init_twc_kernel<float><<<wb, 256, 0, st>>>(geoms_dev, gi);
+  }
   return cudaGetLastError();
 }
 

@@ -48,6 +48,8 @@ struct GeomDev {
   double* wall_acc;       // [n_walls]
   const double* wall_den; // [n_walls]
   const int* wall_cell;   // [n_walls]
+  const int* wall_side;   // [n_walls] side of its cell (0..5: -x +x -y +y -z +z)
+  void* twc;              // [n_cells * 6] wall temperature seen through each side, sweep precision
   void* front;            // [n_ord][rows] row values carried between iterations
   double* phi_acc;        // [1] hot-face flux of the running sweep
   // flux pass outputs
@@ -91,7 +93,11 @@ struct SweepLaunch {
   int* item_counter;  // persistent work queue (nullptr: one item per block)
 };
 
-// sweep.cu
+// sweep.cu (generic block kernel) and the 2D warp kernel (sweep_w*.cu)
+cudaError_t launch_sweep2d_warp(const SweepLaunch& L, int precision, int G, int RMAX, bool has_s,
+                                bool rfixed, int blocks, cudaStream_t st);
+bool sweep2d_warp_exists(int precision, int G, int RMAX, bool has_s, bool rfixed);
+constexpr int kWarpsPerBlock = 4;
 cudaError_t launch_sweep(const SweepLaunch& L, int precision, int dim, int G, int RMAX,
                          bool has_s, int threads, int blocks, size_t smem, cudaStream_t st);
 size_t sweep_smem_bytes(int precision, int dim, int G, int RMAX, int threads);

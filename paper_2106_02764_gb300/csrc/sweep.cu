@@ -1,5 +1,6 @@
 // Dispatch to the compiled sweep kernel variants (sweep_variants.h).
 #include "sweep_variants.h"
+#include "sweep2d_variants.h"
 
 static int prec_of(float*) { return 1; }
 static int prec_of(double*) { return 0; }
@@ -42,4 +43,24 @@ int sweep_blocks_per_sm(int precision, int dim, int G, int RMAX, bool has_s, int
   OBTE_SWEEP_VARIANTS(X)
 #undef X
   return n;
+}
+
+#define OBTE_MATCH2D(T, GG, RR, SS, FF) \
+  (precision == prec_of((T*)nullptr) && G == GG && RMAX == RR && has_s == SS && rfixed == FF)
+
+cudaError_t launch_sweep2d_warp(const SweepLaunch& L, int precision, int G, int RMAX, bool has_s,
+                                bool rfixed, int blocks, cudaStream_t st) {
+#define X(T, GG, RR, SS, FF) \
+  if (OBTE_MATCH2D(T, GG, RR, SS, FF)) return OBTE_SWEEP2D_NAME(T, GG, RR, SS, FF)(&L, blocks, st);
+  OBTE_SWEEP2D_VARIANTS(X)
+#undef X
+  return cudaErrorInvalidValue;
+}
+
+bool sweep2d_warp_exists(int precision, int G, int RMAX, bool has_s, bool rfixed) {
+#define X(T, GG, RR, SS, FF) \
+  if (OBTE_MATCH2D(T, GG, RR, SS, FF)) return true;
+  OBTE_SWEEP2D_VARIANTS(X)
+#undef X
+  return false;
 }

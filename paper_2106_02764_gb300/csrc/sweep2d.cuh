@@ -1,0 +1,224 @@
+// 2D upwind transport sweep, one ordinate group per warp (Eq. iter2 of App. A,
+// one source-iteration pass of Algorithm 1) with the moment reductions fused.
+//
+// Same wavefront as the block kernel (sweep.cuh): row j' visits column
+// i'(d) = (d + d0 - j') mod nx at step d, in the frame mirrored per quadrant;
+// the x neighbour is the row's own previous value and the y neighbour the row
+// below's previous value.  Here a whole group lives in one warp: lane l owns
+// R = ny / tpp consecutive rows (tpp <= 32 lanes in use), so the row below a
+// lane's lowest row is the top row of lane l - 1 (lane tpp - 1 for lane 0 when
+// y is periodic) and arrives by a warp shuffle.  No shared-memory exchange, no
+// barrier: warps never wait for one another.
+//
+// The R rows of a lane sit in the top R of RMAX register rows (slots
+// RMAX - R .. RMAX - 1), so the lane's top row is always slot RMAX - 1; with
+// RFIXED the host guarantees R == RMAX.  Cells are updated branch-free (pores
+// too: their values are never read by a solid cell, whose faces towards a pore
+// are walls); the wall temperature seen through a cell side comes from a
+// per-cell array written by the finalisation, and only the moment atomics and
+// the rare epilogue (walls the ordinates leave into, the hot-contact column,
+// flux / record passes) are predicated on the cell being solid.
+#pragma once
+
+#include "sweep.cuh"
+
+namespace obte {
+
+// Rare per-cell epilogue of the warp kernel, in the sweep precision; sums are
+// widened exactly before the FP64 atomics.  Returns the hot-face flux.
+template <typename T, int G>
+__device__ __noinline__ double cell_epilogue_2d(const GeomDev& gm, const T* __restrict__ val,
+                                                int cell, uint8_t code, int x, int ip, int o0,
+                                                int cnt, int sx, int sy, int flags,
+                                                double kx_sum) {
+  const int nx = gm.nx;
+  const double dT = gm.dT;
+  const uint8_t out_x_bit = sx > 0 ? CODE_WALL_XP : CODE_WALL_XM;
+  const uint8_t out_y_bit = sy > 0 ? CODE_WALL_YP : CODE_WALL_YM;
+  T sxk = T(0), syk = T(0);
+  for (int g = 0; g < cnt; ++g) {
+    sxk = fma(ld<T>(gm.kxa, o0 + g), val[g], sxk);
+    syk = fma(ld<T>(gm.kya, o0 + g), val[g], syk);
+  }
+  const double dx = widen(sxk), dy = widen(syk);
+  if (code & out_x_bit) atomicAdd(gm.wall_acc + gm.wall_id[cell * 6 + (sx > 0 ? 1 : 0)], dx);
+  if (code & out_y_bit) atomicAdd(gm.wall_acc + gm.wall_id[cell * 6 + (sy > 0 ? 3 : 2)], dy);
+  const bool hot = (ip == nx - 1) && !(code & out_x_bit);
+  double phi = 0.0;
+  if (hot) phi = (sx > 0 ? dx : -dx) + (sx > 0 ? dT * kx_sum : 0.0);
+  if (flags & SWEEP_FLUX) {
+    atomicAdd(gm.J_acc + 3 * cell + 0, sx > 0 ? dx : -dx);
+    atomicAdd(gm.J_acc + 3 * cell + 1, sy > 0 ? dy : -dy);
+    if (!(code & out_x_bit)) {
+      const int sec = sx > 0 ? (x + 1) % nx : x;
+      const bool jmp = sx > 0 && x == nx - 1;
+      atomicAdd(gm.phi_sec + sec, (sx > 0 ? dx : -dx) + (jmp ? dT * kx_sum : 0.0));
+    }
+    if (hot)
+      for (int g = 0; g < cnt; ++g) {
+        const double k = (double)sx * (double)ld<T>(gm.kxa, o0 + g);
+        atomicAdd(gm.phi_bin + gm.mbin[o0 + g], k * ((double)val[g] + (sx > 0 ? dT : 0.0)));
+      }
+  }
+  if (flags & SWEEP_RECORD) {
+    T* rec = reinterpret_cast<T*>(gm.rec);
+    for (int g = 0; g < cnt; ++g) {
+      const int sl = gm.rec_slot[o0 + g];
+      if (sl >= 0) rec[(size_t)sl * gm.n_cells + cell] = val[g];
+    }
+  }
+  return phi;
+}
+
+template <typename T, int G, int RMAX, bool HAS_S, bool RFIXED>
+__global__ void __launch_bounds__(32 * kWarpsPerBlock, 1) sweep2d_warp_kernel(const SweepLaunch L) {
+  __shared__ __align__(16) T scratch_all[kWarpsPerBlock][32][G];
+  const int lane = threadIdx.x & 31;
+  const int wib = threadIdx.x >> 5;
+  T* scratch = &scratch_all[wib][lane][0];
+  const int flags = L.flags;
+  const bool rare_pass = (flags & (SWEEP_FLUX | SWEEP_RECORD)) != 0;
+  const unsigned FULL = 0xffffffffu;
+
+  int item = blockIdx.x * kWarpsPerBlock + wib;
+  for (;;) {
+    if (L.item_counter) {
+      int it = 0;
+      if (lane == 0) it = atomicAdd(L.item_counter, 1);
+      item = __shfl_sync(FULL, it, 0);
+    }
+    if (item >= L.n_items) return;
+    const WorkItem wi = L.items[item];
+    const GeomDev& gm = L.geoms[wi.geom];
+    if (*(volatile const int*)gm.done) {
+      if (!L.item_counter) return;
+      continue;
+    }
+    const int nx = gm.nx, ny = gm.ny;
+    const int R = RFIXED ? RMAX : gm.R;  // rows per lane, <= RMAX
+    const int rb = RMAX - R;             // first register row in use
+    const int tpp = gm.tpp;              // lanes in use
+    const int sx = (wi.octant & 1) ? -1 : 1;
+    const int sy = (wi.octant & 2) ? -1 : 1;
+    const int o0 = wi.o0, cnt = wi.count, d0 = wi.d0;
+    const double dT = gm.dT;
+    const bool active = lane < tpp;
+    const int j0 = lane * R;
+    const uint8_t* __restrict__ codev = gm.code;
+    const T* __restrict__ srcv = reinterpret_cast<const T*>(gm.src);
+    const T* __restrict__ twcv = reinterpret_cast<const T*>(gm.twc);
+    const double* __restrict__ sv_ptr = gm.s;
+    double* TLacc = gm.TL_acc;
+
+    T A0[G], AX[G], AY[G], AW[G], JX[G];
+    double kx_sum = 0.0;
+#pragma unroll
+    for (int g = 0; g < G; ++g) {
+      const bool ok = g < cnt;
+      const int o = o0 + (ok ? g : 0);
+      const double a0 = ok ? (double)ld<T>(HAS_S ? gm.diag : gm.inv, o) : 0.0;
+      double ax = ok ? (double)ld<T>(gm.bx, o) : 0.0;
+      double ay = ok ? (double)ld<T>(gm.by, o) : 0.0;
+      if (!HAS_S) {
+        ax *= a0;
+        ay *= a0;
+      }
+      A0[g] = (T)a0;
+      AX[g] = (T)ax;
+      AY[g] = (T)ay;
+      AW[g] = ok ? ld<T>(gm.aw, o) : T(0);
+      JX[g] = (T)(ax * (double)sx * dT);
+      if (ok) kx_sum += (double)sx * (double)ld<T>(gm.kxa, o);
+    }
+
+    T v[RMAX][G];
+    const T* front = reinterpret_cast<const T*>(gm.front);
+#pragma unroll
+    for (int r = 0; r < RMAX; ++r)
+#pragma unroll
+      for (int g = 0; g < G; ++g)
+        v[r][g] = (active && r >= rb && g < cnt) ? front[(size_t)(o0 + g) * ny + j0 + (r - rb)] : T(0);
+
+    // lane holding the row below this lane's lowest row
+    const int below = lane > 0 ? lane - 1 : (gm.py ? tpp - 1 : 0);
+    const uint8_t in_x_bit = sx > 0 ? CODE_WALL_XM : CODE_WALL_XP;
+    const uint8_t in_y_bit = sy > 0 ? CODE_WALL_YM : CODE_WALL_YP;
+    const uint8_t out_wall_bits = (uint8_t)((sx > 0 ? CODE_WALL_XP : CODE_WALL_XM) |
+                                            (sy > 0 ? CODE_WALL_YP : CODE_WALL_YM));
+    const int in_x_side = sx > 0 ? 0 : 1;
+    const int in_y_side = sy > 0 ? 2 : 3;
+    double phi = 0.0;
+
+    for (int d = 0; d < nx; ++d) {
+      T dn0[G];
+#pragma unroll
+      for (int g = 0; g < G; ++g) dn0[g] = __shfl_sync(FULL, v[RMAX - 1][g], below);
+      if (active) {
+#pragma unroll
+        for (int rr = 0; rr < RMAX; ++rr) {
+          const int r = RMAX - 1 - rr;
+          if (RFIXED || r >= rb) {
+            const int jp = j0 + (r - rb);
+            const int ip = pmod(d + d0 - jp, nx);
+            const int x = sx > 0 ? ip : nx - 1 - ip;
+            const int y = sy > 0 ? jp : ny - 1 - jp;
+            const int cell = x + nx * y;
+            const uint8_t code = __ldg(codev + cell);
+            const T src = srcv[cell];
+            const T twx = twcv[cell * 6 + in_x_side];
+            const T twy = twcv[cell * 6 + in_y_side];
+            const bool wx = code & in_x_bit, wy = code & in_y_bit;
+            const bool jump = (ip == 0) && !wx;
+            const bool below_in_lane = RFIXED ? (r > 0) : (r > rb);
+            T sval = T(1);
+            if (HAS_S) sval = (T)__ldg(sv_ptr + cell);
+            T tl = T(0);
+#pragma unroll
+            for (int g = 0; g < G; ++g) {
+              const T ux = wx ? twx : v[r][g];
+              const T ud = below_in_lane ? v[r > 0 ? r - 1 : 0][g] : dn0[g];
+              const T uy = wy ? twy : ud;
+              const T jx = jump ? JX[g] : T(0);
+              T acc;
+              if (HAS_S) acc = fma(AY[g], uy, src + jx);
+              else acc = fma(AY[g], uy, fma(src, A0[g], jx));
+              acc = fma(AX[g], ux, acc);
+              T val;
+              if (HAS_S) {
+                if (sizeof(T) == 4) val = (T)__fdividef((float)acc, (float)(sval + A0[g]));
+                else val = acc / (sval + A0[g]);
+              } else {
+                val = acc;
+              }
+              v[r][g] = val;
+              tl = fma(AW[g], val, tl);
+            }
+            if (code & CODE_SOLID) {
+              atomicAdd(TLacc + cell, widen(tl));
+              if ((code & out_wall_bits) || ip == nx - 1 || rare_pass) {
+#pragma unroll
+                for (int g = 0; g < G; ++g) scratch[g] = v[r][g];
+                phi += cell_epilogue_2d<T, G>(gm, scratch, cell, code, x, ip, o0, cnt, sx, sy,
+                                              flags, kx_sum);
+              }
+            }
+          }
+        }
+      }
+      __syncwarp();
+    }
+
+    T* frontw = reinterpret_cast<T*>(gm.front);
+#pragma unroll
+    for (int r = 0; r < RMAX; ++r)
+#pragma unroll
+      for (int g = 0; g < G; ++g)
+        if (active && r >= rb && g < cnt) frontw[(size_t)(o0 + g) * ny + j0 + (r - rb)] = v[r][g];
+
+    for (int o = 16; o > 0; o >>= 1) phi += __shfl_xor_sync(FULL, phi, o);
+    if (lane == 0 && phi != 0.0) atomicAdd(gm.phi_acc, phi);
+    if (!L.item_counter) return;
+  }
+}
+
+}  // namespace obte

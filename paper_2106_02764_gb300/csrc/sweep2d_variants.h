@@ -1,0 +1,50 @@
+// 2D warp-kernel variants compiled into the library, one list per translation
+// unit.  X(T, G, RMAX, HAS_S, RFIXED).
+#pragma once
+
+#include "obte_internal.h"
+
+#define OBTE_SWEEP2D_WF(X) \
+  X(float, 8, 8, false, true) \
+  X(float, 8, 4, false, true) \
+  X(float, 16, 4, false, true) \
+  X(float, 16, 2, false, true) \
+  X(float, 16, 1, false, true) \
+  X(float, 8, 1, false, true)
+
+#define OBTE_SWEEP2D_WS(X) \
+  X(float, 8, 8, true, true) \
+  X(float, 8, 4, true, true) \
+  X(float, 16, 4, true, true) \
+  X(float, 16, 2, true, true) \
+  X(float, 16, 1, true, true) \
+  X(float, 8, 1, true, true) \
+  X(double, 4, 8, true, true) \
+  X(double, 8, 4, true, true) \
+  X(double, 8, 2, true, true) \
+  X(double, 8, 1, true, true)
+
+#define OBTE_SWEEP2D_WD(X) \
+  X(double, 4, 8, false, true) \
+  X(double, 8, 4, false, true) \
+  X(double, 8, 2, false, true) \
+  X(double, 8, 1, false, true)
+
+#define OBTE_SWEEP2D_WB(X) \
+  X(float, 8, 8, false, false) \
+  X(double, 4, 8, false, false) \
+  X(float, 8, 8, true, false) \
+  X(double, 4, 8, true, false)
+
+#define OBTE_SWEEP2D_VARIANTS(X) OBTE_SWEEP2D_WF(X) OBTE_SWEEP2D_WS(X) OBTE_SWEEP2D_WD(X) OBTE_SWEEP2D_WB(X)
+
+#define OBTE_SWEEP2D_NAME(T, G, R, S, F) obte_sweep2d_##T##_##G##_##R##_##S##_##F
+#define OBTE_SWEEP2D_DECLARE(T, G, R, S, F) \
+  cudaError_t OBTE_SWEEP2D_NAME(T, G, R, S, F)(const SweepLaunch* L, int blocks, cudaStream_t st);
+OBTE_SWEEP2D_VARIANTS(OBTE_SWEEP2D_DECLARE)
+
+#define OBTE_SWEEP2D_DEFINE(T, G, R, S, F)                                                      \
+  cudaError_t OBTE_SWEEP2D_NAME(T, G, R, S, F)(const SweepLaunch* L, int blocks, cudaStream_t st) { \
+    obte::sweep2d_warp_kernel<T, G, R, S, F><<<blocks, 32 * kWarpsPerBlock, 0, st>>>(*L);         \
+    return cudaGetLastError();                                                                 \
+  }

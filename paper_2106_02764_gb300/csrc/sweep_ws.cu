@@ -1,0 +1,5 @@
+// 2D warp-kernel variants: list OBTE_SWEEP2D_WS of sweep2d_variants.h.
+#include "sweep2d.cuh"
+#include "sweep2d_variants.h"
+
+OBTE_SWEEP2D_WS(OBTE_SWEEP2D_DEFINE)
