@@ -71,6 +71,8 @@ struct obte_ctx {
   double* TL_acc = nullptr;
   void* src = nullptr;
   void* twc = nullptr;
+  void* rec4 = nullptr;
+  double* tlq = nullptr;
   double* Tw = nullptr;
   double* wall_acc = nullptr;
   void* front = nullptr;
@@ -132,6 +134,8 @@ struct obte_ctx {
     wall_cell_d = nullptr;
     wall_side_d = nullptr;
     twc = nullptr;
+    rec4 = nullptr;
+    tlq = nullptr;
     s_d = nullptr;
     wall_den_d = nullptr;
     for (auto& a : tab_d)
@@ -683,6 +687,10 @@ static int prepare_state(obte_ctx* ctx, int precision, int G, int R, bool warp, 
   if (ctx->precision != precision) {
     ctx->drop_graph();
     // (re)allocate everything that depends on the precision
+    ctx->dfree(ctx->rec4);
+    ctx->dfree(ctx->tlq);
+    ctx->rec4 = nullptr;
+    ctx->tlq = nullptr;
     for (void* p : {(void*)ctx->TL, (void*)ctx->TL_acc, ctx->src, ctx->twc, (void*)ctx->Tw, (void*)ctx->wall_acc,
                     ctx->front, (void*)ctx->scal, (void*)ctx->ctrl, (void*)ctx->hist, (void*)ctx->TF,
                     (void*)ctx->fwork, (void*)ctx->fiters, (void*)ctx->gd})
@@ -718,6 +726,14 @@ static int prepare_state(obte_ctx* ctx, int precision, int G, int R, bool warp, 
     NEED(ctx->gd);
     ctx->precision = precision;
   }
+  if (warp && !ctx->rec4) {
+    const size_t e = precision == 0 ? 8 : 4;
+    ctx->rec4 = ctx->dalloc(4 * e * 4 * (size_t)ctx->n_cells);
+    ctx->tlq = ctx->dalloc_t<double>(4 * (size_t)ctx->n_cells);
+    NEED(ctx->rec4);
+    NEED(ctx->tlq);
+    CK(cudaMemsetAsync(ctx->tlq, 0, sizeof(double) * 4 * (size_t)ctx->n_cells, ctx->stream));
+  }
   GeomDev& g = ctx->gh;
   std::memset(&g, 0, sizeof(g));
   g.nx = Nx;
@@ -746,6 +762,8 @@ static int prepare_state(obte_ctx* ctx, int precision, int G, int R, bool warp, 
   g.wall_cell = ctx->wall_cell_d;
   g.wall_side = ctx->wall_side_d;
   g.twc = ctx->twc;
+  g.rec4 = warp ? ctx->rec4 : nullptr;
+  g.tlq = warp ? ctx->tlq : nullptr;
   g.front = ctx->front;
   g.phi_acc = ctx->scal;
   g.delta_max = ctx->scal + 1;
@@ -811,8 +829,7 @@ static cudaError_t sweep_once(obte_ctx* ctx, int flags) {
   L.flags = flags;
   L.item_counter = nullptr;
   if (ctx->warp)
-    return launch_sweep2d_warp(L, ctx->precision, ctx->G, ctx->R, ctx->has_s, true,
-                               (L.n_items + kWarpsPerBlock - 1) / kWarpsPerBlock, ctx->stream);
+    return launch_sweep2d_warp(L, ctx->precision, ctx->G, ctx->R, ctx->has_s, true, 0, ctx->stream);
   const size_t smem = sweep_smem_bytes(ctx->precision, ctx->dim, ctx->G, ctx->R, ctx->threads);
   return launch_sweep(L, ctx->precision, ctx->dim, ctx->G, ctx->R, ctx->has_s, ctx->threads,
                       L.n_items, smem, ctx->stream);
@@ -830,6 +847,7 @@ static int init_from_fourier(obte_ctx* ctx, const obte_solve_opts& op, int* fite
   CK(launch_fourier_cg(ctx->gh, ctx->h[0], ctx->h[1], ctx->h[2], prec, fmax, ftol, ctx->TF,
                        ctx->fiters, ctx->fwork, kFourierBlocksMax, ctx->stream));
   CK(launch_init_state_oct(ctx->gd, ctx->gh, 0, ctx->TF, prec, ctx->octant_d, ctx->stream));
+  if (ctx->warp) CK(launch_build_records(ctx->gd, 1, prec, finalize_blocks(ctx->n_cells), ctx->stream));
   if (fiters_out) {
     CK(cudaMemcpyAsync(fiters_out, ctx->fiters, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
   }
@@ -841,6 +859,7 @@ static std::vector<Variant> filtered_candidates(obte_ctx* ctx, int precision,
   std::vector<Variant> out;
   for (auto& c : candidates(precision, ctx->dim, ctx->n[1], ctx->n[2], ctx->has_s)) {
     if (op.kernel == 1 && c.warp) continue;
+    if (c.warp && ctx->n_cells > kMaxSkewCells) continue;  // packed cell index is 22 bits
     if (op.kernel == 2 && !c.warp) continue;
     if (op.group_size > 0 && c.G != op.group_size) continue;
     if (op.rows_per_thread > 0 && c.R != op.rows_per_thread) continue;
@@ -949,6 +968,10 @@ static int run_iterations(obte_ctx* ctx, const obte_solve_opts& op, int* iters, 
       if (op.profile && (e = cudaEventRecordWithFlags(ev[3 * i + 1], ctx->stream, cudaEventRecordExternal)) != cudaSuccess) return e;
       e = launch_finalize(ctx->gd, 1, ctx->precision, finalize_blocks(ctx->n_cells), ctx->stream);
       if (e != cudaSuccess) return e;
+      if (ctx->warp) {
+        e = launch_build_records(ctx->gd, 1, ctx->precision, finalize_blocks(ctx->n_cells), ctx->stream);
+        if (e != cudaSuccess) return e;
+      }
       if (op.profile && (e = cudaEventRecordWithFlags(ev[3 * i + 2], ctx->stream, cudaEventRecordExternal)) != cudaSuccess) return e;
     }
     return cudaSuccess;
@@ -1153,6 +1176,7 @@ static int run_flux_pass(obte_ctx* ctx) {
   CK(sweep_once(ctx, SWEEP_FLUX));
   // the pass does not advance the iterate: drop its moment accumulations
   CK(cudaMemsetAsync(ctx->TL_acc, 0, sizeof(double) * ctx->n_cells, ctx->stream));
+  if (ctx->tlq) CK(cudaMemsetAsync(ctx->tlq, 0, sizeof(double) * 4 * (size_t)ctx->n_cells, ctx->stream));
   CK(cudaMemsetAsync(ctx->wall_acc, 0, sizeof(double) * std::max(1, ctx->n_walls), ctx->stream));
   CK(cudaMemsetAsync(ctx->scal, 0, sizeof(double), ctx->stream));
   int one = 1;
@@ -1306,8 +1330,7 @@ extern "C" int obte_kappa_grad_s(obte_ctx* ctx, double* out, size_t max_field_by
     L.flags = SWEEP_RECORD;
     L.item_counter = nullptr;
     if (ctx->warp) {
-      CK(launch_sweep2d_warp(L, ctx->precision, ctx->G, ctx->R, ctx->has_s, true,
-                             (L.n_items + kWarpsPerBlock - 1) / kWarpsPerBlock, ctx->stream));
+      CK(launch_sweep2d_warp(L, ctx->precision, ctx->G, ctx->R, ctx->has_s, true, 0, ctx->stream));
     } else {
       const size_t smem = sweep_smem_bytes(ctx->precision, ctx->dim, ctx->G, ctx->R, ctx->threads);
       CK(launch_sweep(L, ctx->precision, ctx->dim, ctx->G, ctx->R, ctx->has_s, ctx->threads,
@@ -1316,6 +1339,7 @@ extern "C" int obte_kappa_grad_s(obte_ctx* ctx, double* out, size_t max_field_by
     CK(launch_grad_contract2(ctx->code_d, ctx->TL, ctx->n_cells, rec, (int)b.size(), revl_d, a_d,
                              jscale, grad_d, ctx->precision, ctx->stream));
     CK(cudaMemsetAsync(ctx->TL_acc, 0, sizeof(double) * ctx->n_cells, ctx->stream));
+    if (ctx->tlq) CK(cudaMemsetAsync(ctx->tlq, 0, sizeof(double) * 4 * (size_t)ctx->n_cells, ctx->stream));
     CK(cudaMemsetAsync(ctx->wall_acc, 0, sizeof(double) * std::max(1, ctx->n_walls), ctx->stream));
     CK(cudaMemsetAsync(ctx->scal, 0, sizeof(double), ctx->stream));
     CK(cudaStreamSynchronize(ctx->stream));
@@ -1367,6 +1391,7 @@ extern "C" int obte_solve_batch(obte_ctx* const* ctxs, int n, const obte_solve_o
                   (op.group_size <= 0 || op.group_size == wG);
   for (int i = 0; use_warp && i < n; ++i) {
     const int ny = ctxs[i]->n[1];
+    if (ctxs[i]->n_cells > kMaxSkewCells) use_warp = false;
     for (int R = 1; R <= wR; ++R)
       if (ny % R == 0 && ny / R <= 32) {
         r_eff[i] = R;
@@ -1442,6 +1467,7 @@ extern "C" int obte_solve_batch(obte_ctx* const* ctxs, int n, const obte_solve_o
     cudaError_t e = launch_fourier_cg(c->gh, c->h[0], c->h[1], c->h[2], prec, fmax, ftol, c->TF,
                                       c->fiters, c->fwork, kFourierBlocksMax, ctx->stream);
     if (e == cudaSuccess) e = launch_init_state_oct(gds, gh[i], i, c->TF, prec, c->octant_d, ctx->stream);
+    if (e == cudaSuccess && v.warp) e = launch_build_records(gds + i, 1, prec, finalize_blocks(c->n_cells), ctx->stream);
     c->stream = keep;
     if (e != cudaSuccess) return ctx->cuda_fail(e, "batch init");
   }
@@ -1462,6 +1488,10 @@ extern "C" int obte_solve_batch(obte_ctx* const* ctxs, int n, const obte_solve_o
       if (e != cudaSuccess) return e;
       e = launch_finalize(gds, n, prec, finalize_blocks(max_cells), ctx->stream);
       if (e != cudaSuccess) return e;
+      if (v.warp) {
+        e = launch_build_records(gds, n, prec, finalize_blocks(max_cells), ctx->stream);
+        if (e != cudaSuccess) return e;
+      }
     }
     return cudaSuccess;
   };

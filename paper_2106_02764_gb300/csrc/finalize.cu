@@ -32,8 +32,21 @@ __global__ void finalize_kernel(const GeomDev* geoms) {
   const int stride = gridDim.x * blockDim.x;
   for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < g.n_cells; c += stride) {
     if (!(g.code[c] & CODE_SOLID)) continue;
-    const double t = g.TL_acc[c];
-    g.TL_acc[c] = 0.0;
+    double t;
+    if (g.tlq) {  // 2D warp kernel: four skewed quadrant accumulators
+      const int x = c % g.nx, y = c / g.nx;
+      t = 0.0;
+      for (int q = 0; q < 4; ++q) {
+        const int ip = (q & 1) ? g.nx - 1 - x : x;
+        const int jp = (q & 2) ? g.ny - 1 - y : y;
+        const size_t k = ((size_t)q * g.nx + (ip + jp) % g.nx) * g.ny + jp;
+        t += g.tlq[k];
+        g.tlq[k] = 0.0;
+      }
+    } else {
+      t = g.TL_acc[c];
+      g.TL_acc[c] = 0.0;
+    }
     if (!isfinite(t)) nonfin = 1;
     dmax = fmax(dmax, fabs(t - g.TL[c]));
     g.TL[c] = t;
@@ -193,7 +206,46 @@ __global__ void grad_contract_kernel(const uint8_t* code, const double* TL, int 
   }
 }
 
+// Skewed per-quadrant cell records of the 2D warp kernel (layout in
+// obte_internal.h): source, wall temperatures through the upwind x / y sides,
+// packed cell index, face code and first / last column flags.
+template <typename T>
+__global__ void build_records_kernel(const GeomDev* geoms) {
+  const GeomDev& g = geoms[blockIdx.y];
+  if (!g.rec4 || *(volatile int*)g.done) return;
+  const T* src = reinterpret_cast<const T*>(g.src);
+  const T* twc = reinterpret_cast<const T*>(g.twc);
+  T* rec = reinterpret_cast<T*>(g.rec4);
+  const int stride = gridDim.x * blockDim.x;
+  for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < g.n_cells; c += stride) {
+    const int x = c % g.nx, y = c / g.nx;
+    const uint32_t code = g.code[c];
+    for (int q = 0; q < 4; ++q) {
+      const int ip = (q & 1) ? g.nx - 1 - x : x;
+      const int jp = (q & 2) ? g.ny - 1 - y : y;
+      const size_t k = ((size_t)q * g.nx + (ip + jp) % g.nx) * g.ny + jp;
+      const uint32_t packed = (uint32_t)c | (code << 22) | ((ip == 0 ? 1u : 0u) << 30) |
+                              ((ip == g.nx - 1 ? 1u : 0u) << 31);
+      const int sx_in = (q & 1) ? 1 : 0, sy_in = (q & 2) ? 3 : 2;
+      T* r = rec + 4 * k;
+      r[0] = src[c];
+      r[1] = twc[(size_t)c * 6 + sx_in];
+      r[2] = twc[(size_t)c * 6 + sy_in];
+      if (sizeof(T) == 4) r[3] = (T)__uint_as_float(packed);
+      else r[3] = (T)__longlong_as_double((long long)packed);
+    }
+  }
+}
+
 }  // namespace
+
+cudaError_t launch_build_records(const GeomDev* geoms_dev, int n_geoms, int precision, int blocks,
+                                 cudaStream_t st) {
+  dim3 grid(blocks, n_geoms);
+  if (precision == 0) build_records_kernel<double><<<grid, 256, 0, st>>>(geoms_dev);
+  else build_records_kernel<float><<<grid, 256, 0, st>>>(geoms_dev);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_finalize(const GeomDev* geoms_dev, int n_geoms, int precision, int blocks,
                             cudaStream_t st) {

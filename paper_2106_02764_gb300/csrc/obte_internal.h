@@ -50,6 +50,13 @@ struct GeomDev {
   const int* wall_cell;   // [n_walls]
   const int* wall_side;   // [n_walls] side of its cell (0..5: -x +x -y +y -z +z)
   void* twc;              // [n_cells * 6] wall temperature seen through each side, sweep precision
+  // 2D warp kernel: per-quadrant skewed cell records and T_L accumulators.
+  // Quadrant q's cell (i', j') (mirrored frame) sits at diagonal s = (i' + j') mod nx:
+  //   rec4[(q * nx + s) * ny + j']  = {s_i T_L,i, T_w in-x side, T_w in-y side, packed}
+  //   packed = cell (bits 0-21) | code << 22 | [i' == 0] << 30 | [i' == nx-1] << 31
+  //   tlq[(q * nx + s) * ny + j']   = sum_o a_o T_o of the running sweep (FP64)
+  void* rec4;
+  double* tlq;
   void* front;            // [n_ord][rows] row values carried between iterations
   double* phi_acc;        // [1] hot-face flux of the running sweep
   // flux pass outputs
@@ -108,6 +115,10 @@ int sweep_blocks_per_sm(int precision, int dim, int G, int RMAX, bool has_s, int
 // finalize.cu
 cudaError_t launch_finalize(const GeomDev* geoms_dev, int n_geoms, int precision, int blocks,
                             cudaStream_t st);
+// rebuild the skewed records of the 2D warp kernel (after finalize / init)
+cudaError_t launch_build_records(const GeomDev* geoms_dev, int n_geoms, int precision, int blocks,
+                                 cudaStream_t st);
+constexpr int kMaxSkewCells = 1 << 22;
 cudaError_t launch_init_state_oct(const GeomDev* geoms_dev, const GeomDev& gh, int gi,
                                   const double* T0, int precision, const int* octant_of,
                                   cudaStream_t st);  // uses gh.ord_d0

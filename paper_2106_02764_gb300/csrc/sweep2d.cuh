@@ -1,34 +1,57 @@
 // 2D upwind transport sweep, one ordinate group per warp (Eq. iter2 of App. A,
 // one source-iteration pass of Algorithm 1) with the moment reductions fused.
 //
-// Same wavefront as the block kernel (sweep.cuh): row j' visits column
-// i'(d) = (d + d0 - j') mod nx at step d, in the frame mirrored per quadrant;
-// the x neighbour is the row's own previous value and the y neighbour the row
-// below's previous value.  Here a whole group lives in one warp: lane l owns
-// R = ny / tpp consecutive rows (tpp <= 32 lanes in use), so the row below a
-// lane's lowest row is the top row of lane l - 1 (lane tpp - 1 for lane 0 when
-// y is periodic) and arrives by a warp shuffle.  No shared-memory exchange, no
-// barrier: warps never wait for one another.
+// Same wavefront as the block kernel (sweep.cuh): in the frame mirrored per
+// quadrant, row j' visits column i'(d) = (d + d0 - j') mod nx at step d; the x
+// neighbour is the row's own previous value and the y neighbour the row
+// below's previous value.  A whole group lives in one warp: lane l owns R
+// consecutive rows (ny / R <= 32 lanes in use), so the row below a lane's
+// lowest row is the top row of lane l - 1 (lane tpp - 1 for lane 0 when y is
+// periodic) and arrives by a warp shuffle.  No barrier: warps never wait for
+// one another.
+//
+// Data layout.  All cells a warp visits at step d lie on one diagonal
+// s = (i' + j') mod nx = (d + d0) mod nx of the quadrant frame.  The
+// finalisation stores, per quadrant, every cell's record (source s_i T_L,i,
+// the wall temperatures seen through its upwind x and y sides, and a packed
+// word with the cell index, face code and first / last column flags) at
+// [s][j'], so a lane's R rows of one step are R contiguous records.  They are
+// prefetched one step ahead with cp.async into lane-private shared memory.
+// The T_L moment goes to a per-quadrant accumulator in the same skewed layout
+// (FP64 atomics); the finalisation sums the four quadrants.
+//
+// Cells are updated branch-free (pores too: a pore's value is never read by a
+// solid cell, whose faces towards a pore are walls); only the atomics and the
+// rare epilogue (walls the ordinates leave into, the hot-contact column, flux /
+// record passes) are predicated on the cell being solid.
 //
 // The R rows of a lane sit in the top R of RMAX register rows (slots
 // RMAX - R .. RMAX - 1), so the lane's top row is always slot RMAX - 1; with
-// RFIXED the host guarantees R == RMAX.  Cells are updated branch-free (pores
-// too: their values are never read by a solid cell, whose faces towards a pore
-// are walls); the wall temperature seen through a cell side comes from a
-// per-cell array written by the finalisation, and only the moment atomics and
-// the rare epilogue (walls the ordinates leave into, the hot-contact column,
-// flux / record passes) are predicated on the cell being solid.
+// RFIXED the host guarantees R == RMAX.
 #pragma once
 
 #include "sweep.cuh"
 
 namespace obte {
 
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+
+__device__ __forceinline__ uint32_t rec_bits(float f) { return __float_as_uint(f); }
+__device__ __forceinline__ uint32_t rec_bits(double d) { return (uint32_t)__double_as_longlong(d); }
+
 // Rare per-cell epilogue of the warp kernel, in the sweep precision; sums are
 // widened exactly before the FP64 atomics.  Returns the hot-face flux.
 template <typename T, int G>
 __device__ __noinline__ double cell_epilogue_2d(const GeomDev& gm, const T* __restrict__ val,
-                                                int cell, uint8_t code, int x, int ip, int o0,
+                                                int cell, uint8_t code, bool last, int o0,
                                                 int cnt, int sx, int sy, int flags,
                                                 double kx_sum) {
   const int nx = gm.nx;
@@ -43,10 +66,11 @@ __device__ __noinline__ double cell_epilogue_2d(const GeomDev& gm, const T* __re
   const double dx = widen(sxk), dy = widen(syk);
   if (code & out_x_bit) atomicAdd(gm.wall_acc + gm.wall_id[cell * 6 + (sx > 0 ? 1 : 0)], dx);
   if (code & out_y_bit) atomicAdd(gm.wall_acc + gm.wall_id[cell * 6 + (sy > 0 ? 3 : 2)], dy);
-  const bool hot = (ip == nx - 1) && !(code & out_x_bit);
+  const bool hot = last && !(code & out_x_bit);
   double phi = 0.0;
   if (hot) phi = (sx > 0 ? dx : -dx) + (sx > 0 ? dT * kx_sum : 0.0);
   if (flags & SWEEP_FLUX) {
+    const int x = cell % nx;
     atomicAdd(gm.J_acc + 3 * cell + 0, sx > 0 ? dx : -dx);
     atomicAdd(gm.J_acc + 3 * cell + 1, sy > 0 ? dy : -dy);
     if (!(code & out_x_bit)) {
@@ -70,9 +94,19 @@ __device__ __noinline__ double cell_epilogue_2d(const GeomDev& gm, const T* __re
   return phi;
 }
 
+// warps per block: every warp owns its own staging buffers (static shared
+// memory stays under 48 KB)
+template <typename T, int RMAX>
+struct WarpCfg {
+  static constexpr int WPB = (sizeof(T) == 8 && RMAX >= 8) ? 2 : 4;
+};
+
 template <typename T, int G, int RMAX, bool HAS_S, bool RFIXED>
-__global__ void __launch_bounds__(32 * kWarpsPerBlock, 1) sweep2d_warp_kernel(const SweepLaunch L) {
-  __shared__ __align__(16) T scratch_all[kWarpsPerBlock][32][G];
+__global__ void __launch_bounds__(32 * WarpCfg<T, RMAX>::WPB, 1) sweep2d_warp_kernel(const SweepLaunch L) {
+  constexpr int WPB = WarpCfg<T, RMAX>::WPB;
+  constexpr int CH = (4 * sizeof(T)) / 16;  // 16-byte chunks per record
+  __shared__ __align__(16) T recbuf[WPB][2][32][RMAX][4];
+  __shared__ __align__(16) T scratch_all[WPB][32][G];
   const int lane = threadIdx.x & 31;
   const int wib = threadIdx.x >> 5;
   T* scratch = &scratch_all[wib][lane][0];
@@ -80,7 +114,7 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock, 1) sweep2d_warp_kernel(co
   const bool rare_pass = (flags & (SWEEP_FLUX | SWEEP_RECORD)) != 0;
   const unsigned FULL = 0xffffffffu;
 
-  int item = blockIdx.x * kWarpsPerBlock + wib;
+  int item = blockIdx.x * WPB + wib;
   for (;;) {
     if (L.item_counter) {
       int it = 0;
@@ -98,17 +132,16 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock, 1) sweep2d_warp_kernel(co
     const int R = RFIXED ? RMAX : gm.R;  // rows per lane, <= RMAX
     const int rb = RMAX - R;             // first register row in use
     const int tpp = gm.tpp;              // lanes in use
-    const int sx = (wi.octant & 1) ? -1 : 1;
-    const int sy = (wi.octant & 2) ? -1 : 1;
+    const int q = wi.octant & 3;
+    const int sx = (q & 1) ? -1 : 1;
+    const int sy = (q & 2) ? -1 : 1;
     const int o0 = wi.o0, cnt = wi.count, d0 = wi.d0;
     const double dT = gm.dT;
     const bool active = lane < tpp;
     const int j0 = lane * R;
-    const uint8_t* __restrict__ codev = gm.code;
-    const T* __restrict__ srcv = reinterpret_cast<const T*>(gm.src);
-    const T* __restrict__ twcv = reinterpret_cast<const T*>(gm.twc);
+    const T* __restrict__ recq = reinterpret_cast<const T*>(gm.rec4) + (size_t)q * nx * ny * 4;
+    double* tlq = gm.tlq + (size_t)q * nx * ny;
     const double* __restrict__ sv_ptr = gm.s;
-    double* TLacc = gm.TL_acc;
 
     T A0[G], AX[G], AY[G], AW[G], JX[G];
     double kx_sum = 0.0;
@@ -139,39 +172,57 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock, 1) sweep2d_warp_kernel(co
       for (int g = 0; g < G; ++g)
         v[r][g] = (active && r >= rb && g < cnt) ? front[(size_t)(o0 + g) * ny + j0 + (r - rb)] : T(0);
 
-    // lane holding the row below this lane's lowest row
+    // prefetch the records of the lane's rows on diagonal s into buffer b
+    auto prefetch = [&](int s, int b) {
+      if (active) {
+        const T* g0 = recq + ((size_t)s * ny + j0) * 4;
+#pragma unroll
+        for (int r = 0; r < RMAX; ++r)
+          if (RFIXED || r >= rb)
+#pragma unroll
+            for (int c = 0; c < CH; ++c)
+              cp_async16(reinterpret_cast<char*>(&recbuf[wib][b][lane][r][0]) + 16 * c,
+                         reinterpret_cast<const char*>(g0 + (size_t)(r - rb) * 4) + 16 * c);
+      }
+      cp_async_commit();
+    };
+
     const int below = lane > 0 ? lane - 1 : (gm.py ? tpp - 1 : 0);
     const uint8_t in_x_bit = sx > 0 ? CODE_WALL_XM : CODE_WALL_XP;
     const uint8_t in_y_bit = sy > 0 ? CODE_WALL_YM : CODE_WALL_YP;
-    const uint8_t out_wall_bits = (uint8_t)((sx > 0 ? CODE_WALL_XP : CODE_WALL_XM) |
-                                            (sy > 0 ? CODE_WALL_YP : CODE_WALL_YM));
-    const int in_x_side = sx > 0 ? 0 : 1;
-    const int in_y_side = sy > 0 ? 2 : 3;
+    const uint32_t out_wall_bits = (sx > 0 ? CODE_WALL_XP : CODE_WALL_XM) |
+                                   (sy > 0 ? CODE_WALL_YP : CODE_WALL_YM);
     double phi = 0.0;
+    int s = d0;
+    prefetch(s, 0);
 
     for (int d = 0; d < nx; ++d) {
+      const int cur = d & 1;
+      const int s_next = (s + 1 == nx) ? 0 : s + 1;
+      if (d + 1 < nx) {
+        prefetch(s_next, cur ^ 1);
+        cp_async_wait<1>();
+      } else {
+        cp_async_wait<0>();
+      }
       T dn0[G];
 #pragma unroll
       for (int g = 0; g < G; ++g) dn0[g] = __shfl_sync(FULL, v[RMAX - 1][g], below);
       if (active) {
+        double* tl_row = tlq + (size_t)s * ny + j0 - rb;
 #pragma unroll
         for (int rr = 0; rr < RMAX; ++rr) {
           const int r = RMAX - 1 - rr;
           if (RFIXED || r >= rb) {
-            const int jp = j0 + (r - rb);
-            const int ip = pmod(d + d0 - jp, nx);
-            const int x = sx > 0 ? ip : nx - 1 - ip;
-            const int y = sy > 0 ? jp : ny - 1 - jp;
-            const int cell = x + nx * y;
-            const uint8_t code = __ldg(codev + cell);
-            const T src = srcv[cell];
-            const T twx = twcv[cell * 6 + in_x_side];
-            const T twy = twcv[cell * 6 + in_y_side];
+            const T* rc = &recbuf[wib][cur][lane][r][0];
+            const T src = rc[0], twx = rc[1], twy = rc[2];
+            const uint32_t packed = rec_bits(rc[3]);
+            const uint32_t code = (packed >> 22) & 0xffu;
             const bool wx = code & in_x_bit, wy = code & in_y_bit;
-            const bool jump = (ip == 0) && !wx;
+            const bool jump = ((packed >> 30) & 1u) && !wx;
             const bool below_in_lane = RFIXED ? (r > 0) : (r > rb);
             T sval = T(1);
-            if (HAS_S) sval = (T)__ldg(sv_ptr + cell);
+            if (HAS_S) sval = (T)__ldg(sv_ptr + (packed & 0x3fffffu));
             T tl = T(0);
 #pragma unroll
             for (int g = 0; g < G; ++g) {
@@ -194,17 +245,19 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock, 1) sweep2d_warp_kernel(co
               tl = fma(AW[g], val, tl);
             }
             if (code & CODE_SOLID) {
-              atomicAdd(TLacc + cell, widen(tl));
-              if ((code & out_wall_bits) || ip == nx - 1 || rare_pass) {
+              atomicAdd(tl_row + r, widen(tl));
+              const bool last = (packed >> 31) & 1u;
+              if ((code & out_wall_bits) || last || rare_pass) {
 #pragma unroll
                 for (int g = 0; g < G; ++g) scratch[g] = v[r][g];
-                phi += cell_epilogue_2d<T, G>(gm, scratch, cell, code, x, ip, o0, cnt, sx, sy,
-                                              flags, kx_sum);
+                phi += cell_epilogue_2d<T, G>(gm, scratch, (int)(packed & 0x3fffffu), (uint8_t)code,
+                                              last, o0, cnt, sx, sy, flags, kx_sum);
               }
             }
           }
         }
       }
+      s = s_next;
       __syncwarp();
     }
 

@@ -39,12 +39,16 @@
 #define OBTE_SWEEP2D_VARIANTS(X) OBTE_SWEEP2D_WF(X) OBTE_SWEEP2D_WS(X) OBTE_SWEEP2D_WD(X) OBTE_SWEEP2D_WB(X)
 
 #define OBTE_SWEEP2D_NAME(T, G, R, S, F) obte_sweep2d_##T##_##G##_##R##_##S##_##F
+// blocks == 0: one warp per work item; blocks > 0: that many persistent blocks
 #define OBTE_SWEEP2D_DECLARE(T, G, R, S, F) \
   cudaError_t OBTE_SWEEP2D_NAME(T, G, R, S, F)(const SweepLaunch* L, int blocks, cudaStream_t st);
 OBTE_SWEEP2D_VARIANTS(OBTE_SWEEP2D_DECLARE)
 
 #define OBTE_SWEEP2D_DEFINE(T, G, R, S, F)                                                      \
   cudaError_t OBTE_SWEEP2D_NAME(T, G, R, S, F)(const SweepLaunch* L, int blocks, cudaStream_t st) { \
-    obte::sweep2d_warp_kernel<T, G, R, S, F><<<blocks, 32 * kWarpsPerBlock, 0, st>>>(*L);         \
+    constexpr int wpb = obte::WarpCfg<T, R>::WPB;                                              \
+    const int need = (L->n_items + wpb - 1) / wpb;                                             \
+    const int b = (blocks > 0 && blocks < need) ? blocks : need;                               \
+    obte::sweep2d_warp_kernel<T, G, R, S, F><<<b, 32 * wpb, 0, st>>>(*L);                       \
     return cudaGetLastError();                                                                 \
   }
