@@ -186,6 +186,23 @@ int obte_get_section_flux(obte_ctx* ctx, double* out);
  * max_field_bytes (0: 1 GiB). */
 int obte_kappa_grad_s(obte_ctx* ctx, double* out, size_t max_field_bytes);
 
+/* d kappa_eff / d s_i like obte_kappa_grad_s, for callers that cannot allocate
+ * device memory at the time they need it (for example a framework capturing a
+ * CUDA graph, where cudaMalloc / cudaFree are not allowed, or a service held to
+ * a fixed device-memory budget).  This call allocates nothing: the recorded
+ * ordinate fields, the gradient accumulator and the small index tables live in
+ * a fixed 32 MiB device array inside the library (held by every GPU that loads
+ * the library until the process exits).  The context's own buffers, made by
+ * earlier calls, are reused.  out: host double[nz][ny][nx], 0 in pores.
+ * Returns OBTE_EINVAL with a message when the gradient, the ordinate tables and
+ * one reversed pair of ordinate fields do not fit in the 32 MiB.  The first
+ * call on a device takes the array's device address (cudaGetSymbolAddress);
+ * make that first call before any stream capture.  Every call shares the one
+ * array and overwrites it: calls whose work overlaps on the GPU (other
+ * threads, other contexts on other streams) race and must be serialised by
+ * the caller.  The paper has no counterpart to this entry point. */
+int obte_kappa_grad_s_noalloc(obte_ctx* ctx, double* out);
+
 /* Per-MFP-bin contribution to kappa_eff (the aMFP analogue of the
  * mode-resolved conductivity, App. A): host double[n_mfp]; sums to kappa_eff.
  * Runs with obte_get_flux's extra sweep. */

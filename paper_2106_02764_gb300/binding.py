@@ -78,6 +78,7 @@ SIGNATURES = [
     ("obte_get_section_flux", C.c_int, [C.c_void_p, C.c_void_p]),
     ("obte_kappa_grad_s", C.c_int, [C.c_void_p, C.c_void_p, C.c_size_t]),
     ("obte_get_kappa_bins", C.c_int, [C.c_void_p, C.c_void_p]),
+    ("obte_kappa_grad_s_noalloc", C.c_int, [C.c_void_p, C.c_void_p]),
     ("obte_last_error", C.c_char_p, [C.c_void_p]),
     ("obte_destroy", None, [C.c_void_p]),
 ]
@@ -274,6 +275,17 @@ class Solver:
         out = np.empty(self.shape, dtype=np.float64)
         self._check(self.lib.obte_kappa_grad_s(self.ctx, _ptr(out), C.c_size_t(int(max_field_bytes))))
         return out
+
+
+def _grad_noalloc(self):
+    """d kappa_eff / d s through obte_kappa_grad_s_noalloc (no device
+    allocation: the library's fixed scratch array holds the work buffers)."""
+    out = np.empty(self.shape, dtype=np.float64)
+    self._check(self.lib.obte_kappa_grad_s_noalloc(self.ctx, _ptr(out)))
+    return out
+
+
+Solver.kappa_grad_s_noalloc = _grad_noalloc
 
 
 def solve_batch(solvers, allow_not_converged=False, **kw):

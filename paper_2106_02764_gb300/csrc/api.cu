@@ -4,6 +4,7 @@
 #include <cstdio>
 #include <cstring>
 #include <map>
+#include <mutex>
 #include <string>
 #include <tuple>
 #include <vector>
@@ -1592,5 +1593,171 @@ extern "C" int obte_solve_batch(obte_ctx* const* ctxs, int n, const obte_solve_o
   if (rc) return rc;
   if (worst == OBTE_ENONFINITE) return ctx->fail(worst, "non-finite value in a batch member");
   if (worst == OBTE_NOT_CONVERGED) return ctx->fail(worst, "a batch member did not converge");
+  return OBTE_OK;
+}
+
+// ---------------------------------------------------------------------------
+// d kappa / d s without device allocation
+// ---------------------------------------------------------------------------
+// Some callers cannot allocate device memory when they need the gradient: a
+// framework that is capturing a CUDA graph (cudaMalloc / cudaFree are not
+// allowed while a stream capture is active), a service running under a fixed
+// device-memory budget whose allocator refuses new blocks, or a host thread
+// that must not stall on the implicit synchronisation of cudaFree.  For them,
+// obte_kappa_grad_s_noalloc does the work of obte_kappa_grad_s with every
+// buffer it needs beyond the context's existing state (recorded ordinate
+// fields, gradient accumulator, record slots, work list) carved out of this
+// fixed, file-scope device array.  The array is part of the library image:
+// every GPU that loads the library holds it until the process exits.
+#define OBTE_NOALLOC_SCRATCH_BYTES ((size_t)32 << 20)
+static __device__ __align__(256) unsigned char g_obte_noalloc_scratch[OBTE_NOALLOC_SCRATCH_BYTES];
+
+// Device address of the scratch array on the current device.  In host code the
+// array's name only stands for the device symbol, so its address is taken once
+// per device, with that device current, by cudaGetSymbolAddress.
+static cudaError_t noalloc_scratch(int device, unsigned char** out) {
+  static std::mutex mu;
+  static std::map<int, unsigned char*> ptrs;
+  std::lock_guard<std::mutex> lock(mu);
+  auto it = ptrs.find(device);
+  if (it != ptrs.end()) {
+    *out = it->second;
+    return cudaSuccess;
+  }
+  void* p = nullptr;
+  const cudaError_t e = cudaGetSymbolAddress(&p, g_obte_noalloc_scratch);
+  if (e != cudaSuccess) return e;
+  ptrs[device] = static_cast<unsigned char*>(p);
+  *out = static_cast<unsigned char*>(p);
+  return cudaSuccess;
+}
+
+extern "C" int obte_kappa_grad_s_noalloc(obte_ctx* ctx, double* out) {
+  if (!ctx || !out) return OBTE_EINVAL;
+  if (!ctx->solved) return ctx->fail(OBTE_ESTATE, "solve first");
+  CK(cudaSetDevice(ctx->device));
+  unsigned char* base = nullptr;
+  CK(noalloc_scratch(ctx->device, &base));
+  const int O = ctx->O;
+  std::vector<int> rev(O, -1);
+  {
+    std::map<std::tuple<int, long long, long long, long long>, int> idx;
+    auto keyf = [&](int o, double sgn) {
+      return std::make_tuple(ctx->ord_m[o], llround(sgn * ctx->pk[0][o] * 1e12),
+                             llround(sgn * ctx->pk[1][o] * 1e12), llround(sgn * ctx->pk[2][o] * 1e12));
+    };
+    for (int o = 0; o < O; ++o) idx[keyf(o, 1.0)] = o;
+    for (int o = 0; o < O; ++o) {
+      auto it = idx.find(keyf(o, -1.0));
+      if (it == idx.end()) return ctx->fail(OBTE_EINVAL, "direction set is not symmetric under p -> -p");
+      rev[o] = it->second;
+    }
+  }
+  // scratch layout: grad | slots | work items | per batch ordinate: field + rev + weight
+  auto up = [](size_t b) { return (b + 255) & ~(size_t)255; };
+  const size_t e = ctx->precision == 0 ? 8 : 4;
+  const size_t n_items = ctx->items_h.size();
+  const size_t fixed = up(sizeof(double) * ctx->n_cells) + up(sizeof(int) * O) +
+                       up(sizeof(WorkItem) * n_items) + 2 * 256;
+  const size_t per_ord = e * (size_t)ctx->n_cells + sizeof(int) + sizeof(double);
+  if (fixed + 2 * per_ord > OBTE_NOALLOC_SCRATCH_BYTES)
+    return ctx->fail(OBTE_EINVAL, "problem too large for the no-allocation scratch (" +
+                                      std::to_string(OBTE_NOALLOC_SCRATCH_BYTES >> 20) +
+                                      " MiB: gradient, ordinate slots, work list and one reversed "
+                                      "ordinate pair of fields must fit)");
+  const size_t pairs_cap = (OBTE_NOALLOC_SCRATCH_BYTES - fixed) / (2 * per_ord);
+  size_t off = 0;
+  auto carve = [&](size_t bytes) {
+    unsigned char* p = base + off;
+    off += up(bytes);
+    return p;
+  };
+  double* grad_d = reinterpret_cast<double*>(carve(sizeof(double) * ctx->n_cells));
+  int* slot_d = reinterpret_cast<int*>(carve(sizeof(int) * O));
+  WorkItem* its_d = reinterpret_cast<WorkItem*>(carve(sizeof(WorkItem) * n_items));
+  int* revl_d = reinterpret_cast<int*>(carve(sizeof(int) * 2 * pairs_cap));
+  double* a_d = reinterpret_cast<double*>(carve(sizeof(double) * 2 * pairs_cap));
+  void* rec = carve(e * (size_t)ctx->n_cells * 2 * pairs_cap);
+  if (off > OBTE_NOALLOC_SCRATCH_BYTES) return ctx->fail(OBTE_EINVAL, "no-allocation scratch layout overflow");
+  // batches of reversed ordinate pairs
+  std::vector<std::vector<int>> batches;
+  {
+    int o = 0;
+    while (o < O) {
+      const int q = ctx->octant[o];
+      int e1 = o;
+      while (e1 < O && ctx->octant[e1] == q) ++e1;
+      int e2 = e1;
+      while (e2 < O && ctx->octant[e2] == ctx->octant[e1]) ++e2;
+      const int half = e1 - o;
+      for (int a = 0; a < half; a += (int)pairs_cap) {
+        std::vector<int> b;
+        for (int k2 = a; k2 < std::min(half, a + (int)pairs_cap); ++k2) {
+          b.push_back(o + k2);
+          b.push_back(rev[o + k2]);
+        }
+        batches.push_back(b);
+      }
+      o = e2;
+    }
+  }
+  // the scratch keeps the previous call's contents: start the sum at zero
+  CK(cudaMemsetAsync(grad_d, 0, sizeof(double) * ctx->n_cells, ctx->stream));
+  const double jadj = -ctx->kappa_scale * ctx->d_ang * ctx->h[0] * ctx->sum_k_over_l2;
+  const double jscale = jadj / ctx->dT;
+  std::vector<int> slot(O);
+  int one = 1, zero = 0;
+  for (auto& b : batches) {
+    std::fill(slot.begin(), slot.end(), -1);
+    for (size_t k2 = 0; k2 < b.size(); ++k2) slot[b[k2]] = (int)k2;
+    std::vector<int> revl(b.size());
+    std::vector<double> ab(b.size());
+    for (size_t k2 = 0; k2 < b.size(); ++k2) {
+      revl[k2] = slot[rev[b[k2]]];
+      ab[k2] = ctx->aw[b[k2]];
+    }
+    std::vector<WorkItem> its;
+    for (auto& it : ctx->items_h) {
+      bool any = false;
+      for (int o = it.o0; o < it.o0 + it.count; ++o)
+        if (slot[o] >= 0) any = true;
+      if (any) its.push_back(it);
+    }
+    CK(cudaMemcpyAsync(its_d, its.data(), sizeof(WorkItem) * its.size(), cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaMemcpyAsync(slot_d, slot.data(), sizeof(int) * O, cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaMemcpyAsync(revl_d, revl.data(), sizeof(int) * b.size(), cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaMemcpyAsync(a_d, ab.data(), sizeof(double) * b.size(), cudaMemcpyHostToDevice, ctx->stream));
+    GeomDev g = ctx->gh;
+    g.rec = rec;
+    g.rec_slot = slot_d;
+    CK(cudaMemcpyAsync(ctx->gd, &g, sizeof(GeomDev), cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaMemcpyAsync(ctx->ctrl, &zero, sizeof(int), cudaMemcpyHostToDevice, ctx->stream));
+    SweepLaunch L;
+    L.geoms = ctx->gd;
+    L.items = its_d;
+    L.n_items = (int)its.size();
+    L.flags = SWEEP_RECORD;
+    L.item_counter = nullptr;
+    if (ctx->warp) {
+      CK(launch_sweep2d_warp(L, ctx->precision, ctx->G, ctx->R, ctx->has_s, true, 0, ctx->stream));
+    } else {
+      const size_t smem = sweep_smem_bytes(ctx->precision, ctx->dim, ctx->G, ctx->R, ctx->threads);
+      CK(launch_sweep(L, ctx->precision, ctx->dim, ctx->G, ctx->R, ctx->has_s, ctx->threads,
+                      L.n_items, smem, ctx->stream));
+    }
+    CK(launch_grad_contract2(ctx->code_d, ctx->TL, ctx->n_cells, rec, (int)b.size(), revl_d, a_d,
+                             jscale, grad_d, ctx->precision, ctx->stream));
+    CK(cudaMemsetAsync(ctx->TL_acc, 0, sizeof(double) * ctx->n_cells, ctx->stream));
+    if (ctx->tlq) CK(cudaMemsetAsync(ctx->tlq, 0, sizeof(double) * 4 * (size_t)ctx->n_cells, ctx->stream));
+    CK(cudaMemsetAsync(ctx->wall_acc, 0, sizeof(double) * std::max(1, ctx->n_walls), ctx->stream));
+    CK(cudaMemsetAsync(ctx->scal, 0, sizeof(double), ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));  // host vectors above are copy sources
+  }
+  CK(cudaMemcpyAsync(ctx->gd, &ctx->gh, sizeof(GeomDev), cudaMemcpyHostToDevice, ctx->stream));
+  CK(cudaMemcpyAsync(ctx->ctrl, &one, sizeof(int), cudaMemcpyHostToDevice, ctx->stream));
+  std::vector<double> gk(ctx->n_cells);
+  CK(cudaMemcpyAsync(gk.data(), grad_d, sizeof(double) * ctx->n_cells, cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  to_user(ctx, [&](int c, long ui) { out[ui] = (ctx->code_h[c] & CODE_SOLID) ? gk[c] : 0.0; });
   return OBTE_OK;
 }
