@@ -72,6 +72,7 @@ struct obte_ctx {
   double* TL_acc = nullptr;
   void* src = nullptr;
   void* twc = nullptr;
+  CGArgs* cg_job = nullptr;
   void* rec4 = nullptr;
   double* tlq = nullptr;
   double* Tw = nullptr;
@@ -135,6 +136,7 @@ struct obte_ctx {
     wall_cell_d = nullptr;
     wall_side_d = nullptr;
     twc = nullptr;
+    cg_job = nullptr;
     rec4 = nullptr;
     tlq = nullptr;
     s_d = nullptr;
@@ -845,8 +847,18 @@ static int init_from_fourier(obte_ctx* ctx, const obte_solve_opts& op, int* fite
   const int prec = ctx->precision;
   int fmax = op.fourier_max_iter > 0 ? op.fourier_max_iter : 4 * (ctx->n[0] + ctx->n[1] + ctx->n[2]);
   double ftol = op.fourier_tol > 0 ? op.fourier_tol : (prec == 0 ? 1e-4 : 1e-4);
-  CK(launch_fourier_cg(ctx->gh, ctx->h[0], ctx->h[1], ctx->h[2], prec, fmax, ftol, ctx->TF,
-                       ctx->fiters, ctx->fwork, kFourierBlocksMax, ctx->stream));
+  if (ctx->n_cells <= 4096) {
+    // small mesh: one block solves it, no grid-wide synchronisation
+    if (!ctx->cg_job) ctx->cg_job = ctx->dalloc_t<CGArgs>(1);
+    NEED(ctx->cg_job);
+    const CGArgs job = make_cg_args(ctx->gh, ctx->h[0], ctx->h[1], ctx->h[2], fmax, ftol, ctx->TF,
+                                    ctx->fiters, ctx->fwork, kFourierBlocksMax);
+    CK(cudaMemcpyAsync(ctx->cg_job, &job, sizeof(CGArgs), cudaMemcpyHostToDevice, ctx->stream));
+    CK(launch_fourier_cg_blocks(ctx->cg_job, 1, prec, ctx->stream));
+  } else {
+    CK(launch_fourier_cg(ctx->gh, ctx->h[0], ctx->h[1], ctx->h[2], prec, fmax, ftol, ctx->TF,
+                         ctx->fiters, ctx->fwork, kFourierBlocksMax, ctx->stream));
+  }
   CK(launch_init_state_oct(ctx->gd, ctx->gh, 0, ctx->TF, prec, ctx->octant_d, ctx->stream));
   if (ctx->warp) CK(launch_build_records(ctx->gd, 1, prec, finalize_blocks(ctx->n_cells), ctx->stream));
   if (fiters_out) {
@@ -1457,19 +1469,33 @@ extern "C" int obte_solve_batch(obte_ctx* const* ctxs, int n, const obte_solve_o
   CK(cudaEventCreate(&e1));
   CK(cudaEventCreate(&e2));
   CK(cudaEventRecord(e0, ctx->stream));
-  // Fourier first guess and initial state per geometry (on the batch stream)
-  std::vector<int> fiters(n, 0);
+  // Fourier first guesses: geometries small enough for one block share one
+  // launch (a block each); larger ones get the cooperative solver
+  std::vector<CGArgs> jobs;
   for (int i = 0; i < n; ++i) {
     obte_ctx* c = ctxs[i];
-    cudaStream_t keep = c->stream;
-    c->stream = ctx->stream;
-    int fmax = op.fourier_max_iter > 0 ? op.fourier_max_iter : 4 * (c->n[0] + c->n[1] + c->n[2]);
-    double ftol = op.fourier_tol > 0 ? op.fourier_tol : 1e-4;
-    cudaError_t e = launch_fourier_cg(c->gh, c->h[0], c->h[1], c->h[2], prec, fmax, ftol, c->TF,
-                                      c->fiters, c->fwork, kFourierBlocksMax, ctx->stream);
-    if (e == cudaSuccess) e = launch_init_state_oct(gds, gh[i], i, c->TF, prec, c->octant_d, ctx->stream);
+    const int fmax = op.fourier_max_iter > 0 ? op.fourier_max_iter : 4 * (c->n[0] + c->n[1] + c->n[2]);
+    const double ftol = op.fourier_tol > 0 ? op.fourier_tol : 1e-4;
+    if (c->n_cells <= kBlockCGMaxCells) {
+      jobs.push_back(make_cg_args(c->gh, c->h[0], c->h[1], c->h[2], fmax, ftol, c->TF, c->fiters,
+                                  c->fwork, kFourierBlocksMax));
+    } else {
+      cudaError_t e = launch_fourier_cg(c->gh, c->h[0], c->h[1], c->h[2], prec, fmax, ftol, c->TF,
+                                        c->fiters, c->fwork, kFourierBlocksMax, ctx->stream);
+      if (e != cudaSuccess) return ctx->cuda_fail(e, "batch Fourier");
+    }
+  }
+  CGArgs* jobs_d = nullptr;
+  if (!jobs.empty()) {
+    jobs_d = ctx->dalloc_t<CGArgs>(jobs.size());
+    NEED(jobs_d);
+    CK(cudaMemcpyAsync(jobs_d, jobs.data(), sizeof(CGArgs) * jobs.size(), cudaMemcpyHostToDevice, ctx->stream));
+    CK(launch_fourier_cg_blocks(jobs_d, (int)jobs.size(), prec, ctx->stream));
+  }
+  for (int i = 0; i < n; ++i) {
+    obte_ctx* c = ctxs[i];
+    cudaError_t e = launch_init_state_oct(gds, gh[i], i, c->TF, prec, c->octant_d, ctx->stream);
     if (e == cudaSuccess && v.warp) e = launch_build_records(gds + i, 1, prec, finalize_blocks(c->n_cells), ctx->stream);
-    c->stream = keep;
     if (e != cudaSuccess) return ctx->cuda_fail(e, "batch init");
   }
   CK(cudaEventRecord(e1, ctx->stream));
@@ -1587,6 +1613,7 @@ extern "C" int obte_solve_batch(obte_ctx* const* ctxs, int n, const obte_solve_o
     else if (done != 1 && worst == OBTE_OK) worst = OBTE_NOT_CONVERGED;
   }
   cudaFreeHost(hc);
+  if (jobs_d) ctx->dfree(jobs_d);
   ctx->dfree(gds);
   ctx->dfree(items_d);
   ctx->dfree(counter);

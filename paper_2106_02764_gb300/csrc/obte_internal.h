@@ -129,6 +129,27 @@ cudaError_t launch_grad_contract2(const uint8_t* code, const double* TL, int n, 
                                   double jscale, double* grad, int precision, cudaStream_t st);
 
 // fourier.cu
+// arguments of one Fourier CG solve
+struct CGArgs {
+  const uint8_t* code;
+  int nx, ny, nz, dim, py, pz;
+  double wx, wy, wz, dT;
+  int max_iter;
+  double tol;
+  double* x;
+  double* r;
+  double* p;
+  double* q;
+  double* part;   // [2][gridDim]
+  double* T_out;  // [n] solution, mean 0, 0 in pores
+  int* iters_out;
+};
+CGArgs make_cg_args(const GeomDev& g, double hx, double hy, double hz, int max_iter, double tol,
+                    double* T_out, int* iters_out, double* work, int blocks_max);
+// one block per job (geometries up to kBlockCGMaxCells cells)
+cudaError_t launch_fourier_cg_blocks(const CGArgs* jobs_dev, int n_jobs, int precision,
+                                     cudaStream_t st);
+constexpr int kBlockCGMaxCells = 1 << 18;
 cudaError_t launch_fourier_cg(const GeomDev& g, double hx, double hy, double hz, int precision,
                               int max_iter, double tol, double* T_out, int* iters_out,
                               double* work, int blocks_max, cudaStream_t st);
