@@ -90,6 +90,10 @@ typedef struct {
                            events recorded on the solve stream (stats below)   */
   int kernel;           /* 0: automatic, 1: block kernel (every dimension),
                            2: 2D warp-per-group kernel                          */
+  int accel;            /* Anderson acceleration window (0: plain source
+                           iteration as in Algorithm 1; 1..7: mix the last
+                           accel iterates of (T_L, T_w, carried row values);
+                           same fixed point)                                   */
 } obte_solve_opts;
 
 #define OBTE_MAX_HISTORY 4096

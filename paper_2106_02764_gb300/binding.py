@@ -39,7 +39,7 @@ class SolveOpts(C.Structure):
                 ("max_iter", C.c_int), ("min_iter", C.c_int), ("check_every", C.c_int),
                 ("fourier_max_iter", C.c_int), ("fourier_tol", C.c_double),
                 ("group_size", C.c_int), ("rows_per_thread", C.c_int), ("use_graph", C.c_int),
-                ("profile", C.c_int), ("kernel", C.c_int)]
+                ("profile", C.c_int), ("kernel", C.c_int), ("accel", C.c_int)]
 
 
 class SolveStats(C.Structure):
@@ -223,7 +223,7 @@ class Solver:
     # -- solve
     def options(self, precision="fp64", tol=1e-6, tol_TL=0.0, max_iter=2000, min_iter=2,
                 check_every=8, fourier_max_iter=0, fourier_tol=0.0, group_size=0,
-                rows_per_thread=0, use_graph=True, profile=False, kernel=0):
+                rows_per_thread=0, use_graph=True, profile=False, kernel=0, accel=0):
         o = SolveOpts()
         self.lib.obte_default_opts(C.byref(o))
         o.precision = OBTE_MIXED if precision in ("mixed", OBTE_MIXED) else OBTE_FP64
@@ -232,6 +232,7 @@ class Solver:
         o.group_size, o.rows_per_thread, o.use_graph = int(group_size), int(rows_per_thread), int(bool(use_graph))
         o.profile = int(bool(profile))
         o.kernel = {"auto": 0, "block": 1, "warp": 2}.get(kernel, kernel)
+        o.accel = int(accel)
         return o
 
     def solve(self, allow_not_converged=False, **kw):

@@ -73,6 +73,10 @@ struct obte_ctx {
   void* src = nullptr;
   void* twc = nullptr;
   CGArgs* cg_job = nullptr;
+  int aa_m_alloc = -1;
+  double *aa_xd = nullptr, *aa_fd = nullptr, *aa_small = nullptr;
+  void *aa_xt = nullptr, *aa_ft = nullptr;
+  int* aa_int = nullptr;
   void* rec4 = nullptr;
   double* tlq = nullptr;
   double* Tw = nullptr;
@@ -137,6 +141,10 @@ struct obte_ctx {
     wall_side_d = nullptr;
     twc = nullptr;
     cg_job = nullptr;
+    aa_m_alloc = -1;
+    aa_xd = aa_fd = aa_small = nullptr;
+    aa_xt = aa_ft = nullptr;
+    aa_int = nullptr;
     rec4 = nullptr;
     tlq = nullptr;
     s_d = nullptr;
@@ -192,6 +200,8 @@ extern "C" void obte_default_opts(obte_solve_opts* o) {
   o->rows_per_thread = 0;
   o->use_graph = 1;
   o->profile = 0;
+  o->kernel = 0;
+  o->accel = 0;
 }
 
 extern "C" int obte_create(obte_ctx** out, const obte_device_cfg* cfg) {
@@ -694,6 +704,13 @@ static int prepare_state(obte_ctx* ctx, int precision, int G, int R, bool warp, 
     ctx->dfree(ctx->tlq);
     ctx->rec4 = nullptr;
     ctx->tlq = nullptr;
+    for (void* p : {(void*)ctx->aa_xd, (void*)ctx->aa_fd, ctx->aa_xt, ctx->aa_ft, (void*)ctx->aa_small,
+                    (void*)ctx->aa_int})
+      ctx->dfree(p);
+    ctx->aa_xd = ctx->aa_fd = ctx->aa_small = nullptr;
+    ctx->aa_xt = ctx->aa_ft = nullptr;
+    ctx->aa_int = nullptr;
+    ctx->aa_m_alloc = -1;
     for (void* p : {(void*)ctx->TL, (void*)ctx->TL_acc, ctx->src, ctx->twc, (void*)ctx->Tw, (void*)ctx->wall_acc,
                     ctx->front, (void*)ctx->scal, (void*)ctx->ctrl, (void*)ctx->hist, (void*)ctx->TF,
                     (void*)ctx->fwork, (void*)ctx->fiters, (void*)ctx->gd})
@@ -737,8 +754,46 @@ static int prepare_state(obte_ctx* ctx, int precision, int G, int R, bool warp, 
     NEED(ctx->tlq);
     CK(cudaMemsetAsync(ctx->tlq, 0, sizeof(double) * 4 * (size_t)ctx->n_cells, ctx->stream));
   }
+  const int aa_m = std::max(0, std::min(op.accel, 7));
+  const long aa_nd = (long)ctx->n_cells + ctx->n_walls;
+  const long aa_nt = (long)ctx->O * rows;
+  if (aa_m > 0 && ctx->aa_m_alloc != aa_m) {
+    for (void* p : {(void*)ctx->aa_xd, (void*)ctx->aa_fd, ctx->aa_xt, ctx->aa_ft, (void*)ctx->aa_small,
+                    (void*)ctx->aa_int})
+      ctx->dfree(p);
+    const size_t e = precision == 0 ? 8 : 4;
+    ctx->aa_xd = ctx->dalloc_t<double>((size_t)(aa_m + 1) * aa_nd);
+    ctx->aa_fd = ctx->dalloc_t<double>((size_t)(aa_m + 1) * aa_nd);
+    ctx->aa_xt = ctx->dalloc(e * (size_t)(aa_m + 1) * aa_nt);
+    ctx->aa_ft = ctx->dalloc(e * (size_t)(aa_m + 1) * aa_nt);
+    ctx->aa_small = ctx->dalloc_t<double>(8 + 64 + 8);
+    ctx->aa_int = ctx->dalloc_t<int>(2);
+    NEED(ctx->aa_xd);
+    NEED(ctx->aa_fd);
+    NEED(ctx->aa_xt);
+    NEED(ctx->aa_ft);
+    NEED(ctx->aa_small);
+    NEED(ctx->aa_int);
+    CK(cudaMemsetAsync(ctx->aa_small, 0, sizeof(double) * 80, ctx->stream));
+    CK(cudaMemsetAsync(ctx->aa_int, 0, sizeof(int) * 2, ctx->stream));
+    ctx->aa_m_alloc = aa_m;
+  }
   GeomDev& g = ctx->gh;
   std::memset(&g, 0, sizeof(g));
+  g.aa_m = aa_m;
+  if (aa_m > 0) {
+    g.aa_nd = aa_nd;
+    g.aa_nt = aa_nt;
+    g.aa_xd = ctx->aa_xd;
+    g.aa_fd = ctx->aa_fd;
+    g.aa_xt = ctx->aa_xt;
+    g.aa_ft = ctx->aa_ft;
+    g.aa_dots = ctx->aa_small;
+    g.aa_gram = ctx->aa_small + 8;
+    g.aa_coef = ctx->aa_small + 72;
+    g.aa_k = ctx->aa_int;
+    g.aa_count = reinterpret_cast<unsigned int*>(ctx->aa_int + 1);
+  }
   g.nx = Nx;
   g.ny = Ny;
   g.nz = Nz;
@@ -838,6 +893,11 @@ static cudaError_t sweep_once(obte_ctx* ctx, int flags) {
                       L.n_items, smem, ctx->stream);
 }
 
+static int aa_blocks(int n_cells, int n_ord, int rows) {
+  const long n = std::max((long)n_cells, (long)n_ord * rows);
+  return (int)std::max(1L, std::min((n + 255) / 256, 1216L));
+}
+
 static int finalize_blocks(int n_cells) {
   int b = (n_cells + 255) / 256;
   return std::max(1, std::min(b, 296));
@@ -861,6 +921,8 @@ static int init_from_fourier(obte_ctx* ctx, const obte_solve_opts& op, int* fite
   }
   CK(launch_init_state_oct(ctx->gd, ctx->gh, 0, ctx->TF, prec, ctx->octant_d, ctx->stream));
   if (ctx->warp) CK(launch_build_records(ctx->gd, 1, prec, finalize_blocks(ctx->n_cells), ctx->stream));
+  if (ctx->gh.aa_m > 0)
+    CK(launch_anderson_init(ctx->gd, 1, prec, aa_blocks(ctx->n_cells, ctx->O, ctx->n[1] * ctx->n[2]), ctx->stream));
   if (fiters_out) {
     CK(cudaMemcpyAsync(fiters_out, ctx->fiters, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
   }
@@ -981,6 +1043,11 @@ static int run_iterations(obte_ctx* ctx, const obte_solve_opts& op, int* iters, 
       if (op.profile && (e = cudaEventRecordWithFlags(ev[3 * i + 1], ctx->stream, cudaEventRecordExternal)) != cudaSuccess) return e;
       e = launch_finalize(ctx->gd, 1, ctx->precision, finalize_blocks(ctx->n_cells), ctx->stream);
       if (e != cudaSuccess) return e;
+      if (ctx->gh.aa_m > 0) {
+        e = launch_anderson_step(ctx->gd, 1, ctx->precision,
+                                 aa_blocks(ctx->n_cells, ctx->O, ctx->n[1] * ctx->n[2]), ctx->stream);
+        if (e != cudaSuccess) return e;
+      }
       if (ctx->warp) {
         e = launch_build_records(ctx->gd, 1, ctx->precision, finalize_blocks(ctx->n_cells), ctx->stream);
         if (e != cudaSuccess) return e;
@@ -1461,8 +1528,12 @@ extern "C" int obte_solve_batch(obte_ctx* const* ctxs, int n, const obte_solve_o
   const int blocks = v.warp ? (int)std::min<long>(((long)items.size() + kWarpsPerBlock - 1) / kWarpsPerBlock,
                                                   (long)sms * per_sm)
                             : (int)std::min<long>((long)items.size(), (long)sms * per_sm);
-  int max_cells = 0;
-  for (int i = 0; i < n; ++i) max_cells = std::max(max_cells, ctxs[i]->n_cells);
+  int max_cells = 0, max_ord = 0, max_rows = 0;
+  for (int i = 0; i < n; ++i) {
+    max_cells = std::max(max_cells, ctxs[i]->n_cells);
+    max_ord = std::max(max_ord, ctxs[i]->O);
+    max_rows = std::max(max_rows, ctxs[i]->n[1] * ctxs[i]->n[2]);
+  }
 
   cudaEvent_t e0, e1, e2;
   CK(cudaEventCreate(&e0));
@@ -1496,6 +1567,8 @@ extern "C" int obte_solve_batch(obte_ctx* const* ctxs, int n, const obte_solve_o
     obte_ctx* c = ctxs[i];
     cudaError_t e = launch_init_state_oct(gds, gh[i], i, c->TF, prec, c->octant_d, ctx->stream);
     if (e == cudaSuccess && v.warp) e = launch_build_records(gds + i, 1, prec, finalize_blocks(c->n_cells), ctx->stream);
+    if (e == cudaSuccess && gh[i].aa_m > 0)
+      e = launch_anderson_init(gds + i, 1, prec, aa_blocks(c->n_cells, c->O, c->n[1] * c->n[2]), ctx->stream);
     if (e != cudaSuccess) return ctx->cuda_fail(e, "batch init");
   }
   CK(cudaEventRecord(e1, ctx->stream));
@@ -1515,6 +1588,10 @@ extern "C" int obte_solve_batch(obte_ctx* const* ctxs, int n, const obte_solve_o
       if (e != cudaSuccess) return e;
       e = launch_finalize(gds, n, prec, finalize_blocks(max_cells), ctx->stream);
       if (e != cudaSuccess) return e;
+      if (op.accel > 0) {
+        e = launch_anderson_step(gds, n, prec, aa_blocks(max_cells, max_ord, max_rows), ctx->stream);
+        if (e != cudaSuccess) return e;
+      }
       if (v.warp) {
         e = launch_build_records(gds, n, prec, finalize_blocks(max_cells), ctx->stream);
         if (e != cudaSuccess) return e;

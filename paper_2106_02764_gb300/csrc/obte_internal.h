@@ -80,6 +80,18 @@ struct GeomDev {
   double tol, tol_TL;
   int min_iter, max_iter;
   unsigned int* fin_count;  // [1] blocks done in finalize (last-block pattern)
+  // Anderson acceleration (anderson.cu); aa_m = 0: plain source iteration
+  int aa_m;               // window (history slots aa_m + 1 <= 8)
+  long aa_nd, aa_nt;      // state lengths: FP64 part (T_L, T_w), row values
+  double* aa_xd;          // [(aa_m + 1) * aa_nd] iterates
+  double* aa_fd;          // [(aa_m + 1) * aa_nd] residuals
+  void* aa_xt;            // [(aa_m + 1) * aa_nt] iterates, sweep precision
+  void* aa_ft;            // [(aa_m + 1) * aa_nt] residuals, sweep precision
+  double* aa_dots;        // [8]
+  double* aa_gram;        // [(aa_m + 1)^2] residual Gram matrix by slot
+  double* aa_coef;        // [8] mixing coefficients
+  int* aa_k;              // [1] Anderson step
+  unsigned int* aa_count; // [1] last-block counter
   int* nonfinite;         // [1]
 };
 
@@ -115,6 +127,11 @@ int sweep_blocks_per_sm(int precision, int dim, int G, int RMAX, bool has_s, int
 // finalize.cu
 cudaError_t launch_finalize(const GeomDev* geoms_dev, int n_geoms, int precision, int blocks,
                             cudaStream_t st);
+// Anderson acceleration (anderson.cu)
+cudaError_t launch_anderson_init(const GeomDev* geoms_dev, int n_geoms, int precision, int blocks,
+                                 cudaStream_t st);
+cudaError_t launch_anderson_step(const GeomDev* geoms_dev, int n_geoms, int precision, int blocks,
+                                 cudaStream_t st);
 // rebuild the skewed records of the 2D warp kernel (after finalize / init)
 cudaError_t launch_build_records(const GeomDev* geoms_dev, int n_geoms, int precision, int blocks,
                                  cudaStream_t st);

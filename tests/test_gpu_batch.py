@@ -57,3 +57,15 @@ def test_batch_equals_single():
         one = Solver.from_workload(w)
         one.solve(precision="fp64", tol=1e-12, tol_TL=1e-13, max_iter=200000, allow_not_converged=True)
         assert abs(one.kappa_eff - s.kappa_eff) < 1e-10 * one.kappa_eff
+
+
+def test_batch_anderson():
+    from paper_2106_02764_gb300.binding import Solver, solve_batch
+    geoms = _geoms()
+    solvers = [Solver.from_workload(w) for w in geoms]
+    solve_batch(solvers, precision="fp64", tol=1e-12, tol_TL=1e-13, max_iter=200000, accel=5,
+                allow_not_converged=True)
+    for w, s in zip(geoms, solvers):
+        pr, ref = oracle(w)
+        assert abs(s.kappa_eff - ref.kappa) <= KAPPA_RTOL["fp64"] * ref.kappa
+        assert np.abs(solid_vector(pr, s.T_L()) - ref.T_L).max() <= TL_ATOL

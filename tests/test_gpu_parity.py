@@ -165,3 +165,16 @@ def test_iteration_cap_reports_not_converged():
         s.solve(precision="fp64", tol=1e-14, max_iter=3, check_every=1)
     assert e.value.code == OBTE_NOT_CONVERGED
     assert s.stats["iterations"] == 3 and np.isfinite(s.kappa_eff)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+@pytest.mark.parametrize("name", ["2d_circle_8", "2d_square_16", "3d_film", "2d_scatter", "2d_porefree"])
+def test_anderson_same_fixed_point(name, precision):
+    """Anderson mixing of (T_L, T_w, carried row values) reaches the oracle's
+    fixed point, in fewer iterations than the plain source iteration."""
+    wl, pr, ref = _ref(name, SMALL[name])
+    s, st = gpu(wl, precision, accel=5)
+    _check(wl, pr, ref, s, precision)
+    if precision == "fp64":
+        _, st0 = gpu(wl, precision)
+        assert st["iterations"] < st0["iterations"], (st["iterations"], st0["iterations"])
