@@ -88,8 +88,9 @@ typedef struct {
   int use_graph;        /* 1: capture check_every iterations in a CUDA graph   */
   int profile;          /* 1: time every sweep / finalize launch with CUDA
                            events recorded on the solve stream (stats below)   */
-  int kernel;           /* 0: automatic, 1: block kernel (every dimension),
-                           2: 2D warp-per-group kernel                          */
+  int kernel;           /* 0: automatic, 1: plain block kernel (every dimension),
+                           2: 2D warp-per-group kernel, 3: 3D block kernel
+                           with skewed cell records                            */
   int accel;            /* Anderson acceleration window (0: plain source
                            iteration as in Algorithm 1; 1..7: mix the last
                            accel iterates of (T_L, T_w, carried row values);
@@ -109,7 +110,8 @@ typedef struct {
   double time_total_ms;       /* device time of obte_solve                        */
   double updates_per_s;       /* N_solid * N_ordinates * iterations / time_iter   */
   int group_size, rows_per_thread, threads_per_block, n_groups;
-  int kernel;                 /* 1: block kernel, 2: 2D warp-per-group kernel       */
+  int kernel;                 /* 1: block kernel, 2: 2D warp-per-group kernel,
+                                 3: 3D block kernel with skewed cell records      */
   int n_sweeps;               /* sweep launches timed when opts.profile = 1       */
   double time_sweep_ms;       /* summed device time of those sweep launches       */
   double time_finalize_ms;    /* summed device time of the finalize launches      */

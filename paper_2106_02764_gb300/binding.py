@@ -231,7 +231,7 @@ class Solver:
         o.check_every, o.fourier_max_iter, o.fourier_tol = int(check_every), int(fourier_max_iter), float(fourier_tol)
         o.group_size, o.rows_per_thread, o.use_graph = int(group_size), int(rows_per_thread), int(bool(use_graph))
         o.profile = int(bool(profile))
-        o.kernel = {"auto": 0, "block": 1, "warp": 2}.get(kernel, kernel)
+        o.kernel = {"auto": 0, "block": 1, "warp": 2, "block3d": 3}.get(kernel, kernel)
         o.accel = int(accel)
         return o
 

@@ -74,6 +74,7 @@ struct obte_ctx {
   void* twc = nullptr;
   CGArgs* cg_job = nullptr;
   int aa_m_alloc = -1;
+  int rec_w_alloc = 0;
   double *aa_xd = nullptr, *aa_fd = nullptr, *aa_small = nullptr;
   void *aa_xt = nullptr, *aa_ft = nullptr;
   int* aa_int = nullptr;
@@ -94,6 +95,7 @@ struct obte_ctx {
   bool flux_done = false;
   int G = 0, R = 0, threads = 0;
   bool warp = false;
+  bool k3d = false;
   std::vector<WorkItem> items_h;
   WorkItem* items_d = nullptr;
   double kappa = NAN;
@@ -142,6 +144,7 @@ struct obte_ctx {
     twc = nullptr;
     cg_job = nullptr;
     aa_m_alloc = -1;
+    rec_w_alloc = 0;
     aa_xd = aa_fd = aa_small = nullptr;
     aa_xt = aa_ft = nullptr;
     aa_int = nullptr;
@@ -604,7 +607,8 @@ namespace {
 
 struct Variant {
   int G, R;
-  bool warp;  // 2D warp-per-group kernel (sweep2d.cuh) instead of the block kernel
+  bool warp;         // 2D warp-per-group kernel (sweep2d.cuh)
+  bool k3d = false;  // 3D block kernel with skewed records (sweep3d.cuh)
 };
 
 const Variant kWarp2D_F[] = {{8, 8, true}, {8, 4, true}, {16, 4, true},
@@ -614,9 +618,12 @@ const Variant kVariants2D_F[] = {{16, 4, false}, {8, 4, false}, {8, 8, false}, {
                                  {8, 2, false}, {4, 4, false}, {16, 1, false}};
 const Variant kVariants2D_D[] = {{8, 2, false}, {8, 4, false}, {4, 4, false}, {4, 8, false},
                                  {8, 1, false}};
-const Variant kVariants3D_F[] = {{8, 8, false}, {4, 8, false}, {8, 4, false}, {4, 4, false},
+const Variant kVariants3D_F[] = {{8, 8, false, true}, {4, 8, false, true}, {8, 4, false, true},
+                                 {4, 4, false, true}, {8, 2, false, true},
+                                 {8, 8, false}, {4, 8, false}, {8, 4, false}, {4, 4, false},
                                  {8, 2, false}, {4, 2, false}};
-const Variant kVariants3D_D[] = {{4, 8, false}, {4, 4, false}, {4, 2, false}, {8, 2, false}};
+const Variant kVariants3D_D[] = {{4, 8, false, true}, {4, 4, false, true}, {2, 4, false, true},
+                                 {4, 8, false}, {4, 4, false}, {4, 2, false}, {8, 2, false}};
 
 int threads_for(int ny, int nz, int R) {
   const int tpp = (ny + R - 1) / R;
@@ -632,6 +639,11 @@ void push_fitting(std::vector<Variant>& out, const Variant (&v)[N], int precisio
     if (v[i].warp) {
       if (dim != 2 || ny / v[i].R > 32) continue;
       if (!sweep2d_warp_exists(precision, v[i].G, v[i].R, has_s, true)) continue;
+    } else if (v[i].k3d) {
+      const int thr = threads_for(ny, nz, v[i].R);
+      if (dim != 3 || thr > (v[i].R >= 8 ? 256 : 512)) continue;
+      if (sweep3d_smem_bytes(precision, v[i].G, v[i].R, thr) > 200 * 1024) continue;
+      if (!sweep3d_exists(precision, v[i].G, v[i].R, has_s)) continue;
     } else {
       const int thr = threads_for(ny, nz, v[i].R);
       if (thr > ((dim == 3 && v[i].R < 8) ? 512 : 256)) continue;  // the kernel's launch bound
@@ -693,7 +705,7 @@ static void build_items(obte_ctx* ctx, int geom, int G, std::vector<WorkItem>& i
 
 // allocate the iteration state for a precision / variant; fill gh and gd
 static int prepare_state(obte_ctx* ctx, int precision, int G, int R, bool warp, int max_iter,
-                         const obte_solve_opts& op) {
+                         const obte_solve_opts& op, bool k3d = false) {
   cudaSetDevice(ctx->device);
   const int Nx = ctx->n[0], Ny = ctx->n[1], Nz = ctx->n[2];
   const int rows = Ny * Nz;
@@ -704,6 +716,7 @@ static int prepare_state(obte_ctx* ctx, int precision, int G, int R, bool warp, 
     ctx->dfree(ctx->tlq);
     ctx->rec4 = nullptr;
     ctx->tlq = nullptr;
+    ctx->rec_w_alloc = 0;
     for (void* p : {(void*)ctx->aa_xd, (void*)ctx->aa_fd, ctx->aa_xt, ctx->aa_ft, (void*)ctx->aa_small,
                     (void*)ctx->aa_int})
       ctx->dfree(p);
@@ -746,13 +759,18 @@ static int prepare_state(obte_ctx* ctx, int precision, int G, int R, bool warp, 
     NEED(ctx->gd);
     ctx->precision = precision;
   }
-  if (warp && !ctx->rec4) {
+  const int nq = ctx->dim == 3 ? 8 : 4;          // octants
+  const int rec_w = k3d ? 8 : (warp ? 4 : 0);     // values per skewed record
+  if (rec_w && ctx->rec_w_alloc != rec_w) {
+    ctx->dfree(ctx->rec4);
+    ctx->dfree(ctx->tlq);
     const size_t e = precision == 0 ? 8 : 4;
-    ctx->rec4 = ctx->dalloc(4 * e * 4 * (size_t)ctx->n_cells);
-    ctx->tlq = ctx->dalloc_t<double>(4 * (size_t)ctx->n_cells);
+    ctx->rec4 = ctx->dalloc((size_t)nq * rec_w * e * (size_t)ctx->n_cells);
+    ctx->tlq = ctx->dalloc_t<double>((size_t)nq * ctx->n_cells);
     NEED(ctx->rec4);
     NEED(ctx->tlq);
-    CK(cudaMemsetAsync(ctx->tlq, 0, sizeof(double) * 4 * (size_t)ctx->n_cells, ctx->stream));
+    CK(cudaMemsetAsync(ctx->tlq, 0, sizeof(double) * nq * (size_t)ctx->n_cells, ctx->stream));
+    ctx->rec_w_alloc = rec_w;
   }
   const int aa_m = std::max(0, std::min(op.accel, 7));
   const long aa_nd = (long)ctx->n_cells + ctx->n_walls;
@@ -820,8 +838,9 @@ static int prepare_state(obte_ctx* ctx, int precision, int G, int R, bool warp, 
   g.wall_cell = ctx->wall_cell_d;
   g.wall_side = ctx->wall_side_d;
   g.twc = ctx->twc;
-  g.rec4 = warp ? ctx->rec4 : nullptr;
-  g.tlq = warp ? ctx->tlq : nullptr;
+  g.rec4 = rec_w ? ctx->rec4 : nullptr;
+  g.tlq = rec_w ? ctx->tlq : nullptr;
+  g.rec_w = rec_w;
   g.front = ctx->front;
   g.phi_acc = ctx->scal;
   g.delta_max = ctx->scal + 1;
@@ -855,6 +874,7 @@ static int prepare_state(obte_ctx* ctx, int precision, int G, int R, bool warp, 
   ctx->G = G;
   ctx->R = R;
   ctx->warp = warp;
+  ctx->k3d = k3d;
   ctx->threads = warp ? 32 * kWarpsPerBlock : threads_for(Ny, Nz, R);
   std::vector<WorkItem> items;
   std::vector<int> ord_d0;
@@ -888,6 +908,9 @@ static cudaError_t sweep_once(obte_ctx* ctx, int flags) {
   L.item_counter = nullptr;
   if (ctx->warp)
     return launch_sweep2d_warp(L, ctx->precision, ctx->G, ctx->R, ctx->has_s, true, 0, ctx->stream);
+  if (ctx->k3d)
+    return launch_sweep3d(L, ctx->precision, ctx->G, ctx->R, ctx->has_s, ctx->threads,
+                          sweep3d_smem_bytes(ctx->precision, ctx->G, ctx->R, ctx->threads), ctx->stream);
   const size_t smem = sweep_smem_bytes(ctx->precision, ctx->dim, ctx->G, ctx->R, ctx->threads);
   return launch_sweep(L, ctx->precision, ctx->dim, ctx->G, ctx->R, ctx->has_s, ctx->threads,
                       L.n_items, smem, ctx->stream);
@@ -920,7 +943,7 @@ static int init_from_fourier(obte_ctx* ctx, const obte_solve_opts& op, int* fite
                          ctx->fiters, ctx->fwork, kFourierBlocksMax, ctx->stream));
   }
   CK(launch_init_state_oct(ctx->gd, ctx->gh, 0, ctx->TF, prec, ctx->octant_d, ctx->stream));
-  if (ctx->warp) CK(launch_build_records(ctx->gd, 1, prec, finalize_blocks(ctx->n_cells), ctx->stream));
+  if (ctx->warp || ctx->k3d) CK(launch_build_records(ctx->gd, 1, prec, finalize_blocks(ctx->n_cells), ctx->stream));
   if (ctx->gh.aa_m > 0)
     CK(launch_anderson_init(ctx->gd, 1, prec, aa_blocks(ctx->n_cells, ctx->O, ctx->n[1] * ctx->n[2]), ctx->stream));
   if (fiters_out) {
@@ -933,9 +956,10 @@ static std::vector<Variant> filtered_candidates(obte_ctx* ctx, int precision,
                                                 const obte_solve_opts& op) {
   std::vector<Variant> out;
   for (auto& c : candidates(precision, ctx->dim, ctx->n[1], ctx->n[2], ctx->has_s)) {
-    if (op.kernel == 1 && c.warp) continue;
-    if (c.warp && ctx->n_cells > kMaxSkewCells) continue;  // packed cell index is 22 bits
+    if ((c.warp || c.k3d) && ctx->n_cells > kMaxSkewCells) continue;  // packed cell index is 22 bits
+    if (op.kernel == 1 && (c.warp || c.k3d)) continue;
     if (op.kernel == 2 && !c.warp) continue;
+    if (op.kernel == 3 && !c.k3d) continue;
     if (op.group_size > 0 && c.G != op.group_size) continue;
     if (op.rows_per_thread > 0 && c.R != op.rows_per_thread) continue;
     out.push_back(c);
@@ -981,7 +1005,7 @@ static int autotune(obte_ctx* ctx, int precision, const obte_solve_opts& op, Var
   float best = 1e30f;
   Variant bv = cands[0];
   for (auto& c : cands) {
-    int rc = prepare_state(ctx, precision, c.G, c.R, c.warp, 1 << 30, op);
+    int rc = prepare_state(ctx, precision, c.G, c.R, c.warp, 1 << 30, op, c.k3d);
     if (rc) return rc;
     obte_solve_opts o2 = op;
     o2.fourier_max_iter = 1;
@@ -1048,7 +1072,7 @@ static int run_iterations(obte_ctx* ctx, const obte_solve_opts& op, int* iters, 
                                  aa_blocks(ctx->n_cells, ctx->O, ctx->n[1] * ctx->n[2]), ctx->stream);
         if (e != cudaSuccess) return e;
       }
-      if (ctx->warp) {
+      if (ctx->warp || ctx->k3d) {
         e = launch_build_records(ctx->gd, 1, ctx->precision, finalize_blocks(ctx->n_cells), ctx->stream);
         if (e != cudaSuccess) return e;
       }
@@ -1131,7 +1155,7 @@ extern "C" int obte_solve(obte_ctx* ctx, const obte_solve_opts* opts, obte_solve
   Variant v;
   int rc = (op.group_size < 0) ? autotune(ctx, prec, op, &v) : pick_variant(ctx, prec, op, &v);
   if (rc) return rc;
-  rc = prepare_state(ctx, prec, v.G, v.R, v.warp, op.max_iter, op);
+  rc = prepare_state(ctx, prec, v.G, v.R, v.warp, op.max_iter, op, v.k3d);
   if (rc) return rc;
   ctx->flux_done = false;
   cudaEvent_t e0, e1, e2;
@@ -1185,7 +1209,7 @@ extern "C" int obte_solve(obte_ctx* ctx, const obte_solve_opts* opts, obte_solve
     stats->group_size = ctx->G;
     stats->rows_per_thread = ctx->R;
     stats->threads_per_block = ctx->threads;
-    stats->kernel = ctx->warp ? 2 : 1;
+    stats->kernel = ctx->warp ? 2 : (ctx->k3d ? 3 : 1);
     stats->n_groups = (int)ctx->items_h.size();
     stats->n_history = (int)hist.size();
     for (size_t i = 0; i < hist.size(); ++i) stats->kappa_history[i] = hist[i];
@@ -1256,7 +1280,7 @@ static int run_flux_pass(obte_ctx* ctx) {
   CK(sweep_once(ctx, SWEEP_FLUX));
   // the pass does not advance the iterate: drop its moment accumulations
   CK(cudaMemsetAsync(ctx->TL_acc, 0, sizeof(double) * ctx->n_cells, ctx->stream));
-  if (ctx->tlq) CK(cudaMemsetAsync(ctx->tlq, 0, sizeof(double) * 4 * (size_t)ctx->n_cells, ctx->stream));
+  if (ctx->tlq) CK(cudaMemsetAsync(ctx->tlq, 0, sizeof(double) * (ctx->dim == 3 ? 8 : 4) * (size_t)ctx->n_cells, ctx->stream));
   CK(cudaMemsetAsync(ctx->wall_acc, 0, sizeof(double) * std::max(1, ctx->n_walls), ctx->stream));
   CK(cudaMemsetAsync(ctx->scal, 0, sizeof(double), ctx->stream));
   int one = 1;
@@ -1411,6 +1435,9 @@ extern "C" int obte_kappa_grad_s(obte_ctx* ctx, double* out, size_t max_field_by
     L.item_counter = nullptr;
     if (ctx->warp) {
       CK(launch_sweep2d_warp(L, ctx->precision, ctx->G, ctx->R, ctx->has_s, true, 0, ctx->stream));
+    } else if (ctx->k3d) {
+      CK(launch_sweep3d(L, ctx->precision, ctx->G, ctx->R, ctx->has_s, ctx->threads,
+                        sweep3d_smem_bytes(ctx->precision, ctx->G, ctx->R, ctx->threads), ctx->stream));
     } else {
       const size_t smem = sweep_smem_bytes(ctx->precision, ctx->dim, ctx->G, ctx->R, ctx->threads);
       CK(launch_sweep(L, ctx->precision, ctx->dim, ctx->G, ctx->R, ctx->has_s, ctx->threads,
@@ -1419,7 +1446,7 @@ extern "C" int obte_kappa_grad_s(obte_ctx* ctx, double* out, size_t max_field_by
     CK(launch_grad_contract2(ctx->code_d, ctx->TL, ctx->n_cells, rec, (int)b.size(), revl_d, a_d,
                              jscale, grad_d, ctx->precision, ctx->stream));
     CK(cudaMemsetAsync(ctx->TL_acc, 0, sizeof(double) * ctx->n_cells, ctx->stream));
-    if (ctx->tlq) CK(cudaMemsetAsync(ctx->tlq, 0, sizeof(double) * 4 * (size_t)ctx->n_cells, ctx->stream));
+    if (ctx->tlq) CK(cudaMemsetAsync(ctx->tlq, 0, sizeof(double) * (ctx->dim == 3 ? 8 : 4) * (size_t)ctx->n_cells, ctx->stream));
     CK(cudaMemsetAsync(ctx->wall_acc, 0, sizeof(double) * std::max(1, ctx->n_walls), ctx->stream));
     CK(cudaMemsetAsync(ctx->scal, 0, sizeof(double), ctx->stream));
     CK(cudaStreamSynchronize(ctx->stream));
@@ -1483,7 +1510,7 @@ extern "C" int obte_solve_batch(obte_ctx* const* ctxs, int n, const obte_solve_o
   if (!use_warp) {
     std::vector<Variant> common;
     for (auto& c : candidates(prec, ctx->dim, max_ny, max_nz, any_s)) {
-      if (c.warp) continue;
+      if (c.warp || c.k3d) continue;  // batches of 3D meshes use the plain block kernel
       bool ok = true;
       for (int i = 0; i < n; ++i)
         if (ctxs[i]->n[1] % c.R != 0) ok = false;
@@ -1844,6 +1871,9 @@ extern "C" int obte_kappa_grad_s_noalloc(obte_ctx* ctx, double* out) {
     L.item_counter = nullptr;
     if (ctx->warp) {
       CK(launch_sweep2d_warp(L, ctx->precision, ctx->G, ctx->R, ctx->has_s, true, 0, ctx->stream));
+    } else if (ctx->k3d) {
+      CK(launch_sweep3d(L, ctx->precision, ctx->G, ctx->R, ctx->has_s, ctx->threads,
+                        sweep3d_smem_bytes(ctx->precision, ctx->G, ctx->R, ctx->threads), ctx->stream));
     } else {
       const size_t smem = sweep_smem_bytes(ctx->precision, ctx->dim, ctx->G, ctx->R, ctx->threads);
       CK(launch_sweep(L, ctx->precision, ctx->dim, ctx->G, ctx->R, ctx->has_s, ctx->threads,
@@ -1852,7 +1882,7 @@ extern "C" int obte_kappa_grad_s_noalloc(obte_ctx* ctx, double* out) {
     CK(launch_grad_contract2(ctx->code_d, ctx->TL, ctx->n_cells, rec, (int)b.size(), revl_d, a_d,
                              jscale, grad_d, ctx->precision, ctx->stream));
     CK(cudaMemsetAsync(ctx->TL_acc, 0, sizeof(double) * ctx->n_cells, ctx->stream));
-    if (ctx->tlq) CK(cudaMemsetAsync(ctx->tlq, 0, sizeof(double) * 4 * (size_t)ctx->n_cells, ctx->stream));
+    if (ctx->tlq) CK(cudaMemsetAsync(ctx->tlq, 0, sizeof(double) * (ctx->dim == 3 ? 8 : 4) * (size_t)ctx->n_cells, ctx->stream));
     CK(cudaMemsetAsync(ctx->wall_acc, 0, sizeof(double) * std::max(1, ctx->n_walls), ctx->stream));
     CK(cudaMemsetAsync(ctx->scal, 0, sizeof(double), ctx->stream));
     CK(cudaStreamSynchronize(ctx->stream));  // host vectors above are copy sources

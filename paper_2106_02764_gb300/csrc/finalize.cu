@@ -33,13 +33,15 @@ __global__ void finalize_kernel(const GeomDev* geoms) {
   for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < g.n_cells; c += stride) {
     if (!(g.code[c] & CODE_SOLID)) continue;
     double t;
-    if (g.tlq) {  // 2D warp kernel: four skewed quadrant accumulators
-      const int x = c % g.nx, y = c / g.nx;
+    if (g.tlq) {  // skewed per-octant accumulators (2D warp and 3D kernels)
+      const int x = c % g.nx, y = (c / g.nx) % g.ny, z = c / (g.nx * g.ny);
+      const int nq = g.dim == 3 ? 8 : 4;
       t = 0.0;
-      for (int q = 0; q < 4; ++q) {
+      for (int q = 0; q < nq; ++q) {
         const int ip = (q & 1) ? g.nx - 1 - x : x;
         const int jp = (q & 2) ? g.ny - 1 - y : y;
-        const size_t k = ((size_t)q * g.nx + (ip + jp) % g.nx) * g.ny + jp;
+        const int kp = (q & 4) ? g.nz - 1 - z : z;
+        const size_t k = ((size_t)q * g.nx + (ip + jp + kp) % g.nx) * g.rows + jp + (size_t)g.ny * kp;
         t += g.tlq[k];
         g.tlq[k] = 0.0;
       }
@@ -218,21 +220,30 @@ __global__ void build_records_kernel(const GeomDev* geoms) {
   T* rec = reinterpret_cast<T*>(g.rec4);
   const int stride = gridDim.x * blockDim.x;
   for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < g.n_cells; c += stride) {
-    const int x = c % g.nx, y = c / g.nx;
+    const int x = c % g.nx, y = (c / g.nx) % g.ny, z = c / (g.nx * g.ny);
     const uint32_t code = g.code[c];
-    for (int q = 0; q < 4; ++q) {
+    const int nq = g.dim == 3 ? 8 : 4;
+    for (int q = 0; q < nq; ++q) {
       const int ip = (q & 1) ? g.nx - 1 - x : x;
       const int jp = (q & 2) ? g.ny - 1 - y : y;
-      const size_t k = ((size_t)q * g.nx + (ip + jp) % g.nx) * g.ny + jp;
+      const int kp = (q & 4) ? g.nz - 1 - z : z;
+      const size_t k = ((size_t)q * g.nx + (ip + jp + kp) % g.nx) * g.rows + jp + (size_t)g.ny * kp;
       const uint32_t packed = (uint32_t)c | (code << 22) | ((ip == 0 ? 1u : 0u) << 30) |
                               ((ip == g.nx - 1 ? 1u : 0u) << 31);
-      const int sx_in = (q & 1) ? 1 : 0, sy_in = (q & 2) ? 3 : 2;
-      T* r = rec + 4 * k;
+      T* r = rec + (size_t)g.rec_w * k;
+      const T pk = sizeof(T) == 4 ? (T)__uint_as_float(packed) : (T)__longlong_as_double((long long)packed);
       r[0] = src[c];
-      r[1] = twc[(size_t)c * 6 + sx_in];
-      r[2] = twc[(size_t)c * 6 + sy_in];
-      if (sizeof(T) == 4) r[3] = (T)__uint_as_float(packed);
-      else r[3] = (T)__longlong_as_double((long long)packed);
+      r[1] = twc[(size_t)c * 6 + ((q & 1) ? 1 : 0)];
+      r[2] = twc[(size_t)c * 6 + ((q & 2) ? 3 : 2)];
+      if (g.rec_w == 4) {
+        r[3] = pk;
+      } else {
+        r[3] = twc[(size_t)c * 6 + ((q & 4) ? 5 : 4)];
+        r[4] = pk;
+        r[5] = T(0);
+        r[6] = T(0);
+        r[7] = T(0);
+      }
     }
   }
 }

@@ -50,13 +50,17 @@ struct GeomDev {
   const int* wall_cell;   // [n_walls]
   const int* wall_side;   // [n_walls] side of its cell (0..5: -x +x -y +y -z +z)
   void* twc;              // [n_cells * 6] wall temperature seen through each side, sweep precision
-  // 2D warp kernel: per-quadrant skewed cell records and T_L accumulators.
-  // Quadrant q's cell (i', j') (mirrored frame) sits at diagonal s = (i' + j') mod nx:
-  //   rec4[(q * nx + s) * ny + j']  = {s_i T_L,i, T_w in-x side, T_w in-y side, packed}
+  // Skewed cell records and T_L accumulators of the 2D warp and 3D kernels.
+  // Octant q's cell (i', j', k') (mirrored frame) has row = j' + ny k' and sits
+  // at diagonal s = (i' + j' + k') mod nx:
+  //   rec4[((q * nx + s) * rows + row) * rec_w + f]: rec_w = 4 (2D warp kernel)
+  //     {s_i T_L,i, T_w in-x side, T_w in-y side, packed};  rec_w = 8 (3D)
+  //     {s_i T_L,i, T_w in-x, in-y, in-z sides, packed, 0, 0, 0}
   //   packed = cell (bits 0-21) | code << 22 | [i' == 0] << 30 | [i' == nx-1] << 31
-  //   tlq[(q * nx + s) * ny + j']   = sum_o a_o T_o of the running sweep (FP64)
+  //   tlq[(q * nx + s) * rows + row] = sum_o a_o T_o of the running sweep (FP64)
   void* rec4;
   double* tlq;
+  int rec_w;              // values per record: 4 (2D warp kernel), 8 (3D kernel); 0: none
   void* front;            // [n_ord][rows] row values carried between iterations
   double* phi_acc;        // [1] hot-face flux of the running sweep
   // flux pass outputs
@@ -116,6 +120,11 @@ struct SweepLaunch {
 cudaError_t launch_sweep2d_warp(const SweepLaunch& L, int precision, int G, int RMAX, bool has_s,
                                 bool rfixed, int blocks, cudaStream_t st);
 bool sweep2d_warp_exists(int precision, int G, int RMAX, bool has_s, bool rfixed);
+// 3D block kernel (sweep3d.cuh)
+cudaError_t launch_sweep3d(const SweepLaunch& L, int precision, int G, int RMAX, bool has_s,
+                           int threads, size_t smem, cudaStream_t st);
+bool sweep3d_exists(int precision, int G, int RMAX, bool has_s);
+size_t sweep3d_smem_bytes(int precision, int G, int RMAX, int threads);
 constexpr int kWarpsPerBlock = 4;
 cudaError_t launch_sweep(const SweepLaunch& L, int precision, int dim, int G, int RMAX,
                          bool has_s, int threads, int blocks, size_t smem, cudaStream_t st);

@@ -1,6 +1,7 @@
 // Dispatch to the compiled sweep kernel variants (sweep_variants.h).
 #include "sweep_variants.h"
 #include "sweep2d_variants.h"
+#include "sweep3d_variants.h"
 
 static int prec_of(float*) { return 1; }
 static int prec_of(double*) { return 0; }
@@ -63,4 +64,29 @@ bool sweep2d_warp_exists(int precision, int G, int RMAX, bool has_s, bool rfixed
   OBTE_SWEEP2D_VARIANTS(X)
 #undef X
   return false;
+}
+
+#define OBTE_MATCH3D(T, GG, RR, SS) \
+  (precision == prec_of((T*)nullptr) && G == GG && RMAX == RR && has_s == SS)
+
+cudaError_t launch_sweep3d(const SweepLaunch& L, int precision, int G, int RMAX, bool has_s,
+                           int threads, size_t smem, cudaStream_t st) {
+#define X(T, GG, RR, SS) \
+  if (OBTE_MATCH3D(T, GG, RR, SS)) return OBTE_SWEEP3D_NAME(T, GG, RR, SS)(&L, threads, smem, st);
+  OBTE_SWEEP3D_VARIANTS(X)
+#undef X
+  return cudaErrorInvalidValue;
+}
+
+bool sweep3d_exists(int precision, int G, int RMAX, bool has_s) {
+#define X(T, GG, RR, SS) \
+  if (OBTE_MATCH3D(T, GG, RR, SS)) return true;
+  OBTE_SWEEP3D_VARIANTS(X)
+#undef X
+  return false;
+}
+
+size_t sweep3d_smem_bytes(int precision, int G, int RMAX, int threads) {
+  const size_t e = precision == 0 ? sizeof(double) : sizeof(float);
+  return (2 * (size_t)RMAX + 1) * G * threads * e;  // exchange [2][R][G][threads] + scratch [G][threads]
 }

@@ -1,0 +1,279 @@
+// 3D upwind transport sweep, one ordinate group per thread block (Eq. iter2 of
+// App. A, one source-iteration pass of Algorithm 1), moments fused.
+//
+// Wavefront as in sweep.cuh: in the frame mirrored per octant, row (j', k')
+// visits column i' = (d + d0 - j' - k') mod nx at step d; the x neighbour is
+// the row's own previous value, the y and z neighbours are the rows below one
+// step earlier.  Thread t owns R consecutive rows j' of plane k' = t / tpp and
+// keeps their values for the G ordinates of the group in registers; rows are
+// updated top-down inside a step, so the row below in y still holds its
+// previous-step value.  At the end of every step each thread publishes its
+// R x G values to shared memory, laid out [row][ordinate][thread] so that
+// neighbouring threads touch neighbouring banks; after one barrier the thread
+// above in z (and, for the lowest row, the thread above in y) reads them.
+//
+// Data layout.  All cells visited at step d lie on one diagonal
+// s = (i' + j' + k') mod nx = (d + d0) mod nx of the octant frame, so the
+// finalisation stores every cell's record {s T_L, T_w through the upwind x,
+// y and z sides, packed cell / code / column flags} per octant at
+// [s][j' + ny k']: a thread's rows of one step are contiguous records, loaded
+// one step ahead into registers.  The T_L moment goes to per-octant FP64
+// accumulators in the same layout; the finalisation sums the octants.
+//
+// Cells update branch-free (pore values never reach a solid cell, whose faces
+// towards a pore are walls); atomics and the rare epilogue (walls the
+// ordinates leave into, the hot-contact column, flux / record passes; sums in
+// the sweep precision, widened exactly) are predicated on solid cells.
+#pragma once
+
+#include "sweep.cuh"
+
+namespace obte {
+
+template <typename T>
+__device__ __forceinline__ uint32_t rec3_bits(T v);
+template <>
+__device__ __forceinline__ uint32_t rec3_bits<float>(float v) { return __float_as_uint(v); }
+template <>
+__device__ __forceinline__ uint32_t rec3_bits<double>(double v) { return (uint32_t)__double_as_longlong(v); }
+
+// Rare per-cell epilogue (3D); the cell's G values are at val[g * stride].
+template <typename T, int G>
+__device__ __noinline__ double cell_epilogue_3d(const GeomDev& gm, const T* val, int stride, int cell,
+                                                uint32_t code, bool last, int o0, int cnt, int sx,
+                                                int sy, int sz, int flags, double kx_sum) {
+  const int nx = gm.nx;
+  const double dT = gm.dT;
+  const uint32_t out_x_bit = sx > 0 ? CODE_WALL_XP : CODE_WALL_XM;
+  const uint32_t out_y_bit = sy > 0 ? CODE_WALL_YP : CODE_WALL_YM;
+  const uint32_t out_z_bit = sz > 0 ? CODE_WALL_ZP : CODE_WALL_ZM;
+  T sxk = T(0), syk = T(0), szk = T(0);
+  for (int g = 0; g < cnt; ++g) {
+    const T v = val[g * stride];
+    sxk = fma(ld<T>(gm.kxa, o0 + g), v, sxk);
+    syk = fma(ld<T>(gm.kya, o0 + g), v, syk);
+    szk = fma(ld<T>(gm.kza, o0 + g), v, szk);
+  }
+  const double dx = widen(sxk), dy = widen(syk), dz = widen(szk);
+  if (code & out_x_bit) atomicAdd(gm.wall_acc + gm.wall_id[cell * 6 + (sx > 0 ? 1 : 0)], dx);
+  if (code & out_y_bit) atomicAdd(gm.wall_acc + gm.wall_id[cell * 6 + (sy > 0 ? 3 : 2)], dy);
+  if (code & out_z_bit) atomicAdd(gm.wall_acc + gm.wall_id[cell * 6 + (sz > 0 ? 5 : 4)], dz);
+  const bool hot = last && !(code & out_x_bit);
+  double phi = 0.0;
+  if (hot) phi = (sx > 0 ? dx : -dx) + (sx > 0 ? dT * kx_sum : 0.0);
+  if (flags & SWEEP_FLUX) {
+    const int x = cell % nx;
+    atomicAdd(gm.J_acc + 3 * cell + 0, sx > 0 ? dx : -dx);
+    atomicAdd(gm.J_acc + 3 * cell + 1, sy > 0 ? dy : -dy);
+    atomicAdd(gm.J_acc + 3 * cell + 2, sz > 0 ? dz : -dz);
+    if (!(code & out_x_bit)) {
+      const int sec = sx > 0 ? (x + 1) % nx : x;
+      const bool jmp = sx > 0 && x == nx - 1;
+      atomicAdd(gm.phi_sec + sec, (sx > 0 ? dx : -dx) + (jmp ? dT * kx_sum : 0.0));
+    }
+    if (hot)
+      for (int g = 0; g < cnt; ++g) {
+        const double k = (double)sx * (double)ld<T>(gm.kxa, o0 + g);
+        atomicAdd(gm.phi_bin + gm.mbin[o0 + g], k * ((double)val[g * stride] + (sx > 0 ? dT : 0.0)));
+      }
+  }
+  if (flags & SWEEP_RECORD) {
+    T* rec = reinterpret_cast<T*>(gm.rec);
+    for (int g = 0; g < cnt; ++g) {
+      const int sl = gm.rec_slot[o0 + g];
+      if (sl >= 0) rec[(size_t)sl * gm.n_cells + cell] = val[g * stride];
+    }
+  }
+  return phi;
+}
+
+template <typename T, int G, int RMAX, bool HAS_S>
+__global__ void __launch_bounds__(RMAX >= 8 ? 256 : 512, 1) sweep3d_kernel(const SweepLaunch L) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ double red[32];
+  const int nthr = blockDim.x;
+  const int t = threadIdx.x;
+  T* xall = reinterpret_cast<T*>(smem_raw);  // [2][RMAX][G][nthr]
+  T* scratch = xall + 2 * RMAX * G * nthr;   // [G][nthr]
+  const int flags = L.flags;
+  const bool rare_pass = (flags & (SWEEP_FLUX | SWEEP_RECORD)) != 0;
+  auto XA = [&](int b, int r, int g, int th) -> T& { return xall[((b * RMAX + r) * G + g) * nthr + th]; };
+
+  const int item = blockIdx.x;
+  if (item >= L.n_items) return;
+  const WorkItem wi = L.items[item];
+  const GeomDev& gm = L.geoms[wi.geom];
+  if (*(volatile const int*)gm.done) return;
+  const int nx = gm.nx, ny = gm.ny, nz = gm.nz, tpp = gm.tpp;
+  const int rows = gm.rows;
+  const int q = wi.octant & 7;
+  const int sx = (q & 1) ? -1 : 1;
+  const int sy = (q & 2) ? -1 : 1;
+  const int sz = (q & 4) ? -1 : 1;
+  const int o0 = wi.o0, cnt = wi.count, d0 = wi.d0;
+  const double dT = gm.dT;
+  const int jb = t % tpp, kp = t / tpp;
+  const int j0 = jb * RMAX;
+  const bool active = kp < nz;
+  const int row0 = j0 + ny * kp;
+  const T* __restrict__ recq = reinterpret_cast<const T*>(gm.rec4) + (size_t)q * nx * rows * 8;
+  double* tlq = gm.tlq + (size_t)q * nx * rows;
+  const double* __restrict__ sv_ptr = gm.s;
+
+  T A0[G], AX[G], AY[G], AZ[G], AW[G], JX[G];
+  double kx_sum = 0.0;
+#pragma unroll
+  for (int g = 0; g < G; ++g) {
+    const bool ok = g < cnt;
+    const int o = o0 + (ok ? g : 0);
+    const double a0 = ok ? (double)ld<T>(HAS_S ? gm.diag : gm.inv, o) : 0.0;
+    double ax = ok ? (double)ld<T>(gm.bx, o) : 0.0;
+    double ay = ok ? (double)ld<T>(gm.by, o) : 0.0;
+    double az = ok ? (double)ld<T>(gm.bz, o) : 0.0;
+    if (!HAS_S) {
+      ax *= a0;
+      ay *= a0;
+      az *= a0;
+    }
+    A0[g] = (T)a0;
+    AX[g] = (T)ax;
+    AY[g] = (T)ay;
+    AZ[g] = (T)az;
+    AW[g] = ok ? ld<T>(gm.aw, o) : T(0);
+    JX[g] = (T)(ax * (double)sx * dT);
+    if (ok) kx_sum += (double)sx * (double)ld<T>(gm.kxa, o);
+  }
+
+  T v[RMAX][G];
+  const T* front = reinterpret_cast<const T*>(gm.front);
+#pragma unroll
+  for (int r = 0; r < RMAX; ++r)
+#pragma unroll
+    for (int g = 0; g < G; ++g)
+      v[r][g] = (active && g < cnt) ? front[(size_t)(o0 + g) * rows + row0 + r] : T(0);
+#pragma unroll
+  for (int r = 0; r < RMAX; ++r)
+#pragma unroll
+    for (int g = 0; g < G; ++g) XA(1, r, g, t) = v[r][g];
+
+  int tb = -1;  // thread owning the row below j0 (same plane)
+  if (active) {
+    if (jb > 0) tb = t - 1;
+    else if (gm.py) tb = kp * tpp + (tpp - 1);
+  }
+  int tz = -1;  // thread owning the same rows in the plane below
+  if (active) {
+    if (kp > 0) tz = t - tpp;
+    else if (gm.pz) tz = (nz - 1) * tpp + jb;
+  }
+  const uint32_t in_x_bit = sx > 0 ? CODE_WALL_XM : CODE_WALL_XP;
+  const uint32_t in_y_bit = sy > 0 ? CODE_WALL_YM : CODE_WALL_YP;
+  const uint32_t in_z_bit = sz > 0 ? CODE_WALL_ZM : CODE_WALL_ZP;
+  const uint32_t out_wall_bits = (sx > 0 ? CODE_WALL_XP : CODE_WALL_XM) |
+                                 (sy > 0 ? CODE_WALL_YP : CODE_WALL_YM) |
+                                 (sz > 0 ? CODE_WALL_ZP : CODE_WALL_ZM);
+  double phi = 0.0;
+  int s = d0;
+
+  // records of the first step
+  T rc[RMAX][5];
+  auto load_recs = [&](int sd, T (&dst)[RMAX][5]) {
+#pragma unroll
+    for (int r = 0; r < RMAX; ++r) {
+      if (active) {
+        const T* p = recq + ((size_t)sd * rows + row0 + r) * 8;
+        if (sizeof(T) == 4) {
+          const float4 a = __ldg(reinterpret_cast<const float4*>(p));
+          const float b = __ldg(reinterpret_cast<const float*>(p) + 4);
+          dst[r][0] = (T)a.x;
+          dst[r][1] = (T)a.y;
+          dst[r][2] = (T)a.z;
+          dst[r][3] = (T)a.w;
+          dst[r][4] = (T)b;
+        } else {
+          for (int f = 0; f < 5; ++f) dst[r][f] = __ldg(p + f);
+        }
+      } else {
+        for (int f = 0; f < 5; ++f) dst[r][f] = T(0);
+      }
+    }
+  };
+  load_recs(s, rc);
+  __syncthreads();
+
+  for (int d = 0; d < nx; ++d) {
+    const int cur = d & 1, prv = cur ^ 1;
+    const int s_next = (s + 1 == nx) ? 0 : s + 1;
+    T rn[RMAX][5];
+    if (d + 1 < nx) load_recs(s_next, rn);
+    if (active) {
+      T dny[G];
+#pragma unroll
+      for (int g = 0; g < G; ++g) dny[g] = (tb >= 0) ? XA(prv, RMAX - 1, g, tb) : T(0);
+      double* tl_row = tlq + (size_t)s * rows + row0;
+#pragma unroll
+      for (int rr = 0; rr < RMAX; ++rr) {
+        const int r = RMAX - 1 - rr;
+        const T src = rc[r][0], twx = rc[r][1], twy = rc[r][2], twz = rc[r][3];
+        const uint32_t packed = rec3_bits<T>(rc[r][4]);
+        const uint32_t code = (packed >> 22) & 0xffu;
+        const bool wx = code & in_x_bit, wy = code & in_y_bit, wz = code & in_z_bit;
+        const bool jump = ((packed >> 30) & 1u) && !wx;
+        T sval = T(1);
+        if (HAS_S) sval = (T)__ldg(sv_ptr + (packed & 0x3fffffu));
+        T tl = T(0);
+#pragma unroll
+        for (int g = 0; g < G; ++g) {
+          const T ux = wx ? twx : v[r][g];
+          const T uy = wy ? twy : (r > 0 ? v[r > 0 ? r - 1 : 0][g] : dny[g]);
+          const T uz = wz ? twz : ((tz >= 0) ? XA(prv, r, g, tz) : T(0));
+          const T jx = jump ? JX[g] : T(0);
+          T acc;
+          if (HAS_S) acc = src + jx;
+          else acc = fma(src, A0[g], jx);
+          acc = fma(AZ[g], uz, fma(AY[g], uy, fma(AX[g], ux, acc)));
+          T val;
+          if (HAS_S) {
+            if (sizeof(T) == 4) val = (T)__fdividef((float)acc, (float)(sval + A0[g]));
+            else val = acc / (sval + A0[g]);
+          } else {
+            val = acc;
+          }
+          v[r][g] = val;
+          tl = fma(AW[g], val, tl);
+        }
+        if (code & CODE_SOLID) {
+          atomicAdd(tl_row + r, widen(tl));
+          const bool last = (packed >> 31) & 1u;
+          if ((code & out_wall_bits) || last || rare_pass) {
+#pragma unroll
+            for (int g = 0; g < G; ++g) scratch[g * nthr + t] = v[r][g];
+            phi += cell_epilogue_3d<T, G>(gm, scratch + t, nthr, (int)(packed & 0x3fffffu), code,
+                                          last, o0, cnt, sx, sy, sz, flags, kx_sum);
+          }
+        }
+      }
+#pragma unroll
+      for (int r = 0; r < RMAX; ++r)
+#pragma unroll
+        for (int g = 0; g < G; ++g) XA(cur, r, g, t) = v[r][g];
+    }
+#pragma unroll
+    for (int r = 0; r < RMAX; ++r)
+#pragma unroll
+      for (int f = 0; f < 5; ++f) rc[r][f] = rn[r][f];
+    s = s_next;
+    __syncthreads();
+  }
+
+  T* frontw = reinterpret_cast<T*>(gm.front);
+#pragma unroll
+  for (int r = 0; r < RMAX; ++r)
+#pragma unroll
+    for (int g = 0; g < G; ++g)
+      if (active && g < cnt) frontw[(size_t)(o0 + g) * rows + row0 + r] = v[r][g];
+  const double ps = block_sum(phi, red);
+  if (t == 0 && ps != 0.0) atomicAdd(gm.phi_acc, ps);
+}
+
+}  // namespace obte

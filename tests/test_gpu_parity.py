@@ -178,3 +178,32 @@ def test_anderson_same_fixed_point(name, precision):
     if precision == "fp64":
         _, st0 = gpu(wl, precision)
         assert st["iterations"] < st0["iterations"], (st["iterations"], st0["iterations"])
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+@pytest.mark.parametrize("kernel", ["block", "block3d"])
+def test_3d_kernels(precision, kernel):
+    """Both 3D kernels (plain block kernel, block kernel with skewed records)
+    against the oracle on the small film, with and without pores."""
+    for name in ("3d_film", "3d_film_porefree"):
+        wl, pr, ref = _ref(name, SMALL[name])
+        s, st = gpu(wl, precision, kernel=kernel)
+        assert st["kernel"] == (3 if kernel == "block3d" else 1)
+        _check(wl, pr, ref, s, precision)
+
+
+def test_3d_periodic_cube_porefree():
+    """3D periodic cube (nz = nx): the z wrap through the skewed exchange."""
+    import numpy as np
+    from paper_2106_02764_gb300 import inputs as I
+    from oracle import bte
+    L = 60e-9
+    k, lam = I.mfp_bins(2)
+    mask = np.ones((8, 8, 8), np.uint8)
+    mask[:, 3:5, 2:6] = 0
+    wl = I.Workload("cube", 3, (8, 8, 8), (L, L, L), mask, (1, 1, 1), 1.0, k, lam,
+                    I.sphere_quadrature(4, 2))
+    pr, ref = oracle(wl)
+    for precision in ("fp64", "mixed"):
+        s, st = gpu(wl, precision)
+        _check(wl, pr, ref, s, precision)
