@@ -6,8 +6,10 @@
 //     x_{k+1} = g_k - sum_i gamma_i (g_{i+1} - g_i),
 //     gamma = argmin || f_k - sum_i gamma_i (f_{i+1} - f_i) ||,  f = g(x) - x,
 // over the last m differences.  The fixed point is unchanged (f = 0 there);
-// only the trajectory is.  Dot products and the small least-squares solve are
-// FP64; the carried row values are kept in the sweep precision.
+// only the trajectory is.
+//
+// The row-value part of the state (most of its length) is combined in the
+// sweep precision; T_L, T_w, the reductions and the solve stay FP64.
 //
 // Per iteration (after the finalisation):
 //   aa_residual_kernel: f_k = g_k - x_k into history slot, dots f_k . F_j for
@@ -87,29 +89,42 @@ __global__ void aa_residual_kernel(const GeomDev* geoms) {
   const int tid = blockIdx.x * blockDim.x + threadIdx.x;
   const int stride = gridDim.x * blockDim.x;
   const int nvalid = k + 1 < S ? k + 1 : S;  // slots holding residuals after this step
+  // slot j of the window (j = 0: this step) -> its base pointers
+  const double* fdj[8];
+  const T* ftj[8];
+  for (int j = 0; j < 8; ++j) {
+    const int sl = (k - j + S * 8) % S;
+    fdj[j] = AAView<T>::fd(g, sl);
+    ftj[j] = AAView<T>::ft(g, sl);
+  }
   double* fcur = AAView<T>::fd(g, cur);
   const double* xcur = AAView<T>::xd(g, cur);
   for (long i = tid; i < g.aa_nd; i += stride) {
     const double f = state_d(g, i) - xcur[i];
     fcur[i] = f;
-    for (int j = 0; j < 8; ++j)
-      if (j < nvalid) {
-        const int sl = (k - j + S * 8) % S;
-        dots[j] += f * (j == 0 ? f : AAView<T>::fd(g, sl)[i]);
-      }
+    dots[0] += f * f;
+#pragma unroll
+    for (int j = 1; j < 8; ++j)
+      if (j < nvalid) dots[j] += f * fdj[j][i];
   }
+  // row values: sweep precision products, summed per thread in the same
+  // precision over its few elements, then widened for the block reduction
   T* ftc = AAView<T>::ft(g, cur);
   const T* xtc = AAView<T>::xt(g, cur);
   const T* front = reinterpret_cast<const T*>(g.front);
+  T tdots[8];
+#pragma unroll
+  for (int j = 0; j < 8; ++j) tdots[j] = T(0);
   for (long i = tid; i < g.aa_nt; i += stride) {
-    const double f = (double)front[i] - (double)xtc[i];
-    ftc[i] = (T)f;
-    for (int j = 0; j < 8; ++j)
-      if (j < nvalid) {
-        const int sl = (k - j + S * 8) % S;
-        dots[j] += f * (j == 0 ? f : (double)AAView<T>::ft(g, sl)[i]);
-      }
+    const T f = front[i] - xtc[i];
+    ftc[i] = f;
+    tdots[0] = fma(f, f, tdots[0]);
+#pragma unroll
+    for (int j = 1; j < 8; ++j)
+      if (j < nvalid) tdots[j] = fma(f, ftj[j][i], tdots[j]);
   }
+#pragma unroll
+  for (int j = 0; j < 8; ++j) dots[j] += (double)tdots[j];
   // block reduction of the dots, then FP64 atomics into the geometry's buffer
   for (int j = 0; j < 8; ++j) {
     double v = dots[j];
@@ -183,10 +198,17 @@ __global__ void aa_mix_kernel(const GeomDev* geoms) {
   const int mk = nvalid - 1;
   const int nxt = (k + 1) % S;
   double c[8];
-  int sl[8];
+  T ct[8];
+  const double *xdl[8], *fdl[8];
+  const T *xtl[8], *ftl[8];
   for (int l = 0; l < 8; ++l) {
-    c[l] = g.aa_coef[l];
-    sl[l] = (k - mk + l + S * 8) % S;
+    c[l] = l <= mk ? g.aa_coef[l] : 0.0;
+    ct[l] = (T)c[l];
+    const int sl = (k - mk + l + S * 8) % S;
+    xdl[l] = AAView<T>::xd(g, sl);
+    fdl[l] = AAView<T>::fd(g, sl);
+    xtl[l] = AAView<T>::xt(g, sl);
+    ftl[l] = AAView<T>::ft(g, sl);
   }
   const int tid = blockIdx.x * blockDim.x + threadIdx.x;
   const int stride = gridDim.x * blockDim.x;
@@ -195,8 +217,9 @@ __global__ void aa_mix_kernel(const GeomDev* geoms) {
   double* xn = AAView<T>::xd(g, nxt);
   for (long i = tid; i < g.aa_nd; i += stride) {
     double v = 0.0;
+#pragma unroll
     for (int l = 0; l < 8; ++l)
-      if (l <= mk) v += c[l] * (AAView<T>::xd(g, sl[l])[i] + AAView<T>::fd(g, sl[l])[i]);
+      if (l <= mk) v += c[l] * (xdl[l][i] + fdl[l][i]);
     if (i < g.n_cells) {
       if (!(g.code[i] & CODE_SOLID)) v = 0.0;
       g.TL[i] = v;
@@ -208,17 +231,16 @@ __global__ void aa_mix_kernel(const GeomDev* geoms) {
     }
     xn[i] = v;
   }
+  // row values in the sweep precision
   T* front = reinterpret_cast<T*>(g.front);
   T* xtn = AAView<T>::xt(g, nxt);
   for (long i = tid; i < g.aa_nt; i += stride) {
-    double v = 0.0;
+    T v = T(0);
+#pragma unroll
     for (int l = 0; l < 8; ++l)
-      if (l <= mk) v += c[l] * ((double)AAView<T>::xt(g, sl[l])[i] + (double)AAView<T>::ft(g, sl[l])[i]);
-    front[i] = (T)v;
-    xtn[i] = (T)v;
-  }
-  if (tid == 0) {
-    __threadfence();
+      if (l <= mk) v = fma(ct[l], xtl[l][i] + ftl[l][i], v);
+    front[i] = v;
+    xtn[i] = v;
   }
 }
 

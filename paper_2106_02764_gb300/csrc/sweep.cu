@@ -88,5 +88,7 @@ bool sweep3d_exists(int precision, int G, int RMAX, bool has_s) {
 
 size_t sweep3d_smem_bytes(int precision, int G, int RMAX, int threads) {
   const size_t e = precision == 0 ? sizeof(double) : sizeof(float);
-  return (2 * (size_t)RMAX + 1) * G * threads * e;  // exchange [2][R][G][threads] + scratch [G][threads]
+  const size_t nt = RMAX >= 8 ? 256 : 512;  // the kernel's compile-time block stride
+  (void)threads;
+  return (2 * (size_t)RMAX + 1) * G * nt * e;  // exchange [2][R][G][nt] + scratch [G][nt]
 }

@@ -143,7 +143,7 @@ __global__ void __launch_bounds__(32 * WarpCfg<T, RMAX>::WPB, 1) sweep2d_warp_ke
     double* tlq = gm.tlq + (size_t)q * nx * ny;
     const double* __restrict__ sv_ptr = gm.s;
 
-    T A0[G], AX[G], AY[G], AW[G], JX[G];
+    T A0[G], AX[G], AY[G], AW[G], JX[G], KX[G];
     double kx_sum = 0.0;
 #pragma unroll
     for (int g = 0; g < G; ++g) {
@@ -161,6 +161,7 @@ __global__ void __launch_bounds__(32 * WarpCfg<T, RMAX>::WPB, 1) sweep2d_warp_ke
       AY[g] = (T)ay;
       AW[g] = ok ? ld<T>(gm.aw, o) : T(0);
       JX[g] = (T)(ax * (double)sx * dT);
+      KX[g] = ok ? ld<T>(gm.kxa, o) : T(0);  // |K_gx|
       if (ok) kx_sum += (double)sx * (double)ld<T>(gm.kxa, o);
     }
 
@@ -223,7 +224,7 @@ __global__ void __launch_bounds__(32 * WarpCfg<T, RMAX>::WPB, 1) sweep2d_warp_ke
             const bool below_in_lane = RFIXED ? (r > 0) : (r > rb);
             T sval = T(1);
             if (HAS_S) sval = (T)__ldg(sv_ptr + (packed & 0x3fffffu));
-            T tl = T(0);
+            T tl = T(0), tl2 = T(0);  // two partial chains of the T_L moment
 #pragma unroll
             for (int g = 0; g < G; ++g) {
               const T ux = wx ? twx : v[r][g];
@@ -242,16 +243,24 @@ __global__ void __launch_bounds__(32 * WarpCfg<T, RMAX>::WPB, 1) sweep2d_warp_ke
                 val = acc;
               }
               v[r][g] = val;
-              tl = fma(AW[g], val, tl);
+              if (g & 1) tl2 = fma(AW[g], val, tl2);
+              else tl = fma(AW[g], val, tl);
             }
             if (code & CODE_SOLID) {
-              atomicAdd(tl_row + r, widen(tl));
+              atomicAdd(tl_row + r, widen(tl + tl2));
               const bool last = (packed >> 31) & 1u;
-              if ((code & out_wall_bits) || last || rare_pass) {
+              if ((code & out_wall_bits) || rare_pass) {
 #pragma unroll
                 for (int g = 0; g < G; ++g) scratch[g] = v[r][g];
                 phi += cell_epilogue_2d<T, G>(gm, scratch, (int)(packed & 0x3fffffu), (uint8_t)code,
                                               last, o0, cnt, sx, sy, flags, kx_sum);
+              } else if (last) {
+                // hot-contact face (solid on both sides): sum_g K_gx (T_g + [p_x > 0] dT)
+                T sk = T(0);
+#pragma unroll
+                for (int g = 0; g < G; ++g) sk = fma(KX[g], v[r][g], sk);
+                const double dk = widen(sk);
+                phi += (sx > 0 ? dk : -dk) + (sx > 0 ? dT * kx_sum : 0.0);
               }
             }
           }

@@ -87,17 +87,25 @@ __device__ __noinline__ double cell_epilogue_3d(const GeomDev& gm, const T* val,
   return phi;
 }
 
+// threads per block the kernel is built for (the launch bound); the exchange
+// buffers use it as a compile-time stride
+template <int RMAX>
+struct Sweep3DCfg {
+  static constexpr int NT = RMAX >= 8 ? 256 : 512;
+};
+
 template <typename T, int G, int RMAX, bool HAS_S>
-__global__ void __launch_bounds__(RMAX >= 8 ? 256 : 512, 1) sweep3d_kernel(const SweepLaunch L) {
+__global__ void __launch_bounds__(Sweep3DCfg<RMAX>::NT, 1) sweep3d_kernel(const SweepLaunch L) {
+  constexpr int NT = Sweep3DCfg<RMAX>::NT;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ double red[32];
-  const int nthr = blockDim.x;
+  const int nthr = NT;
   const int t = threadIdx.x;
-  T* xall = reinterpret_cast<T*>(smem_raw);  // [2][RMAX][G][nthr]
-  T* scratch = xall + 2 * RMAX * G * nthr;   // [G][nthr]
+  T* xall = reinterpret_cast<T*>(smem_raw);  // [2][RMAX][G][NT]
+  T* scratch = xall + 2 * RMAX * G * NT;     // [G][NT]
   const int flags = L.flags;
   const bool rare_pass = (flags & (SWEEP_FLUX | SWEEP_RECORD)) != 0;
-  auto XA = [&](int b, int r, int g, int th) -> T& { return xall[((b * RMAX + r) * G + g) * nthr + th]; };
+  auto XA = [&](int b, int r, int g, int th) -> T& { return xall[((b * RMAX + r) * G + g) * NT + th]; };
 
   const int item = blockIdx.x;
   if (item >= L.n_items) return;
