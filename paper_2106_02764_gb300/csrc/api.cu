@@ -611,9 +611,9 @@ struct Variant {
   bool k3d = false;  // 3D block kernel with skewed records (sweep3d.cuh)
 };
 
-const Variant kWarp2D_F[] = {{8, 8, true}, {8, 4, true}, {16, 4, true},
-                             {16, 2, true}, {16, 1, true}, {8, 1, true}};
-const Variant kWarp2D_D[] = {{4, 8, true}, {8, 4, true}, {8, 2, true}, {8, 1, true}};
+const Variant kWarp2D_F[] = {{8, 8, true}, {8, 4, true}, {16, 4, true}, {16, 2, true},
+                             {16, 1, true}, {8, 1, true},  {4, 8, true},  {4, 4, true}};
+const Variant kWarp2D_D[] = {{4, 8, true}, {8, 4, true}, {8, 2, true}, {8, 1, true}, {2, 8, true}};
 const Variant kVariants2D_F[] = {{16, 4, false}, {8, 4, false}, {8, 8, false}, {16, 2, false},
                                  {8, 2, false}, {4, 4, false}, {16, 1, false}};
 const Variant kVariants2D_D[] = {{8, 2, false}, {8, 4, false}, {4, 4, false}, {4, 8, false},
@@ -735,7 +735,7 @@ static int prepare_state(obte_ctx* ctx, int precision, int G, int R, bool warp, 
     ctx->twc = ctx->dalloc(e * (size_t)ctx->n_cells * 6);
     NEED(ctx->twc);
     ctx->Tw = ctx->dalloc_t<double>(std::max(1, ctx->n_walls));
-    ctx->wall_acc = ctx->dalloc_t<double>(std::max(1, ctx->n_walls));
+    ctx->wall_acc = ctx->dalloc_t<double>((size_t)ctx->n_cells * 6);
     ctx->front = ctx->dalloc(e * (size_t)ctx->O * rows);
     ctx->scal = ctx->dalloc_t<double>(4);
     ctx->ctrl = ctx->dalloc_t<int>(4);
@@ -983,14 +983,16 @@ static int pick_variant(obte_ctx* ctx, int precision, const obte_solve_opts& op,
   // of work; the lists are ordered by measured preference
   int sms = 148;
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ctx->device);
+  // (a warp kernel whose rows leave lanes idle comes after one that fills all 32)
   *out = cands[0];
-  for (auto& c : cands) {
-    const long units = (ctx->O + c.G - 1) / c.G;
-    if (units >= sms) {
+  for (int pass = 0; pass < 2; ++pass)
+    for (auto& c : cands) {
+      const long units = (ctx->O + c.G - 1) / c.G;
+      if (units < sms) continue;
+      if (pass == 0 && c.warp && ctx->n[1] / c.R != 32) continue;
       *out = c;
-      break;
+      return OBTE_OK;
     }
-  }
   return OBTE_OK;
 }
 
@@ -1281,7 +1283,7 @@ static int run_flux_pass(obte_ctx* ctx) {
   // the pass does not advance the iterate: drop its moment accumulations
   CK(cudaMemsetAsync(ctx->TL_acc, 0, sizeof(double) * ctx->n_cells, ctx->stream));
   if (ctx->tlq) CK(cudaMemsetAsync(ctx->tlq, 0, sizeof(double) * (ctx->dim == 3 ? 8 : 4) * (size_t)ctx->n_cells, ctx->stream));
-  CK(cudaMemsetAsync(ctx->wall_acc, 0, sizeof(double) * std::max(1, ctx->n_walls), ctx->stream));
+  CK(cudaMemsetAsync(ctx->wall_acc, 0, sizeof(double) * 6 * (size_t)ctx->n_cells, ctx->stream));
   CK(cudaMemsetAsync(ctx->scal, 0, sizeof(double), ctx->stream));
   int one = 1;
   CK(cudaMemcpyAsync(ctx->ctrl, &one, sizeof(int), cudaMemcpyHostToDevice, ctx->stream));
@@ -1447,7 +1449,7 @@ extern "C" int obte_kappa_grad_s(obte_ctx* ctx, double* out, size_t max_field_by
                              jscale, grad_d, ctx->precision, ctx->stream));
     CK(cudaMemsetAsync(ctx->TL_acc, 0, sizeof(double) * ctx->n_cells, ctx->stream));
     if (ctx->tlq) CK(cudaMemsetAsync(ctx->tlq, 0, sizeof(double) * (ctx->dim == 3 ? 8 : 4) * (size_t)ctx->n_cells, ctx->stream));
-    CK(cudaMemsetAsync(ctx->wall_acc, 0, sizeof(double) * std::max(1, ctx->n_walls), ctx->stream));
+    CK(cudaMemsetAsync(ctx->wall_acc, 0, sizeof(double) * 6 * (size_t)ctx->n_cells, ctx->stream));
     CK(cudaMemsetAsync(ctx->scal, 0, sizeof(double), ctx->stream));
     CK(cudaStreamSynchronize(ctx->stream));
     ctx->dfree(its_d);
@@ -1883,7 +1885,7 @@ extern "C" int obte_kappa_grad_s_noalloc(obte_ctx* ctx, double* out) {
                              jscale, grad_d, ctx->precision, ctx->stream));
     CK(cudaMemsetAsync(ctx->TL_acc, 0, sizeof(double) * ctx->n_cells, ctx->stream));
     if (ctx->tlq) CK(cudaMemsetAsync(ctx->tlq, 0, sizeof(double) * (ctx->dim == 3 ? 8 : 4) * (size_t)ctx->n_cells, ctx->stream));
-    CK(cudaMemsetAsync(ctx->wall_acc, 0, sizeof(double) * std::max(1, ctx->n_walls), ctx->stream));
+    CK(cudaMemsetAsync(ctx->wall_acc, 0, sizeof(double) * 6 * (size_t)ctx->n_cells, ctx->stream));
     CK(cudaMemsetAsync(ctx->scal, 0, sizeof(double), ctx->stream));
     CK(cudaStreamSynchronize(ctx->stream));  // host vectors above are copy sources
   }

@@ -56,8 +56,9 @@ __global__ void finalize_kernel(const GeomDev* geoms) {
   }
   T* twc = reinterpret_cast<T*>(g.twc);
   for (int f = blockIdx.x * blockDim.x + threadIdx.x; f < g.n_walls; f += stride) {
-    const double w = g.wall_acc[f] / g.wall_den[f];
-    g.wall_acc[f] = 0.0;
+    const size_t k = (size_t)g.wall_cell[f] * 6 + g.wall_side[f];
+    const double w = g.wall_acc[k] / g.wall_den[f];
+    g.wall_acc[k] = 0.0;
     if (!isfinite(w)) nonfin = 1;
     g.Tw[f] = w;
     twc[(size_t)g.wall_cell[f] * 6 + g.wall_side[f]] = (T)w;
@@ -124,7 +125,7 @@ __global__ void init_state_kernel(const GeomDev* geoms, int gi, const double* T0
   for (long i = tid; i < (long)g.n_cells * 6; i += stride) twc[i] = T(0);
   for (int f = tid; f < g.n_walls; f += stride) {
     g.Tw[f] = T0[g.wall_cell[f]];
-    g.wall_acc[f] = 0.0;
+    g.wall_acc[(size_t)g.wall_cell[f] * 6 + g.wall_side[f]] = 0.0;
   }
   T* front = reinterpret_cast<T*>(g.front);
   const long total = (long)g.n_ord * g.rows;

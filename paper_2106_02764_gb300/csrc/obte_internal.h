@@ -45,7 +45,7 @@ struct GeomDev {
   double* TL_acc;         // [n_cells] sum_o a_o T_o of the running sweep
   void* src;              // [n_cells] s_i T_L,i in the sweep precision
   double* Tw;             // [n_walls]
-  double* wall_acc;       // [n_walls]
+  double* wall_acc;       // [n_cells * 6] numerator of E3 per (cell, side); only wall sides used
   const double* wall_den; // [n_walls]
   const int* wall_cell;   // [n_walls]
   const int* wall_side;   // [n_walls] side of its cell (0..5: -x +x -y +y -z +z)

@@ -115,9 +115,9 @@ __device__ __noinline__ double cell_epilogue(const GeomDev& gm, const T* __restr
     syk += (double)ld<T>(gm.kya, o0 + g) * v;
     if (DIM == 3) szk += (double)ld<T>(gm.kza, o0 + g) * v;
   }
-  if (code & out_x_bit) atomicAdd(gm.wall_acc + gm.wall_id[cell * 6 + out_x_side], sxk);
-  if (code & out_y_bit) atomicAdd(gm.wall_acc + gm.wall_id[cell * 6 + out_y_side], syk);
-  if (DIM == 3 && (code & out_z_bit)) atomicAdd(gm.wall_acc + gm.wall_id[cell * 6 + out_z_side], szk);
+  if (code & out_x_bit) atomicAdd(gm.wall_acc + cell * 6 + out_x_side, sxk);
+  if (code & out_y_bit) atomicAdd(gm.wall_acc + cell * 6 + out_y_side, syk);
+  if (DIM == 3 && (code & out_z_bit)) atomicAdd(gm.wall_acc + cell * 6 + out_z_side, szk);
   // the x = 0 plane is the out-of-cell x face of the last column i' = nx-1
   const bool hot = (ip == nx - 1) && !(code & out_x_bit);
   double phi = 0.0;

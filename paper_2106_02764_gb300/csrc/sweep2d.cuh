@@ -64,8 +64,8 @@ __device__ __noinline__ double cell_epilogue_2d(const GeomDev& gm, const T* __re
     syk = fma(ld<T>(gm.kya, o0 + g), val[g], syk);
   }
   const double dx = widen(sxk), dy = widen(syk);
-  if (code & out_x_bit) atomicAdd(gm.wall_acc + gm.wall_id[cell * 6 + (sx > 0 ? 1 : 0)], dx);
-  if (code & out_y_bit) atomicAdd(gm.wall_acc + gm.wall_id[cell * 6 + (sy > 0 ? 3 : 2)], dy);
+  if (code & out_x_bit) atomicAdd(gm.wall_acc + cell * 6 + (sx > 0 ? 1 : 0), dx);
+  if (code & out_y_bit) atomicAdd(gm.wall_acc + cell * 6 + (sy > 0 ? 3 : 2), dy);
   const bool hot = last && !(code & out_x_bit);
   double phi = 0.0;
   if (hot) phi = (sx > 0 ? dx : -dx) + (sx > 0 ? dT * kx_sum : 0.0);
@@ -95,18 +95,36 @@ __device__ __noinline__ double cell_epilogue_2d(const GeomDev& gm, const T* __re
 }
 
 // warps per block: every warp owns its own staging buffers (static shared
-// memory stays under 48 KB)
-template <typename T, int RMAX>
+// memory stays under 48 KB).  Narrow groups (G <= 4 in FP32, G <= 2 in FP64)
+// hold few row values; they are built for four resident blocks per SM
+// (<= 128 registers) so that more warps hide the latencies of a step.
+template <typename T, int G, int RMAX>
 struct WarpCfg {
   static constexpr int WPB = (sizeof(T) == 8 && RMAX >= 8) ? 2 : 4;
+  static constexpr int MINB = (G * (int)sizeof(T) <= 16) ? 4 : 1;
 };
 
+// Shared-memory slot of the record of (lane, register row r): each 16-byte
+// part c of a record lives in plane c; inside a plane, lane l's rows occupy
+// slots l*RMAX .. l*RMAX+RMAX-1 in an order permuted by an XOR of the lane's
+// bits, so that the eight lanes of a quarter-warp reading the same r hit
+// eight different 16-byte bank groups (the unpermuted layout puts them all
+// on the same banks).
+template <int RMAX>
+__device__ __forceinline__ int rec_slot(int lane, int r) {
+  constexpr int SH = RMAX >= 8 ? 0 : (RMAX == 4 ? 1 : (RMAX == 2 ? 2 : 0));
+  constexpr int MSK = RMAX >= 8 ? 7 : RMAX - 1;
+  return lane * RMAX + (r ^ ((lane >> SH) & MSK));
+}
+
 template <typename T, int G, int RMAX, bool HAS_S, bool RFIXED>
-__global__ void __launch_bounds__(32 * WarpCfg<T, RMAX>::WPB, 1) sweep2d_warp_kernel(const SweepLaunch L) {
-  constexpr int WPB = WarpCfg<T, RMAX>::WPB;
-  constexpr int CH = (4 * sizeof(T)) / 16;  // 16-byte chunks per record
-  __shared__ __align__(16) T recbuf[WPB][2][32][RMAX][4];
+__global__ void __launch_bounds__(32 * WarpCfg<T, G, RMAX>::WPB, WarpCfg<T, G, RMAX>::MINB)
+    sweep2d_warp_kernel(const SweepLaunch L) {
+  constexpr int WPB = WarpCfg<T, G, RMAX>::WPB;
+  constexpr int CH = (4 * sizeof(T)) / 16;  // 16-byte parts per record
+  __shared__ __align__(16) uint4 recbuf[WPB][2][CH][32 * RMAX];
   __shared__ __align__(16) T scratch_all[WPB][32][G];
+  __shared__ T kcoef[WPB][2][G];  // |K_gx|, |K_gy| of the warp's group (rare path only)
   const int lane = threadIdx.x & 31;
   const int wib = threadIdx.x >> 5;
   T* scratch = &scratch_all[wib][lane][0];
@@ -142,9 +160,20 @@ __global__ void __launch_bounds__(32 * WarpCfg<T, RMAX>::WPB, 1) sweep2d_warp_ke
     const T* __restrict__ recq = reinterpret_cast<const T*>(gm.rec4) + (size_t)q * nx * ny * 4;
     double* tlq = gm.tlq + (size_t)q * nx * ny;
     const double* __restrict__ sv_ptr = gm.s;
+    double* wacc = gm.wall_acc;
 
-    T A0[G], AX[G], AY[G], AW[G], JX[G], KX[G];
+    // FP32: the jump is added to the x upwind value (one FADD); FP64, whose
+    // pipe is the narrow one: a select of the premultiplied term JX instead
+    constexpr bool JSEL = sizeof(T) == 8;
+    T A0[G], AX[G], AY[G], AW[G], JX[JSEL ? G : 1];
     double kx_sum = 0.0;
+    __syncwarp();  // the previous item's rare path is done with kcoef
+    if (lane < G) {
+      const bool ok = lane < cnt;
+      kcoef[wib][0][lane] = ok ? ld<T>(gm.kxa, o0 + lane) : T(0);
+      kcoef[wib][1][lane] = ok ? ld<T>(gm.kya, o0 + lane) : T(0);
+    }
+    const T sdT = (T)((double)sx * dT);  // jump added to the x upwind value at i' = 0
 #pragma unroll
     for (int g = 0; g < G; ++g) {
       const bool ok = g < cnt;
@@ -160,8 +189,7 @@ __global__ void __launch_bounds__(32 * WarpCfg<T, RMAX>::WPB, 1) sweep2d_warp_ke
       AX[g] = (T)ax;
       AY[g] = (T)ay;
       AW[g] = ok ? ld<T>(gm.aw, o) : T(0);
-      JX[g] = (T)(ax * (double)sx * dT);
-      KX[g] = ok ? ld<T>(gm.kxa, o) : T(0);  // |K_gx|
+      if (JSEL) JX[JSEL ? g : 0] = (T)(ax * (double)sx * dT);
       if (ok) kx_sum += (double)sx * (double)ld<T>(gm.kxa, o);
     }
 
@@ -173,26 +201,39 @@ __global__ void __launch_bounds__(32 * WarpCfg<T, RMAX>::WPB, 1) sweep2d_warp_ke
       for (int g = 0; g < G; ++g)
         v[r][g] = (active && r >= rb && g < cnt) ? front[(size_t)(o0 + g) * ny + j0 + (r - rb)] : T(0);
 
-    // prefetch the records of the lane's rows on diagonal s into buffer b
+    // Prefetch the records of diagonal s into buffer b.  With RFIXED the
+    // warp's ny records are one contiguous run and part m of it is copied by
+    // lane m % 32 (coalesced); otherwise every lane copies its own rows.
     auto prefetch = [&](int s, int b) {
-      if (active) {
-        const T* g0 = recq + ((size_t)s * ny + j0) * 4;
+      const char* g0 = reinterpret_cast<const char*>(recq + (size_t)s * ny * 4);
+      if (RFIXED) {
+        const int n16 = ny * CH;
+#pragma unroll
+        for (int k = 0; k < RMAX * CH; ++k) {
+          const int m = k * 32 + lane;
+          if (m < n16) {
+            const int jr = m / CH, c = m % CH;
+            cp_async16(&recbuf[wib][b][c][rec_slot<RMAX>(jr / RMAX, jr % RMAX)], g0 + (size_t)m * 16);
+          }
+        }
+      } else if (active) {
 #pragma unroll
         for (int r = 0; r < RMAX; ++r)
-          if (RFIXED || r >= rb)
+          if (r >= rb)
 #pragma unroll
             for (int c = 0; c < CH; ++c)
-              cp_async16(reinterpret_cast<char*>(&recbuf[wib][b][lane][r][0]) + 16 * c,
-                         reinterpret_cast<const char*>(g0 + (size_t)(r - rb) * 4) + 16 * c);
+              cp_async16(&recbuf[wib][b][c][rec_slot<RMAX>(lane, r)],
+                         g0 + ((size_t)(j0 + r - rb) * CH + c) * 16);
       }
       cp_async_commit();
     };
 
     const int below = lane > 0 ? lane - 1 : (gm.py ? tpp - 1 : 0);
-    const uint8_t in_x_bit = sx > 0 ? CODE_WALL_XM : CODE_WALL_XP;
-    const uint8_t in_y_bit = sy > 0 ? CODE_WALL_YM : CODE_WALL_YP;
-    const uint32_t out_wall_bits = (sx > 0 ? CODE_WALL_XP : CODE_WALL_XM) |
-                                   (sy > 0 ? CODE_WALL_YP : CODE_WALL_YM);
+    const uint32_t in_x_bit = sx > 0 ? CODE_WALL_XM : CODE_WALL_XP;
+    const uint32_t in_y_bit = sy > 0 ? CODE_WALL_YM : CODE_WALL_YP;
+    const uint32_t out_x_bit = sx > 0 ? CODE_WALL_XP : CODE_WALL_XM;
+    const uint32_t out_y_bit = sy > 0 ? CODE_WALL_YP : CODE_WALL_YM;
+    const int out_x_side = sx > 0 ? 1 : 0, out_y_side = sy > 0 ? 3 : 2;
     double phi = 0.0;
     int s = d0;
     prefetch(s, 0);
@@ -206,34 +247,43 @@ __global__ void __launch_bounds__(32 * WarpCfg<T, RMAX>::WPB, 1) sweep2d_warp_ke
       } else {
         cp_async_wait<0>();
       }
+      __syncwarp();  // parts copied by other lanes are visible
       T dn0[G];
 #pragma unroll
       for (int g = 0; g < G; ++g) dn0[g] = __shfl_sync(FULL, v[RMAX - 1][g], below);
       if (active) {
         double* tl_row = tlq + (size_t)s * ny + j0 - rb;
+        uint32_t pk[RMAX];
+        T tls[RMAX];
+        // branch-free update of all rows of the step (top row first: the row
+        // below still holds its previous value, the y upwind neighbour)
 #pragma unroll
         for (int rr = 0; rr < RMAX; ++rr) {
           const int r = RMAX - 1 - rr;
           if (RFIXED || r >= rb) {
-            const T* rc = &recbuf[wib][cur][lane][r][0];
-            const T src = rc[0], twx = rc[1], twy = rc[2];
-            const uint32_t packed = rec_bits(rc[3]);
+            const int slot = rec_slot<RMAX>(lane, r);
+            const T* rc0 = reinterpret_cast<const T*>(&recbuf[wib][cur][0][slot]);
+            const T* rc1 = reinterpret_cast<const T*>(&recbuf[wib][cur][CH - 1][slot]);
+            const T src = rc0[0], twx = rc0[1];
+            const T twy = CH == 1 ? rc0[2] : rc1[0];
+            const uint32_t packed = rec_bits(CH == 1 ? rc0[3] : rc1[1]);
             const uint32_t code = (packed >> 22) & 0xffu;
             const bool wx = code & in_x_bit, wy = code & in_y_bit;
             const bool jump = ((packed >> 30) & 1u) && !wx;
+            const T jdt = (jump && !JSEL) ? sdT : T(0);
             const bool below_in_lane = RFIXED ? (r > 0) : (r > rb);
             T sval = T(1);
             if (HAS_S) sval = (T)__ldg(sv_ptr + (packed & 0x3fffffu));
             T tl = T(0), tl2 = T(0);  // two partial chains of the T_L moment
 #pragma unroll
             for (int g = 0; g < G; ++g) {
-              const T ux = wx ? twx : v[r][g];
+              const T ux = JSEL ? (wx ? twx : v[r][g]) : (wx ? twx : v[r][g]) + jdt;
               const T ud = below_in_lane ? v[r > 0 ? r - 1 : 0][g] : dn0[g];
               const T uy = wy ? twy : ud;
-              const T jx = jump ? JX[g] : T(0);
+              const T jx = (JSEL && jump) ? JX[JSEL ? g : 0] : T(0);
               T acc;
-              if (HAS_S) acc = fma(AY[g], uy, src + jx);
-              else acc = fma(AY[g], uy, fma(src, A0[g], jx));
+              if (HAS_S) acc = fma(AY[g], uy, JSEL ? src + jx : src);
+              else acc = fma(AY[g], uy, JSEL ? fma(src, A0[g], jx) : src * A0[g]);
               acc = fma(AX[g], ux, acc);
               T val;
               if (HAS_S) {
@@ -246,22 +296,52 @@ __global__ void __launch_bounds__(32 * WarpCfg<T, RMAX>::WPB, 1) sweep2d_warp_ke
               if (g & 1) tl2 = fma(AW[g], val, tl2);
               else tl = fma(AW[g], val, tl);
             }
-            if (code & CODE_SOLID) {
-              atomicAdd(tl_row + r, widen(tl + tl2));
-              const bool last = (packed >> 31) & 1u;
-              if ((code & out_wall_bits) || rare_pass) {
+            pk[r] = packed;
+            tls[r] = tl + tl2;
+          }
+        }
+        // The moment atomics come after all rows: a generic-address atomic
+        // between two rows would keep the next row's shared-memory loads
+        // from being scheduled ahead of it.
+        uint32_t rare_mask = 0;
 #pragma unroll
-                for (int g = 0; g < G; ++g) scratch[g] = v[r][g];
-                phi += cell_epilogue_2d<T, G>(gm, scratch, (int)(packed & 0x3fffffu), (uint8_t)code,
-                                              last, o0, cnt, sx, sy, flags, kx_sum);
-              } else if (last) {
-                // hot-contact face (solid on both sides): sum_g K_gx (T_g + [p_x > 0] dT)
-                T sk = T(0);
+        for (int r = 0; r < RMAX; ++r) {
+          if (!(RFIXED || r >= rb)) continue;
+          const uint32_t code = (pk[r] >> 22) & 0xffu;
+          const bool solid = code & CODE_SOLID;
+          if (solid) atomicAdd(tl_row + r, widen(tls[r]));
+          const bool rare = (code & (out_x_bit | out_y_bit)) || ((pk[r] >> 31) & 1u);
+          rare_mask |= ((solid && (rare || rare_pass)) ? 1u : 0u) << r;
+        }
+        // cells leaving into a wall, the hot-contact column, flux / record passes
+        if (rare_mask) {
+          const T* KX = kcoef[wib][0];
+          const T* KY = kcoef[wib][1];
 #pragma unroll
-                for (int g = 0; g < G; ++g) sk = fma(KX[g], v[r][g], sk);
-                const double dk = widen(sk);
-                phi += (sx > 0 ? dk : -dk) + (sx > 0 ? dT * kx_sum : 0.0);
-              }
+          for (int r = 0; r < RMAX; ++r) {
+            if (!(RFIXED || r >= rb) || !((rare_mask >> r) & 1u)) continue;
+            const uint32_t packed = pk[r];
+            const int cell = (int)(packed & 0x3fffffu);
+            const uint32_t code = (packed >> 22) & 0xffu;
+            const bool last = (packed >> 31) & 1u;
+            if (rare_pass) {
+#pragma unroll
+              for (int g = 0; g < G; ++g) scratch[g] = v[r][g];
+              phi += cell_epilogue_2d<T, G>(gm, scratch, cell, (uint8_t)code, last, o0, cnt, sx, sy,
+                                            flags, kx_sum);
+              continue;
+            }
+            T sk = T(0);
+#pragma unroll
+            for (int g = 0; g < G; ++g) sk = fma(KX[g], v[r][g], sk);
+            const double dk = widen(sk);
+            if (code & out_x_bit) atomicAdd(wacc + (size_t)cell * 6 + out_x_side, dk);
+            else if (last) phi += (sx > 0 ? dk : -dk) + (sx > 0 ? dT * kx_sum : 0.0);
+            if (code & out_y_bit) {
+              T sy_k = T(0);
+#pragma unroll
+              for (int g = 0; g < G; ++g) sy_k = fma(KY[g], v[r][g], sy_k);
+              atomicAdd(wacc + (size_t)cell * 6 + out_y_side, widen(sy_k));
             }
           }
         }

@@ -6,6 +6,8 @@
 
 #define OBTE_SWEEP2D_WF(X) \
   X(float, 8, 8, false, true) \
+  X(float, 4, 8, false, true) \
+  X(float, 4, 4, false, true) \
   X(float, 8, 4, false, true) \
   X(float, 16, 4, false, true) \
   X(float, 16, 2, false, true) \
@@ -14,6 +16,8 @@
 
 #define OBTE_SWEEP2D_WS(X) \
   X(float, 8, 8, true, true) \
+  X(float, 4, 8, true, true) \
+  X(float, 4, 4, true, true) \
   X(float, 8, 4, true, true) \
   X(float, 16, 4, true, true) \
   X(float, 16, 2, true, true) \
@@ -26,6 +30,7 @@
 
 #define OBTE_SWEEP2D_WD(X) \
   X(double, 4, 8, false, true) \
+  X(double, 2, 8, false, true) \
   X(double, 8, 4, false, true) \
   X(double, 8, 2, false, true) \
   X(double, 8, 1, false, true)
@@ -46,7 +51,7 @@ OBTE_SWEEP2D_VARIANTS(OBTE_SWEEP2D_DECLARE)
 
 #define OBTE_SWEEP2D_DEFINE(T, G, R, S, F)                                                      \
   cudaError_t OBTE_SWEEP2D_NAME(T, G, R, S, F)(const SweepLaunch* L, int blocks, cudaStream_t st) { \
-    constexpr int wpb = obte::WarpCfg<T, R>::WPB;                                              \
+    constexpr int wpb = obte::WarpCfg<T, G, R>::WPB;                                            \
     const int need = (L->n_items + wpb - 1) / wpb;                                             \
     const int b = (blocks > 0 && blocks < need) ? blocks : need;                               \
     obte::sweep2d_warp_kernel<T, G, R, S, F><<<b, 32 * wpb, 0, st>>>(*L);                       \

@@ -55,9 +55,9 @@ __device__ __noinline__ double cell_epilogue_3d(const GeomDev& gm, const T* val,
     szk = fma(ld<T>(gm.kza, o0 + g), v, szk);
   }
   const double dx = widen(sxk), dy = widen(syk), dz = widen(szk);
-  if (code & out_x_bit) atomicAdd(gm.wall_acc + gm.wall_id[cell * 6 + (sx > 0 ? 1 : 0)], dx);
-  if (code & out_y_bit) atomicAdd(gm.wall_acc + gm.wall_id[cell * 6 + (sy > 0 ? 3 : 2)], dy);
-  if (code & out_z_bit) atomicAdd(gm.wall_acc + gm.wall_id[cell * 6 + (sz > 0 ? 5 : 4)], dz);
+  if (code & out_x_bit) atomicAdd(gm.wall_acc + cell * 6 + (sx > 0 ? 1 : 0), dx);
+  if (code & out_y_bit) atomicAdd(gm.wall_acc + cell * 6 + (sy > 0 ? 3 : 2), dy);
+  if (code & out_z_bit) atomicAdd(gm.wall_acc + cell * 6 + (sz > 0 ? 5 : 4), dz);
   const bool hot = last && !(code & out_x_bit);
   double phi = 0.0;
   if (hot) phi = (sx > 0 ? dx : -dx) + (sx > 0 ? dT * kx_sum : 0.0);
