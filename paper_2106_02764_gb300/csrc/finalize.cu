@@ -229,8 +229,23 @@ __global__ void build_records_kernel(const GeomDev* geoms) {
       const int jp = (q & 2) ? g.ny - 1 - y : y;
       const int kp = (q & 4) ? g.nz - 1 - z : z;
       const size_t k = ((size_t)q * g.nx + (ip + jp + kp) % g.nx) * g.rows + jp + (size_t)g.ny * kp;
-      const uint32_t packed = (uint32_t)c | (code << 22) | ((ip == 0 ? 1u : 0u) << 30) |
-                              ((ip == g.nx - 1 ? 1u : 0u) << 31);
+      const uint32_t in_x = (q & 1) ? CODE_WALL_XP : CODE_WALL_XM;
+      const uint32_t in_y = (q & 2) ? CODE_WALL_YP : CODE_WALL_YM;
+      const uint32_t in_z = (q & 4) ? CODE_WALL_ZP : CODE_WALL_ZM;
+      const uint32_t out_x = (q & 1) ? CODE_WALL_XM : CODE_WALL_XP;
+      const uint32_t out_y = (q & 2) ? CODE_WALL_YM : CODE_WALL_YP;
+      const uint32_t out_z = (q & 4) ? CODE_WALL_ZM : CODE_WALL_ZP;
+      uint32_t packed = (uint32_t)c;
+      if (code & in_x) packed |= REC_WIN_X;
+      if (code & in_y) packed |= REC_WIN_Y;
+      if (g.dim == 3 && (code & in_z)) packed |= REC_WIN_Z;
+      if (ip == 0 && !(code & in_x)) packed |= REC_JUMP;
+      if (code & CODE_SOLID) packed |= REC_SOLID;
+      if (code & out_x) packed |= REC_WOUT_X;
+      if (code & out_y) packed |= REC_WOUT_Y;
+      if (g.dim == 3 && (code & out_z)) packed |= REC_WOUT_Z;
+      if (ip == 0) packed |= REC_FIRST;
+      if (ip == g.nx - 1) packed |= REC_LAST;
       T* r = rec + (size_t)g.rec_w * k;
       const T pk = sizeof(T) == 4 ? (T)__uint_as_float(packed) : (T)__longlong_as_double((long long)packed);
       r[0] = src[c];

@@ -18,6 +18,22 @@ enum : uint8_t {
   CODE_SOLID = 1u << 6,
 };
 
+// Flags of a skewed cell record (bits 22-31 of its packed word), oriented for
+// the record's octant: "in" sides are the upwind ones, "out" the downwind ones.
+enum : uint32_t {
+  REC_CELL_MASK = (1u << 22) - 1,
+  REC_WIN_X = 1u << 22,    // upwind x side is a wall
+  REC_WIN_Y = 1u << 23,
+  REC_WIN_Z = 1u << 24,
+  REC_JUMP = 1u << 25,     // first column of the octant frame, x upwind across the jump
+  REC_SOLID = 1u << 26,
+  REC_WOUT_X = 1u << 27,   // downwind x side is a wall
+  REC_WOUT_Y = 1u << 28,
+  REC_WOUT_Z = 1u << 29,
+  REC_FIRST = 1u << 30,    // i' == 0
+  REC_LAST = 1u << 31,     // i' == nx - 1
+};
+
 // sweep flags (runtime, uniform)
 enum : int {
   SWEEP_HAS_S = 1 << 0,   // per-cell scattering scale: divide per update
@@ -56,7 +72,7 @@ struct GeomDev {
   //   rec4[((q * nx + s) * rows + row) * rec_w + f]: rec_w = 4 (2D warp kernel)
   //     {s_i T_L,i, T_w in-x side, T_w in-y side, packed};  rec_w = 8 (3D)
   //     {s_i T_L,i, T_w in-x, in-y, in-z sides, packed, 0, 0, 0}
-  //   packed = cell (bits 0-21) | code << 22 | [i' == 0] << 30 | [i' == nx-1] << 31
+  //   packed = cell (bits 0-21) | REC_* flags of octant q (bits 22-31)
   //   tlq[(q * nx + s) * rows + row] = sum_o a_o T_o of the running sweep (FP64)
   void* rec4;
   double* tlq;

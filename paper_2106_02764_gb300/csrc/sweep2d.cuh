@@ -51,29 +51,28 @@ __device__ __forceinline__ uint32_t rec_bits(double d) { return (uint32_t)__doub
 // widened exactly before the FP64 atomics.  Returns the hot-face flux.
 template <typename T, int G>
 __device__ __noinline__ double cell_epilogue_2d(const GeomDev& gm, const T* __restrict__ val,
-                                                int cell, uint8_t code, bool last, int o0,
+                                                int cell, uint32_t packed, bool last, int o0,
                                                 int cnt, int sx, int sy, int flags,
                                                 double kx_sum) {
   const int nx = gm.nx;
   const double dT = gm.dT;
-  const uint8_t out_x_bit = sx > 0 ? CODE_WALL_XP : CODE_WALL_XM;
-  const uint8_t out_y_bit = sy > 0 ? CODE_WALL_YP : CODE_WALL_YM;
+  const bool out_x = packed & REC_WOUT_X, out_y = packed & REC_WOUT_Y;
   T sxk = T(0), syk = T(0);
   for (int g = 0; g < cnt; ++g) {
     sxk = fma(ld<T>(gm.kxa, o0 + g), val[g], sxk);
     syk = fma(ld<T>(gm.kya, o0 + g), val[g], syk);
   }
   const double dx = widen(sxk), dy = widen(syk);
-  if (code & out_x_bit) atomicAdd(gm.wall_acc + cell * 6 + (sx > 0 ? 1 : 0), dx);
-  if (code & out_y_bit) atomicAdd(gm.wall_acc + cell * 6 + (sy > 0 ? 3 : 2), dy);
-  const bool hot = last && !(code & out_x_bit);
+  if (out_x) atomicAdd(gm.wall_acc + cell * 6 + (sx > 0 ? 1 : 0), dx);
+  if (out_y) atomicAdd(gm.wall_acc + cell * 6 + (sy > 0 ? 3 : 2), dy);
+  const bool hot = last && !out_x;
   double phi = 0.0;
   if (hot) phi = (sx > 0 ? dx : -dx) + (sx > 0 ? dT * kx_sum : 0.0);
   if (flags & SWEEP_FLUX) {
     const int x = cell % nx;
     atomicAdd(gm.J_acc + 3 * cell + 0, sx > 0 ? dx : -dx);
     atomicAdd(gm.J_acc + 3 * cell + 1, sy > 0 ? dy : -dy);
-    if (!(code & out_x_bit)) {
+    if (!out_x) {
       const int sec = sx > 0 ? (x + 1) % nx : x;
       const bool jmp = sx > 0 && x == nx - 1;
       atomicAdd(gm.phi_sec + sec, (sx > 0 ? dx : -dx) + (jmp ? dT * kx_sum : 0.0));
@@ -162,8 +161,9 @@ __global__ void __launch_bounds__(32 * WarpCfg<T, G, RMAX>::WPB, WarpCfg<T, G, R
     const double* __restrict__ sv_ptr = gm.s;
     double* wacc = gm.wall_acc;
 
-    // FP32: the jump is added to the x upwind value (one FADD); FP64, whose
-    // pipe is the narrow one: a select of the premultiplied term JX instead
+    // the jump across the x period: FP32 adds it to the x upwind value (one
+    // FADD); FP64, whose pipe is the narrow one, selects the premultiplied
+    // term JX instead
     constexpr bool JSEL = sizeof(T) == 8;
     T A0[G], AX[G], AY[G], AW[G], JX[JSEL ? G : 1];
     double kx_sum = 0.0;
@@ -173,7 +173,7 @@ __global__ void __launch_bounds__(32 * WarpCfg<T, G, RMAX>::WPB, WarpCfg<T, G, R
       kcoef[wib][0][lane] = ok ? ld<T>(gm.kxa, o0 + lane) : T(0);
       kcoef[wib][1][lane] = ok ? ld<T>(gm.kya, o0 + lane) : T(0);
     }
-    const T sdT = (T)((double)sx * dT);  // jump added to the x upwind value at i' = 0
+    const T sdT = (T)((double)sx * dT);  // jump of the x upwind value at i' = 0
 #pragma unroll
     for (int g = 0; g < G; ++g) {
       const bool ok = g < cnt;
@@ -229,10 +229,6 @@ __global__ void __launch_bounds__(32 * WarpCfg<T, G, RMAX>::WPB, WarpCfg<T, G, R
     };
 
     const int below = lane > 0 ? lane - 1 : (gm.py ? tpp - 1 : 0);
-    const uint32_t in_x_bit = sx > 0 ? CODE_WALL_XM : CODE_WALL_XP;
-    const uint32_t in_y_bit = sy > 0 ? CODE_WALL_YM : CODE_WALL_YP;
-    const uint32_t out_x_bit = sx > 0 ? CODE_WALL_XP : CODE_WALL_XM;
-    const uint32_t out_y_bit = sy > 0 ? CODE_WALL_YP : CODE_WALL_YM;
     const int out_x_side = sx > 0 ? 1 : 0, out_y_side = sy > 0 ? 3 : 2;
     double phi = 0.0;
     int s = d0;
@@ -267,13 +263,12 @@ __global__ void __launch_bounds__(32 * WarpCfg<T, G, RMAX>::WPB, WarpCfg<T, G, R
             const T src = rc0[0], twx = rc0[1];
             const T twy = CH == 1 ? rc0[2] : rc1[0];
             const uint32_t packed = rec_bits(CH == 1 ? rc0[3] : rc1[1]);
-            const uint32_t code = (packed >> 22) & 0xffu;
-            const bool wx = code & in_x_bit, wy = code & in_y_bit;
-            const bool jump = ((packed >> 30) & 1u) && !wx;
+            const bool wx = packed & REC_WIN_X, wy = packed & REC_WIN_Y;
+            const bool jump = packed & REC_JUMP;
             const T jdt = (jump && !JSEL) ? sdT : T(0);
             const bool below_in_lane = RFIXED ? (r > 0) : (r > rb);
             T sval = T(1);
-            if (HAS_S) sval = (T)__ldg(sv_ptr + (packed & 0x3fffffu));
+            if (HAS_S) sval = (T)__ldg(sv_ptr + (packed & REC_CELL_MASK));
             T tl = T(0), tl2 = T(0);  // two partial chains of the T_L moment
 #pragma unroll
             for (int g = 0; g < G; ++g) {
@@ -300,18 +295,12 @@ __global__ void __launch_bounds__(32 * WarpCfg<T, G, RMAX>::WPB, WarpCfg<T, G, R
             tls[r] = tl + tl2;
           }
         }
-        // The moment atomics come after all rows: a generic-address atomic
-        // between two rows would keep the next row's shared-memory loads
-        // from being scheduled ahead of it.
         uint32_t rare_mask = 0;
 #pragma unroll
         for (int r = 0; r < RMAX; ++r) {
           if (!(RFIXED || r >= rb)) continue;
-          const uint32_t code = (pk[r] >> 22) & 0xffu;
-          const bool solid = code & CODE_SOLID;
-          if (solid) atomicAdd(tl_row + r, widen(tls[r]));
-          const bool rare = (code & (out_x_bit | out_y_bit)) || ((pk[r] >> 31) & 1u);
-          rare_mask |= ((solid && (rare || rare_pass)) ? 1u : 0u) << r;
+          const bool rare = rare_pass || (pk[r] & (REC_WOUT_X | REC_WOUT_Y | REC_LAST));
+          rare_mask |= (((pk[r] & REC_SOLID) && rare) ? 1u : 0u) << r;
         }
         // cells leaving into a wall, the hot-contact column, flux / record passes
         if (rare_mask) {
@@ -321,23 +310,24 @@ __global__ void __launch_bounds__(32 * WarpCfg<T, G, RMAX>::WPB, WarpCfg<T, G, R
           for (int r = 0; r < RMAX; ++r) {
             if (!(RFIXED || r >= rb) || !((rare_mask >> r) & 1u)) continue;
             const uint32_t packed = pk[r];
-            const int cell = (int)(packed & 0x3fffffu);
-            const uint32_t code = (packed >> 22) & 0xffu;
-            const bool last = (packed >> 31) & 1u;
+            const int cell = (int)(packed & REC_CELL_MASK);
+            const bool last = packed & REC_LAST;
             if (rare_pass) {
 #pragma unroll
               for (int g = 0; g < G; ++g) scratch[g] = v[r][g];
-              phi += cell_epilogue_2d<T, G>(gm, scratch, cell, (uint8_t)code, last, o0, cnt, sx, sy,
+              phi += cell_epilogue_2d<T, G>(gm, scratch, cell, packed, last, o0, cnt, sx, sy,
                                             flags, kx_sum);
               continue;
             }
-            T sk = T(0);
+            if (packed & (REC_WOUT_X | REC_LAST)) {
+              T sk = T(0);
 #pragma unroll
-            for (int g = 0; g < G; ++g) sk = fma(KX[g], v[r][g], sk);
-            const double dk = widen(sk);
-            if (code & out_x_bit) atomicAdd(wacc + (size_t)cell * 6 + out_x_side, dk);
-            else if (last) phi += (sx > 0 ? dk : -dk) + (sx > 0 ? dT * kx_sum : 0.0);
-            if (code & out_y_bit) {
+              for (int g = 0; g < G; ++g) sk = fma(KX[g], v[r][g], sk);
+              const double dk = widen(sk);
+              if (packed & REC_WOUT_X) atomicAdd(wacc + (size_t)cell * 6 + out_x_side, dk);
+              else phi += (sx > 0 ? dk : -dk) + (sx > 0 ? dT * kx_sum : 0.0);
+            }
+            if (packed & REC_WOUT_Y) {
               T sy_k = T(0);
 #pragma unroll
               for (int g = 0; g < G; ++g) sy_k = fma(KY[g], v[r][g], sy_k);
@@ -345,6 +335,12 @@ __global__ void __launch_bounds__(32 * WarpCfg<T, G, RMAX>::WPB, WarpCfg<T, G, R
             }
           }
         }
+        // the moment atomics come after all rows: a generic-address atomic
+        // between two rows would keep the next row's shared-memory loads from
+        // being scheduled ahead of it
+#pragma unroll
+        for (int r = 0; r < RMAX; ++r)
+          if ((RFIXED || r >= rb) && (pk[r] & REC_SOLID)) atomicAdd(tl_row + r, widen(tls[r]));
       }
       s = s_next;
       __syncwarp();

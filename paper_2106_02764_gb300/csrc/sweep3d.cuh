@@ -40,13 +40,11 @@ __device__ __forceinline__ uint32_t rec3_bits<double>(double v) { return (uint32
 // Rare per-cell epilogue (3D); the cell's G values are at val[g * stride].
 template <typename T, int G>
 __device__ __noinline__ double cell_epilogue_3d(const GeomDev& gm, const T* val, int stride, int cell,
-                                                uint32_t code, bool last, int o0, int cnt, int sx,
+                                                uint32_t packed, bool last, int o0, int cnt, int sx,
                                                 int sy, int sz, int flags, double kx_sum) {
   const int nx = gm.nx;
   const double dT = gm.dT;
-  const uint32_t out_x_bit = sx > 0 ? CODE_WALL_XP : CODE_WALL_XM;
-  const uint32_t out_y_bit = sy > 0 ? CODE_WALL_YP : CODE_WALL_YM;
-  const uint32_t out_z_bit = sz > 0 ? CODE_WALL_ZP : CODE_WALL_ZM;
+  const bool out_x = packed & REC_WOUT_X, out_y = packed & REC_WOUT_Y, out_z = packed & REC_WOUT_Z;
   T sxk = T(0), syk = T(0), szk = T(0);
   for (int g = 0; g < cnt; ++g) {
     const T v = val[g * stride];
@@ -55,10 +53,10 @@ __device__ __noinline__ double cell_epilogue_3d(const GeomDev& gm, const T* val,
     szk = fma(ld<T>(gm.kza, o0 + g), v, szk);
   }
   const double dx = widen(sxk), dy = widen(syk), dz = widen(szk);
-  if (code & out_x_bit) atomicAdd(gm.wall_acc + cell * 6 + (sx > 0 ? 1 : 0), dx);
-  if (code & out_y_bit) atomicAdd(gm.wall_acc + cell * 6 + (sy > 0 ? 3 : 2), dy);
-  if (code & out_z_bit) atomicAdd(gm.wall_acc + cell * 6 + (sz > 0 ? 5 : 4), dz);
-  const bool hot = last && !(code & out_x_bit);
+  if (out_x) atomicAdd(gm.wall_acc + cell * 6 + (sx > 0 ? 1 : 0), dx);
+  if (out_y) atomicAdd(gm.wall_acc + cell * 6 + (sy > 0 ? 3 : 2), dy);
+  if (out_z) atomicAdd(gm.wall_acc + cell * 6 + (sz > 0 ? 5 : 4), dz);
+  const bool hot = last && !out_x;
   double phi = 0.0;
   if (hot) phi = (sx > 0 ? dx : -dx) + (sx > 0 ? dT * kx_sum : 0.0);
   if (flags & SWEEP_FLUX) {
@@ -66,7 +64,7 @@ __device__ __noinline__ double cell_epilogue_3d(const GeomDev& gm, const T* val,
     atomicAdd(gm.J_acc + 3 * cell + 0, sx > 0 ? dx : -dx);
     atomicAdd(gm.J_acc + 3 * cell + 1, sy > 0 ? dy : -dy);
     atomicAdd(gm.J_acc + 3 * cell + 2, sz > 0 ? dz : -dz);
-    if (!(code & out_x_bit)) {
+    if (!out_x) {
       const int sec = sx > 0 ? (x + 1) % nx : x;
       const bool jmp = sx > 0 && x == nx - 1;
       atomicAdd(gm.phi_sec + sec, (sx > 0 ? dx : -dx) + (jmp ? dT * kx_sum : 0.0));
@@ -174,12 +172,6 @@ __global__ void __launch_bounds__(Sweep3DCfg<RMAX>::NT, 1) sweep3d_kernel(const 
     if (kp > 0) tz = t - tpp;
     else if (gm.pz) tz = (nz - 1) * tpp + jb;
   }
-  const uint32_t in_x_bit = sx > 0 ? CODE_WALL_XM : CODE_WALL_XP;
-  const uint32_t in_y_bit = sy > 0 ? CODE_WALL_YM : CODE_WALL_YP;
-  const uint32_t in_z_bit = sz > 0 ? CODE_WALL_ZM : CODE_WALL_ZP;
-  const uint32_t out_wall_bits = (sx > 0 ? CODE_WALL_XP : CODE_WALL_XM) |
-                                 (sy > 0 ? CODE_WALL_YP : CODE_WALL_YM) |
-                                 (sz > 0 ? CODE_WALL_ZP : CODE_WALL_ZM);
   double phi = 0.0;
   int s = d0;
 
@@ -224,11 +216,10 @@ __global__ void __launch_bounds__(Sweep3DCfg<RMAX>::NT, 1) sweep3d_kernel(const 
         const int r = RMAX - 1 - rr;
         const T src = rc[r][0], twx = rc[r][1], twy = rc[r][2], twz = rc[r][3];
         const uint32_t packed = rec3_bits<T>(rc[r][4]);
-        const uint32_t code = (packed >> 22) & 0xffu;
-        const bool wx = code & in_x_bit, wy = code & in_y_bit, wz = code & in_z_bit;
-        const bool jump = ((packed >> 30) & 1u) && !wx;
+        const bool wx = packed & REC_WIN_X, wy = packed & REC_WIN_Y, wz = packed & REC_WIN_Z;
+        const bool jump = packed & REC_JUMP;
         T sval = T(1);
-        if (HAS_S) sval = (T)__ldg(sv_ptr + (packed & 0x3fffffu));
+        if (HAS_S) sval = (T)__ldg(sv_ptr + (packed & REC_CELL_MASK));
         T tl = T(0);
 #pragma unroll
         for (int g = 0; g < G; ++g) {
@@ -250,14 +241,15 @@ __global__ void __launch_bounds__(Sweep3DCfg<RMAX>::NT, 1) sweep3d_kernel(const 
           v[r][g] = val;
           tl = fma(AW[g], val, tl);
         }
-        if (code & CODE_SOLID) {
+        if (packed & REC_SOLID) {
           atomicAdd(tl_row + r, widen(tl));
-          const bool last = (packed >> 31) & 1u;
-          if ((code & out_wall_bits) || last || rare_pass) {
+          const bool last = packed & REC_LAST;
+          if ((packed & (REC_WOUT_X | REC_WOUT_Y | REC_WOUT_Z)) || last || rare_pass) {
 #pragma unroll
             for (int g = 0; g < G; ++g) scratch[g * nthr + t] = v[r][g];
-            phi += cell_epilogue_3d<T, G>(gm, scratch + t, nthr, (int)(packed & 0x3fffffu), code,
-                                          last, o0, cnt, sx, sy, sz, flags, kx_sum);
+            const int cell = (int)(packed & REC_CELL_MASK);
+            phi += cell_epilogue_3d<T, G>(gm, scratch + t, nthr, cell, packed, last, o0,
+                                          cnt, sx, sy, sz, flags, kx_sum);
           }
         }
       }
