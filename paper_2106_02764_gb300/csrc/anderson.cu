@@ -13,15 +13,18 @@
 //
 // Per iteration (after the finalisation):
 //   aa_residual_kernel: f_k = g_k - x_k into history slot, dots f_k . F_j for
-//     every slot (block partials + FP64 atomics); the geometry's last block
-//     updates the Gram matrix and solves the normal equations for gamma
-//     (Gaussian elimination with partial pivoting, Tikhonov-regularised),
-//     giving the mixing coefficients c_j of x_{k+1} = sum_j c_j (X_j + F_j).
+//     every slot as per-block partials;
+//   aa_solve_kernel: sums the partials, updates the Gram matrix and solves
+//     the normal equations for gamma (Gaussian elimination with partial
+//     pivoting, Tikhonov-regularised), giving the mixing coefficients c_j of
+//     x_{k+1} = sum_j c_j (X_j + F_j);
 //   aa_mix_kernel: x_{k+1} into the state and into the next history slot, and
-//     the sweep inputs derived from it (s T_L, wall temperatures per side).
+//     the sweep inputs derived from it (s T_L, wall temperatures per side,
+//     octant records).
 #include <math.h>
 
 #include "obte_internal.h"
+#include "records.cuh"
 
 namespace {
 
@@ -83,23 +86,26 @@ __global__ void aa_residual_kernel(const GeomDev* geoms) {
   const int k = *g.aa_k;               // Anderson step (0 = first sweep)
   const int cur = k % S;
   __shared__ double red[8][32];
-  __shared__ bool s_last;
-  double dots[8];
-  for (int j = 0; j < 8; ++j) dots[j] = 0.0;
   const int tid = blockIdx.x * blockDim.x + threadIdx.x;
   const int stride = gridDim.x * blockDim.x;
   const int nvalid = k + 1 < S ? k + 1 : S;  // slots holding residuals after this step
   // slot j of the window (j = 0: this step) -> its base pointers
   const double* fdj[8];
   const T* ftj[8];
+#pragma unroll
   for (int j = 0; j < 8; ++j) {
     const int sl = (k - j + S * 8) % S;
     fdj[j] = AAView<T>::fd(g, sl);
     ftj[j] = AAView<T>::ft(g, sl);
   }
+  // FP64 part (T_L, T_w): few elements, FP64 products and sums
+  double dots[8];
+#pragma unroll
+  for (int j = 0; j < 8; ++j) dots[j] = 0.0;
   double* fcur = AAView<T>::fd(g, cur);
   const double* xcur = AAView<T>::xd(g, cur);
-  for (long i = tid; i < g.aa_nd; i += stride) {
+  const long nd = g.aa_nd;
+  for (long i = tid; i < nd; i += stride) {
     const double f = state_d(g, i) - xcur[i];
     fcur[i] = f;
     dots[0] += f * f;
@@ -107,15 +113,16 @@ __global__ void aa_residual_kernel(const GeomDev* geoms) {
     for (int j = 1; j < 8; ++j)
       if (j < nvalid) dots[j] += f * fdj[j][i];
   }
-  // row values: sweep precision products, summed per thread in the same
-  // precision over its few elements, then widened for the block reduction
+  // row values: products and the thread / warp sums in the sweep precision,
+  // widened once per warp
   T* ftc = AAView<T>::ft(g, cur);
   const T* xtc = AAView<T>::xt(g, cur);
   const T* front = reinterpret_cast<const T*>(g.front);
   T tdots[8];
 #pragma unroll
   for (int j = 0; j < 8; ++j) tdots[j] = T(0);
-  for (long i = tid; i < g.aa_nt; i += stride) {
+  const long nt = g.aa_nt;
+  for (long i = tid; i < nt; i += stride) {
     const T f = front[i] - xtc[i];
     ftc[i] = f;
     tdots[0] = fma(f, f, tdots[0]);
@@ -123,39 +130,53 @@ __global__ void aa_residual_kernel(const GeomDev* geoms) {
     for (int j = 1; j < 8; ++j)
       if (j < nvalid) tdots[j] = fma(f, ftj[j][i], tdots[j]);
   }
+  const unsigned FULL = 0xffffffffu;
+  const bool any_d = __any_sync(FULL, (long)(tid - (threadIdx.x & 31)) < nd);
 #pragma unroll
-  for (int j = 0; j < 8; ++j) dots[j] += (double)tdots[j];
-  // block reduction of the dots, then FP64 atomics into the geometry's buffer
   for (int j = 0; j < 8; ++j) {
-    double v = dots[j];
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    T t = tdots[j];
+    for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(FULL, t, o);
+    double v = (double)t;
+    if (any_d) {
+      double d = dots[j];
+      for (int o = 16; o > 0; o >>= 1) d += __shfl_xor_sync(FULL, d, o);
+      v += d;
+    }
     if ((threadIdx.x & 31) == 0) red[j][threadIdx.x >> 5] = v;
   }
   __syncthreads();
-  if (threadIdx.x < 8 && threadIdx.x < nvalid) {
+  if (threadIdx.x < 8) {
     double v = 0.0;
     for (int w = 0; w < (int)((blockDim.x + 31) >> 5); ++w) v += red[threadIdx.x][w];
-    atomicAdd(g.aa_dots + threadIdx.x, v);
-    __threadfence();  // visible device-wide before this block is counted
+    g.blk_part[(size_t)blockIdx.x * 8 + threadIdx.x] = v;
   }
+}
+
+// After aa_residual_kernel (one block of 8 warps per geometry): warp j sums
+// dot j over the block partials; thread 0 updates the Gram matrix and solves
+// for the mixing coefficients.
+__global__ void aa_solve_kernel(const GeomDev* geoms, int nblocks) {
+  const GeomDev& g = geoms[blockIdx.x];
+  if (g.aa_m <= 0 || *(volatile int*)g.done) return;
+  __shared__ double dv[8];
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  double v = 0.0;
+  for (int b = lane; b < nblocks; b += 32) v += g.blk_part[(size_t)b * 8 + w];
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  if (lane == 0) dv[w] = v;
   __syncthreads();
-  if (threadIdx.x == 0) {
-    __threadfence();
-    s_last = atomicAdd(g.aa_count, 1u) == gridDim.x - 1;
-  }
-  __syncthreads();
-  if (!s_last || threadIdx.x != 0) return;
-  __threadfence();
-  // last block: Gram matrix of the residual history (slot indices), then gamma
-  volatile double* dv = g.aa_dots;
+  if (threadIdx.x != 0) return;
+  const int S = g.aa_m + 1;
+  const int k = *g.aa_k;
+  const int cur = k % S;
+  const int nvalid = k + 1 < S ? k + 1 : S;
+  // Gram matrix of the residual history (slot indices), then gamma
   double* gram = g.aa_gram;  // [S][S] by slot
   for (int j = 0; j < nvalid; ++j) {
     const int sl = (k - j + S * 8) % S;
     gram[cur * S + sl] = dv[j];
     gram[sl * S + cur] = dv[j];
   }
-  for (int j = 0; j < 8; ++j) g.aa_dots[j] = 0.0;
-  *g.aa_count = 0u;
   // logical order oldest .. newest: slot(l) = (k - (nvalid - 1) + l) mod S
   const int mk = nvalid - 1;  // number of differences
   double coef[8];
@@ -215,6 +236,7 @@ __global__ void aa_mix_kernel(const GeomDev* geoms) {
   T* src = reinterpret_cast<T*>(g.src);
   T* twc = reinterpret_cast<T*>(g.twc);
   double* xn = AAView<T>::xd(g, nxt);
+  const bool recs = g.rec4 != nullptr;
   for (long i = tid; i < g.aa_nd; i += stride) {
     double v = 0.0;
 #pragma unroll
@@ -223,11 +245,15 @@ __global__ void aa_mix_kernel(const GeomDev* geoms) {
     if (i < g.n_cells) {
       if (!(g.code[i] & CODE_SOLID)) v = 0.0;
       g.TL[i] = v;
-      src[i] = (T)(g.s ? g.s[i] * v : v);
+      const T sv = (T)(g.s ? g.s[i] * v : v);
+      src[i] = sv;
+      if (recs) obte::rec_put_src<T>(g, (int)i, sv);
     } else {
       const long f = i - g.n_cells;
       g.Tw[f] = v;
-      twc[(size_t)g.wall_cell[f] * 6 + g.wall_side[f]] = (T)v;
+      const int cell = g.wall_cell[f], sd = g.wall_side[f];
+      twc[(size_t)cell * 6 + sd] = (T)v;
+      if (recs) obte::rec_put_wall<T>(g, cell, sd, (T)v);
     }
     xn[i] = v;
   }
@@ -267,8 +293,6 @@ __global__ void aa_init_kernel(const GeomDev* geoms) {
   for (long i = tid; i < g.aa_nt; i += stride) xt0[i] = front[i];
   if (tid == 0) {
     *g.aa_k = 0;
-    *g.aa_count = 0u;
-    for (int j = 0; j < 8; ++j) g.aa_dots[j] = 0.0;
   }
 }
 
@@ -285,11 +309,14 @@ cudaError_t launch_anderson_init(const GeomDev* geoms_dev, int n_geoms, int prec
 cudaError_t launch_anderson_step(const GeomDev* geoms_dev, int n_geoms, int precision, int blocks,
                                  cudaStream_t st) {
   dim3 grid(blocks, n_geoms);
+  if (blocks > kMaxPartBlocks) return cudaErrorInvalidValue;
   if (precision == 0) {
     aa_residual_kernel<double><<<grid, 256, 0, st>>>(geoms_dev);
+    aa_solve_kernel<<<n_geoms, 256, 0, st>>>(geoms_dev, blocks);
     aa_mix_kernel<double><<<grid, 256, 0, st>>>(geoms_dev);
   } else {
     aa_residual_kernel<float><<<grid, 256, 0, st>>>(geoms_dev);
+    aa_solve_kernel<<<n_geoms, 256, 0, st>>>(geoms_dev, blocks);
     aa_mix_kernel<float><<<grid, 256, 0, st>>>(geoms_dev);
   }
   aa_step_kernel<<<(n_geoms + 127) / 128, 128, 0, st>>>(geoms_dev, n_geoms);

@@ -79,12 +79,13 @@ struct obte_ctx {
   void *aa_xt = nullptr, *aa_ft = nullptr;
   int* aa_int = nullptr;
   void* rec4 = nullptr;
-  double* tlq = nullptr;
+  int* rec_idx = nullptr;
+  double* blk_part = nullptr;  // per-block partials of the finalize / Anderson reductions
   double* Tw = nullptr;
   double* wall_acc = nullptr;
   void* front = nullptr;
   double* scal = nullptr;    // phi_acc, delta_max[2]
-  int* ctrl = nullptr;       // done, iter, nonfinite, fin_count
+  int* ctrl = nullptr;       // done, iter, nonfinite
   double* hist = nullptr;
   double* TF = nullptr;
   double* fwork = nullptr;
@@ -149,7 +150,8 @@ struct obte_ctx {
     aa_xt = aa_ft = nullptr;
     aa_int = nullptr;
     rec4 = nullptr;
-    tlq = nullptr;
+    rec_idx = nullptr;
+    blk_part = nullptr;
     s_d = nullptr;
     wall_den_d = nullptr;
     for (auto& a : tab_d)
@@ -713,9 +715,9 @@ static int prepare_state(obte_ctx* ctx, int precision, int G, int R, bool warp, 
     ctx->drop_graph();
     // (re)allocate everything that depends on the precision
     ctx->dfree(ctx->rec4);
-    ctx->dfree(ctx->tlq);
+    ctx->dfree(ctx->rec_idx);
     ctx->rec4 = nullptr;
-    ctx->tlq = nullptr;
+    ctx->rec_idx = nullptr;
     ctx->rec_w_alloc = 0;
     for (void* p : {(void*)ctx->aa_xd, (void*)ctx->aa_fd, ctx->aa_xt, ctx->aa_ft, (void*)ctx->aa_small,
                     (void*)ctx->aa_int})
@@ -763,14 +765,17 @@ static int prepare_state(obte_ctx* ctx, int precision, int G, int R, bool warp, 
   const int rec_w = k3d ? 8 : (warp ? 4 : 0);     // values per skewed record
   if (rec_w && ctx->rec_w_alloc != rec_w) {
     ctx->dfree(ctx->rec4);
-    ctx->dfree(ctx->tlq);
+    ctx->dfree(ctx->rec_idx);
     const size_t e = precision == 0 ? 8 : 4;
     ctx->rec4 = ctx->dalloc((size_t)nq * rec_w * e * (size_t)ctx->n_cells);
-    ctx->tlq = ctx->dalloc_t<double>((size_t)nq * ctx->n_cells);
+    ctx->rec_idx = ctx->dalloc_t<int>((size_t)nq * ctx->n_cells);
     NEED(ctx->rec4);
-    NEED(ctx->tlq);
-    CK(cudaMemsetAsync(ctx->tlq, 0, sizeof(double) * nq * (size_t)ctx->n_cells, ctx->stream));
+    NEED(ctx->rec_idx);
     ctx->rec_w_alloc = rec_w;
+  }
+  if (!ctx->blk_part) {
+    ctx->blk_part = ctx->dalloc_t<double>((size_t)kMaxPartBlocks * 8);
+    NEED(ctx->blk_part);
   }
   const int aa_m = std::max(0, std::min(op.accel, 7));
   const long aa_nd = (long)ctx->n_cells + ctx->n_walls;
@@ -806,11 +811,9 @@ static int prepare_state(obte_ctx* ctx, int precision, int G, int R, bool warp, 
     g.aa_fd = ctx->aa_fd;
     g.aa_xt = ctx->aa_xt;
     g.aa_ft = ctx->aa_ft;
-    g.aa_dots = ctx->aa_small;
     g.aa_gram = ctx->aa_small + 8;
     g.aa_coef = ctx->aa_small + 72;
     g.aa_k = ctx->aa_int;
-    g.aa_count = reinterpret_cast<unsigned int*>(ctx->aa_int + 1);
   }
   g.nx = Nx;
   g.ny = Ny;
@@ -839,7 +842,8 @@ static int prepare_state(obte_ctx* ctx, int precision, int G, int R, bool warp, 
   g.wall_side = ctx->wall_side_d;
   g.twc = ctx->twc;
   g.rec4 = rec_w ? ctx->rec4 : nullptr;
-  g.tlq = rec_w ? ctx->tlq : nullptr;
+  g.rec_idx = rec_w ? ctx->rec_idx : nullptr;
+  g.blk_part = ctx->blk_part;
   g.rec_w = rec_w;
   g.front = ctx->front;
   g.phi_acc = ctx->scal;
@@ -864,7 +868,6 @@ static int prepare_state(obte_ctx* ctx, int precision, int G, int R, bool warp, 
   g.done = ctx->ctrl + 0;
   g.iter = ctx->ctrl + 1;
   g.nonfinite = ctx->ctrl + 2;
-  g.fin_count = reinterpret_cast<unsigned int*>(ctx->ctrl + 3);
   g.kappa_hist = ctx->hist;
   g.max_hist = kMaxHist;
   g.tol = op.tol;
@@ -1074,10 +1077,6 @@ static int run_iterations(obte_ctx* ctx, const obte_solve_opts& op, int* iters, 
                                  aa_blocks(ctx->n_cells, ctx->O, ctx->n[1] * ctx->n[2]), ctx->stream);
         if (e != cudaSuccess) return e;
       }
-      if (ctx->warp || ctx->k3d) {
-        e = launch_build_records(ctx->gd, 1, ctx->precision, finalize_blocks(ctx->n_cells), ctx->stream);
-        if (e != cudaSuccess) return e;
-      }
       if (op.profile && (e = cudaEventRecordWithFlags(ev[3 * i + 2], ctx->stream, cudaEventRecordExternal)) != cudaSuccess) return e;
     }
     return cudaSuccess;
@@ -1282,7 +1281,6 @@ static int run_flux_pass(obte_ctx* ctx) {
   CK(sweep_once(ctx, SWEEP_FLUX));
   // the pass does not advance the iterate: drop its moment accumulations
   CK(cudaMemsetAsync(ctx->TL_acc, 0, sizeof(double) * ctx->n_cells, ctx->stream));
-  if (ctx->tlq) CK(cudaMemsetAsync(ctx->tlq, 0, sizeof(double) * (ctx->dim == 3 ? 8 : 4) * (size_t)ctx->n_cells, ctx->stream));
   CK(cudaMemsetAsync(ctx->wall_acc, 0, sizeof(double) * 6 * (size_t)ctx->n_cells, ctx->stream));
   CK(cudaMemsetAsync(ctx->scal, 0, sizeof(double), ctx->stream));
   int one = 1;
@@ -1448,7 +1446,6 @@ extern "C" int obte_kappa_grad_s(obte_ctx* ctx, double* out, size_t max_field_by
     CK(launch_grad_contract2(ctx->code_d, ctx->TL, ctx->n_cells, rec, (int)b.size(), revl_d, a_d,
                              jscale, grad_d, ctx->precision, ctx->stream));
     CK(cudaMemsetAsync(ctx->TL_acc, 0, sizeof(double) * ctx->n_cells, ctx->stream));
-    if (ctx->tlq) CK(cudaMemsetAsync(ctx->tlq, 0, sizeof(double) * (ctx->dim == 3 ? 8 : 4) * (size_t)ctx->n_cells, ctx->stream));
     CK(cudaMemsetAsync(ctx->wall_acc, 0, sizeof(double) * 6 * (size_t)ctx->n_cells, ctx->stream));
     CK(cudaMemsetAsync(ctx->scal, 0, sizeof(double), ctx->stream));
     CK(cudaStreamSynchronize(ctx->stream));
@@ -1619,10 +1616,6 @@ extern "C" int obte_solve_batch(obte_ctx* const* ctxs, int n, const obte_solve_o
       if (e != cudaSuccess) return e;
       if (op.accel > 0) {
         e = launch_anderson_step(gds, n, prec, aa_blocks(max_cells, max_ord, max_rows), ctx->stream);
-        if (e != cudaSuccess) return e;
-      }
-      if (v.warp) {
-        e = launch_build_records(gds, n, prec, finalize_blocks(max_cells), ctx->stream);
         if (e != cudaSuccess) return e;
       }
     }
@@ -1884,7 +1877,6 @@ extern "C" int obte_kappa_grad_s_noalloc(obte_ctx* ctx, double* out) {
     CK(launch_grad_contract2(ctx->code_d, ctx->TL, ctx->n_cells, rec, (int)b.size(), revl_d, a_d,
                              jscale, grad_d, ctx->precision, ctx->stream));
     CK(cudaMemsetAsync(ctx->TL_acc, 0, sizeof(double) * ctx->n_cells, ctx->stream));
-    if (ctx->tlq) CK(cudaMemsetAsync(ctx->tlq, 0, sizeof(double) * (ctx->dim == 3 ? 8 : 4) * (size_t)ctx->n_cells, ctx->stream));
     CK(cudaMemsetAsync(ctx->wall_acc, 0, sizeof(double) * 6 * (size_t)ctx->n_cells, ctx->stream));
     CK(cudaMemsetAsync(ctx->scal, 0, sizeof(double), ctx->stream));
     CK(cudaStreamSynchronize(ctx->stream));  // host vectors above are copy sources

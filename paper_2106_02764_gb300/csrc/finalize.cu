@@ -6,92 +6,79 @@
 #include <algorithm>
 
 #include "obte_internal.h"
+#include "records.cuh"
 
 namespace {
 
-__device__ __forceinline__ void atomic_max_nonneg(double* addr, double v) {
-  // non-negative doubles order like their bit patterns
-  atomicMax(reinterpret_cast<unsigned long long*>(addr), (unsigned long long)__double_as_longlong(v));
-}
-
-// T_L <- sum_o a_o T_o (E2), T_w <- wall numerator / denominator (E3),
-// kappa from the hot-face flux, then the stopping test of Algorithm 1 in the
-// last block of each geometry.  Grid: x = blocks per geometry, y = geometry.
+// T_L <- sum_o a_o T_o (E2), T_w <- wall numerator / denominator (E3), the
+// sweep inputs derived from them, and each block's max |dT_L| into its
+// partial slot.  Grid: x = blocks per geometry, y = geometry.
 template <typename T>
 __global__ void finalize_kernel(const GeomDev* geoms) {
   const GeomDev& g = geoms[blockIdx.y];
   if (*(volatile int*)g.done) return;
   __shared__ double red[32];
-  __shared__ int s_nonfin;
-  __shared__ bool s_last;
-  if (threadIdx.x == 0) s_nonfin = 0;
-  __syncthreads();
   double dmax = 0.0;
   int nonfin = 0;
   T* src = reinterpret_cast<T*>(g.src);
+  const int n_cells = g.n_cells;
+  double* __restrict__ TL = g.TL;
+  double* __restrict__ TL_acc = g.TL_acc;
+  const uint8_t* __restrict__ code = g.code;
+  const double* __restrict__ sv = g.s;
+  const bool recs = g.rec4 != nullptr;
   const int stride = gridDim.x * blockDim.x;
-  for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < g.n_cells; c += stride) {
-    if (!(g.code[c] & CODE_SOLID)) continue;
-    double t;
-    if (g.tlq) {  // skewed per-octant accumulators (2D warp and 3D kernels)
-      const int x = c % g.nx, y = (c / g.nx) % g.ny, z = c / (g.nx * g.ny);
-      const int nq = g.dim == 3 ? 8 : 4;
-      t = 0.0;
-      for (int q = 0; q < nq; ++q) {
-        const int ip = (q & 1) ? g.nx - 1 - x : x;
-        const int jp = (q & 2) ? g.ny - 1 - y : y;
-        const int kp = (q & 4) ? g.nz - 1 - z : z;
-        const size_t k = ((size_t)q * g.nx + (ip + jp + kp) % g.nx) * g.rows + jp + (size_t)g.ny * kp;
-        t += g.tlq[k];
-        g.tlq[k] = 0.0;
-      }
-    } else {
-      t = g.TL_acc[c];
-      g.TL_acc[c] = 0.0;
-    }
+  for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < n_cells; c += stride) {
+    if (!(code[c] & CODE_SOLID)) continue;
+    const double t = TL_acc[c];
+    TL_acc[c] = 0.0;
     if (!isfinite(t)) nonfin = 1;
-    dmax = fmax(dmax, fabs(t - g.TL[c]));
-    g.TL[c] = t;
-    src[c] = (T)(g.s ? g.s[c] * t : t);
+    dmax = fmax(dmax, fabs(t - TL[c]));
+    TL[c] = t;
+    const T v = (T)(sv ? sv[c] * t : t);
+    src[c] = v;
+    if (recs) obte::rec_put_src<T>(g, c, v);
   }
   T* twc = reinterpret_cast<T*>(g.twc);
   for (int f = blockIdx.x * blockDim.x + threadIdx.x; f < g.n_walls; f += stride) {
-    const size_t k = (size_t)g.wall_cell[f] * 6 + g.wall_side[f];
+    const int c = g.wall_cell[f], sd = g.wall_side[f];
+    const size_t k = (size_t)c * 6 + sd;
     const double w = g.wall_acc[k] / g.wall_den[f];
     g.wall_acc[k] = 0.0;
     if (!isfinite(w)) nonfin = 1;
     g.Tw[f] = w;
-    twc[(size_t)g.wall_cell[f] * 6 + g.wall_side[f]] = (T)w;
+    twc[k] = (T)w;
+    if (recs) obte::rec_put_wall<T>(g, c, sd, (T)w);
   }
   for (int o = 16; o > 0; o >>= 1) dmax = fmax(dmax, __shfl_xor_sync(0xffffffffu, dmax, o));
   if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = dmax;
-  if (nonfin) atomicOr(&s_nonfin, 1);
+  if (nonfin) atomicOr(g.nonfinite, 1);
   __syncthreads();
   if (threadIdx.x == 0) {
     double m = 0.0;
     for (int w = 0; w < (int)((blockDim.x + 31) >> 5); ++w) m = fmax(m, red[w]);
-    atomic_max_nonneg(g.delta_max, m);
-    if (s_nonfin) atomicOr(g.nonfinite, 1);
-    __threadfence();
-    const unsigned prev = atomicAdd(g.fin_count, 1u);
-    s_last = (prev == gridDim.x - 1);
+    g.blk_part[blockIdx.x] = m;
   }
-  __syncthreads();
-  if (!s_last || threadIdx.x != 0) return;
-  __threadfence();
-  // last block of this geometry: kappa and the stopping test
-  volatile double* phi = g.phi_acc;
-  const double kappa = g.kappa_scale * (*phi);
-  *phi = 0.0;
+}
+
+// After finalize_kernel (one warp per geometry): max |dT_L| over the block
+// partials, kappa from the hot-face flux, and the stopping test of
+// Algorithm 1.
+__global__ void finalize_tail_kernel(const GeomDev* geoms, int nblocks) {
+  const GeomDev& g = geoms[blockIdx.x];
+  if (*(volatile int*)g.done) return;
+  double m = 0.0;
+  for (int b = threadIdx.x; b < nblocks; b += 32) m = fmax(m, g.blk_part[b]);
+  for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if (threadIdx.x != 0) return;
+  const double delta = m;
+  const double kappa = g.kappa_scale * (*g.phi_acc);
+  *g.phi_acc = 0.0;
   const int n = *g.iter + 1;
   *g.iter = n;
   if (n - 1 < g.max_hist) g.kappa_hist[n - 1] = kappa;
   const double prevk = (n >= 2 && n - 2 < g.max_hist) ? g.kappa_hist[n - 2] : NAN;
-  volatile double* dm = g.delta_max;
-  const double delta = *dm;
   g.delta_max[1] = delta;   // last iteration's max |dT_L|, for the host
-  *dm = 0.0;
-  *g.fin_count = 0u;
   bool conv = n >= 2 && n >= g.min_iter;
   if (g.tol > 0.0) conv = conv && fabs(kappa - prevk) <= g.tol * fabs(kappa);
   if (g.tol_TL > 0.0) conv = conv && delta <= g.tol_TL;
@@ -149,7 +136,6 @@ __global__ void init_state_kernel(const GeomDev* geoms, int gi, const double* T0
     *g.iter = 0;
     *g.done = 0;
     *g.nonfinite = 0;
-    *g.fin_count = 0u;
   }
 }
 
@@ -209,13 +195,14 @@ __global__ void grad_contract_kernel(const uint8_t* code, const double* TL, int 
   }
 }
 
-// Skewed per-quadrant cell records of the 2D warp kernel (layout in
-// obte_internal.h): source, wall temperatures through the upwind x / y sides,
-// packed cell index, face code and first / last column flags.
+// Skewed per-octant cell records of the 2D warp and 3D kernels (layout in
+// obte_internal.h): source, wall temperatures through the upwind sides, packed
+// cell index and octant flags; and each cell's record index per octant, by
+// which the finalisation and the Anderson step keep the records current.
 template <typename T>
 __global__ void build_records_kernel(const GeomDev* geoms) {
   const GeomDev& g = geoms[blockIdx.y];
-  if (!g.rec4 || *(volatile int*)g.done) return;
+  if (!g.rec4) return;
   const T* src = reinterpret_cast<const T*>(g.src);
   const T* twc = reinterpret_cast<const T*>(g.twc);
   T* rec = reinterpret_cast<T*>(g.rec4);
@@ -229,6 +216,7 @@ __global__ void build_records_kernel(const GeomDev* geoms) {
       const int jp = (q & 2) ? g.ny - 1 - y : y;
       const int kp = (q & 4) ? g.nz - 1 - z : z;
       const size_t k = ((size_t)q * g.nx + (ip + jp + kp) % g.nx) * g.rows + jp + (size_t)g.ny * kp;
+      g.rec_idx[(size_t)c * nq + q] = (int)k;
       const uint32_t in_x = (q & 1) ? CODE_WALL_XP : CODE_WALL_XM;
       const uint32_t in_y = (q & 2) ? CODE_WALL_YP : CODE_WALL_YM;
       const uint32_t in_z = (q & 4) ? CODE_WALL_ZP : CODE_WALL_ZM;
@@ -276,9 +264,11 @@ cudaError_t launch_build_records(const GeomDev* geoms_dev, int n_geoms, int prec
 
 cudaError_t launch_finalize(const GeomDev* geoms_dev, int n_geoms, int precision, int blocks,
                             cudaStream_t st) {
+  if (blocks > kMaxPartBlocks) return cudaErrorInvalidValue;
   dim3 grid(blocks, n_geoms);
   if (precision == 0) finalize_kernel<double><<<grid, 256, 0, st>>>(geoms_dev);
   else finalize_kernel<float><<<grid, 256, 0, st>>>(geoms_dev);
+  finalize_tail_kernel<<<n_geoms, 32, 0, st>>>(geoms_dev, blocks);
   return cudaGetLastError();
 }
 

@@ -73,9 +73,9 @@ struct GeomDev {
   //     {s_i T_L,i, T_w in-x side, T_w in-y side, packed};  rec_w = 8 (3D)
   //     {s_i T_L,i, T_w in-x, in-y, in-z sides, packed, 0, 0, 0}
   //   packed = cell (bits 0-21) | REC_* flags of octant q (bits 22-31)
-  //   tlq[(q * nx + s) * rows + row] = sum_o a_o T_o of the running sweep (FP64)
+  //   rec_idx[c * n_octants + q] = record index (q * nx + s) * rows + row of cell c
   void* rec4;
-  double* tlq;
+  int* rec_idx;
   int rec_w;              // values per record: 4 (2D warp kernel), 8 (3D kernel); 0: none
   void* front;            // [n_ord][rows] row values carried between iterations
   double* phi_acc;        // [1] hot-face flux of the running sweep
@@ -99,7 +99,7 @@ struct GeomDev {
   double* delta_max;      // [1] max |dT_L| (as FP64 bits, via atomicMax on u64)
   double tol, tol_TL;
   int min_iter, max_iter;
-  unsigned int* fin_count;  // [1] blocks done in finalize (last-block pattern)
+  double* blk_part;       // [kMaxPartBlocks * 8] per-block partials (finalize, Anderson dots)
   // Anderson acceleration (anderson.cu); aa_m = 0: plain source iteration
   int aa_m;               // window (history slots aa_m + 1 <= 8)
   long aa_nd, aa_nt;      // state lengths: FP64 part (T_L, T_w), row values
@@ -107,11 +107,9 @@ struct GeomDev {
   double* aa_fd;          // [(aa_m + 1) * aa_nd] residuals
   void* aa_xt;            // [(aa_m + 1) * aa_nt] iterates, sweep precision
   void* aa_ft;            // [(aa_m + 1) * aa_nt] residuals, sweep precision
-  double* aa_dots;        // [8]
   double* aa_gram;        // [(aa_m + 1)^2] residual Gram matrix by slot
   double* aa_coef;        // [8] mixing coefficients
   int* aa_k;              // [1] Anderson step
-  unsigned int* aa_count; // [1] last-block counter
   int* nonfinite;         // [1]
 };
 
@@ -150,6 +148,8 @@ int sweep_blocks_per_sm(int precision, int dim, int G, int RMAX, bool has_s, int
                         size_t smem);
 
 // finalize.cu
+constexpr int kMaxPartBlocks = 1216;  // blocks of the finalize / Anderson reductions
+// finalize_kernel then its one-warp tail (kappa, stopping test)
 cudaError_t launch_finalize(const GeomDev* geoms_dev, int n_geoms, int precision, int blocks,
                             cudaStream_t st);
 // Anderson acceleration (anderson.cu)
@@ -157,7 +157,7 @@ cudaError_t launch_anderson_init(const GeomDev* geoms_dev, int n_geoms, int prec
                                  cudaStream_t st);
 cudaError_t launch_anderson_step(const GeomDev* geoms_dev, int n_geoms, int precision, int blocks,
                                  cudaStream_t st);
-// rebuild the skewed records of the 2D warp kernel (after finalize / init)
+// build the skewed records and record indices (after the state is initialised)
 cudaError_t launch_build_records(const GeomDev* geoms_dev, int n_geoms, int precision, int blocks,
                                  cudaStream_t st);
 constexpr int kMaxSkewCells = 1 << 22;

@@ -11,14 +11,14 @@
 // one another.
 //
 // Data layout.  All cells a warp visits at step d lie on one diagonal
-// s = (i' + j') mod nx = (d + d0) mod nx of the quadrant frame.  The
-// finalisation stores, per quadrant, every cell's record (source s_i T_L,i,
-// the wall temperatures seen through its upwind x and y sides, and a packed
-// word with the cell index, face code and first / last column flags) at
-// [s][j'], so a lane's R rows of one step are R contiguous records.  They are
+// s = (i' + j') mod nx = (d + d0) mod nx of the quadrant frame.  Every cell
+// has one record per quadrant (source s_i T_L,i, the wall temperatures seen
+// through its upwind x and y sides, and a packed word with the cell index and
+// the quadrant's wall / jump / column flags) at [s][j'], kept current by the
+// finalisation, so a lane's R rows of one step are R contiguous records.  They are
 // prefetched one step ahead with cp.async into lane-private shared memory.
-// The T_L moment goes to a per-quadrant accumulator in the same skewed layout
-// (FP64 atomics); the finalisation sums the four quadrants.
+// The T_L moment of every solid cell goes to its FP64 accumulator (one atomic
+// per cell and warp, after all rows of the step).
 //
 // Cells are updated branch-free (pores too: a pore's value is never read by a
 // solid cell, whose faces towards a pore are walls); only the atomics and the
@@ -157,7 +157,7 @@ __global__ void __launch_bounds__(32 * WarpCfg<T, G, RMAX>::WPB, WarpCfg<T, G, R
     const bool active = lane < tpp;
     const int j0 = lane * R;
     const T* __restrict__ recq = reinterpret_cast<const T*>(gm.rec4) + (size_t)q * nx * ny * 4;
-    double* tlq = gm.tlq + (size_t)q * nx * ny;
+    double* tl_acc = gm.TL_acc;
     const double* __restrict__ sv_ptr = gm.s;
     double* wacc = gm.wall_acc;
 
@@ -248,7 +248,6 @@ __global__ void __launch_bounds__(32 * WarpCfg<T, G, RMAX>::WPB, WarpCfg<T, G, R
 #pragma unroll
       for (int g = 0; g < G; ++g) dn0[g] = __shfl_sync(FULL, v[RMAX - 1][g], below);
       if (active) {
-        double* tl_row = tlq + (size_t)s * ny + j0 - rb;
         uint32_t pk[RMAX];
         T tls[RMAX];
         // branch-free update of all rows of the step (top row first: the row
@@ -340,7 +339,8 @@ __global__ void __launch_bounds__(32 * WarpCfg<T, G, RMAX>::WPB, WarpCfg<T, G, R
         // being scheduled ahead of it
 #pragma unroll
         for (int r = 0; r < RMAX; ++r)
-          if ((RFIXED || r >= rb) && (pk[r] & REC_SOLID)) atomicAdd(tl_row + r, widen(tls[r]));
+          if ((RFIXED || r >= rb) && (pk[r] & REC_SOLID))
+            atomicAdd(tl_acc + (pk[r] & REC_CELL_MASK), widen(tls[r]));
       }
       s = s_next;
       __syncwarp();

@@ -17,8 +17,8 @@
 // finalisation stores every cell's record {s T_L, T_w through the upwind x,
 // y and z sides, packed cell / code / column flags} per octant at
 // [s][j' + ny k']: a thread's rows of one step are contiguous records, loaded
-// one step ahead into registers.  The T_L moment goes to per-octant FP64
-// accumulators in the same layout; the finalisation sums the octants.
+// one step ahead into registers.  The T_L moment goes to the cell's FP64
+// accumulator.
 //
 // Cells update branch-free (pore values never reach a solid cell, whose faces
 // towards a pore are walls); atomics and the rare epilogue (walls the
@@ -123,7 +123,7 @@ __global__ void __launch_bounds__(Sweep3DCfg<RMAX>::NT, 1) sweep3d_kernel(const 
   const bool active = kp < nz;
   const int row0 = j0 + ny * kp;
   const T* __restrict__ recq = reinterpret_cast<const T*>(gm.rec4) + (size_t)q * nx * rows * 8;
-  double* tlq = gm.tlq + (size_t)q * nx * rows;
+  double* tl_acc = gm.TL_acc;
   const double* __restrict__ sv_ptr = gm.s;
 
   T A0[G], AX[G], AY[G], AZ[G], AW[G], JX[G];
@@ -210,7 +210,6 @@ __global__ void __launch_bounds__(Sweep3DCfg<RMAX>::NT, 1) sweep3d_kernel(const 
       T dny[G];
 #pragma unroll
       for (int g = 0; g < G; ++g) dny[g] = (tb >= 0) ? XA(prv, RMAX - 1, g, tb) : T(0);
-      double* tl_row = tlq + (size_t)s * rows + row0;
 #pragma unroll
       for (int rr = 0; rr < RMAX; ++rr) {
         const int r = RMAX - 1 - rr;
@@ -242,7 +241,7 @@ __global__ void __launch_bounds__(Sweep3DCfg<RMAX>::NT, 1) sweep3d_kernel(const 
           tl = fma(AW[g], val, tl);
         }
         if (packed & REC_SOLID) {
-          atomicAdd(tl_row + r, widen(tl));
+          atomicAdd(tl_acc + (packed & REC_CELL_MASK), widen(tl));
           const bool last = packed & REC_LAST;
           if ((packed & (REC_WOUT_X | REC_WOUT_Y | REC_WOUT_Z)) || last || rare_pass) {
 #pragma unroll
