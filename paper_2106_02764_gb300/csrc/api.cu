@@ -785,9 +785,10 @@ static int prepare_state(obte_ctx* ctx, int precision, int G, int R, bool warp, 
                     (void*)ctx->aa_int})
       ctx->dfree(p);
     const size_t e = precision == 0 ? 8 : 4;
-    ctx->aa_xd = ctx->dalloc_t<double>((size_t)(aa_m + 1) * aa_nd);
+    // g(x) history slots plus the current iterate (last slot); f history
+    ctx->aa_xd = ctx->dalloc_t<double>((size_t)(aa_m + 2) * aa_nd);
     ctx->aa_fd = ctx->dalloc_t<double>((size_t)(aa_m + 1) * aa_nd);
-    ctx->aa_xt = ctx->dalloc(e * (size_t)(aa_m + 1) * aa_nt);
+    ctx->aa_xt = ctx->dalloc(e * (size_t)(aa_m + 2) * aa_nt);
     ctx->aa_ft = ctx->dalloc(e * (size_t)(aa_m + 1) * aa_nt);
     ctx->aa_small = ctx->dalloc_t<double>(8 + 64 + 8);
     ctx->aa_int = ctx->dalloc_t<int>(2);
@@ -807,10 +808,12 @@ static int prepare_state(obte_ctx* ctx, int precision, int G, int R, bool warp, 
   if (aa_m > 0) {
     g.aa_nd = aa_nd;
     g.aa_nt = aa_nt;
-    g.aa_xd = ctx->aa_xd;
+    g.aa_gd = ctx->aa_xd;
     g.aa_fd = ctx->aa_fd;
-    g.aa_xt = ctx->aa_xt;
+    g.aa_xcd = ctx->aa_xd + (size_t)(aa_m + 1) * aa_nd;
+    g.aa_gt = ctx->aa_xt;
     g.aa_ft = ctx->aa_ft;
+    g.aa_xct = static_cast<char*>(ctx->aa_xt) + (size_t)(aa_m + 1) * aa_nt * (precision == 0 ? 8 : 4);
     g.aa_gram = ctx->aa_small + 8;
     g.aa_coef = ctx->aa_small + 72;
     g.aa_k = ctx->aa_int;

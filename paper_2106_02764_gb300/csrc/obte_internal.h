@@ -103,13 +103,15 @@ struct GeomDev {
   // Anderson acceleration (anderson.cu); aa_m = 0: plain source iteration
   int aa_m;               // window (history slots aa_m + 1 <= 8)
   long aa_nd, aa_nt;      // state lengths: FP64 part (T_L, T_w), row values
-  double* aa_xd;          // [(aa_m + 1) * aa_nd] iterates
-  double* aa_fd;          // [(aa_m + 1) * aa_nd] residuals
-  void* aa_xt;            // [(aa_m + 1) * aa_nt] iterates, sweep precision
-  void* aa_ft;            // [(aa_m + 1) * aa_nt] residuals, sweep precision
+  double* aa_gd;          // [(aa_m + 1) * aa_nd] history of g(x)
+  double* aa_fd;          // [(aa_m + 1) * aa_nd] history of f = g(x) - x
+  double* aa_xcd;         // [aa_nd] current iterate
+  void* aa_gt;            // [(aa_m + 1) * aa_nt] the same for the row values, sweep precision
+  void* aa_ft;            // [(aa_m + 1) * aa_nt]
+  void* aa_xct;           // [aa_nt]
   double* aa_gram;        // [(aa_m + 1)^2] residual Gram matrix by slot
   double* aa_coef;        // [8] mixing coefficients
-  int* aa_k;              // [1] Anderson step
+  int* aa_k;              // [2] Anderson step; the step being mixed
   int* nonfinite;         // [1]
 };
 
