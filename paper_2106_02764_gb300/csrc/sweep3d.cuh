@@ -97,6 +97,7 @@ __global__ void __launch_bounds__(Sweep3DCfg<RMAX>::NT, 1) sweep3d_kernel(const 
   constexpr int NT = Sweep3DCfg<RMAX>::NT;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ double red[32];
+  __shared__ T kcoef[3][G];  // |K_gx|, |K_gy|, |K_gz| of the group (rare path only)
   const int nthr = NT;
   const int t = threadIdx.x;
   T* xall = reinterpret_cast<T*>(smem_raw);  // [2][RMAX][G][NT]
@@ -149,6 +150,15 @@ __global__ void __launch_bounds__(Sweep3DCfg<RMAX>::NT, 1) sweep3d_kernel(const 
     JX[g] = (T)(ax * (double)sx * dT);
     if (ok) kx_sum += (double)sx * (double)ld<T>(gm.kxa, o);
   }
+
+  if (t < G) {
+    const bool ok = t < cnt;
+    kcoef[0][t] = ok ? ld<T>(gm.kxa, o0 + t) : T(0);
+    kcoef[1][t] = ok ? ld<T>(gm.kya, o0 + t) : T(0);
+    kcoef[2][t] = ok ? ld<T>(gm.kza, o0 + t) : T(0);
+  }
+  const int out_side_x = sx > 0 ? 1 : 0, out_side_y = sy > 0 ? 3 : 2, out_side_z = sz > 0 ? 5 : 4;
+  double* wacc = gm.wall_acc;
 
   T v[RMAX][G];
   const T* front = reinterpret_cast<const T*>(gm.front);
@@ -210,6 +220,10 @@ __global__ void __launch_bounds__(Sweep3DCfg<RMAX>::NT, 1) sweep3d_kernel(const 
       T dny[G];
 #pragma unroll
       for (int g = 0; g < G; ++g) dny[g] = (tb >= 0) ? XA(prv, RMAX - 1, g, tb) : T(0);
+      uint32_t pk[RMAX];
+      T tls[RMAX];
+      // branch-free update of all rows (top row first: the row below in y
+      // still holds its previous value)
 #pragma unroll
       for (int rr = 0; rr < RMAX; ++rr) {
         const int r = RMAX - 1 - rr;
@@ -219,7 +233,7 @@ __global__ void __launch_bounds__(Sweep3DCfg<RMAX>::NT, 1) sweep3d_kernel(const 
         const bool jump = packed & REC_JUMP;
         T sval = T(1);
         if (HAS_S) sval = (T)__ldg(sv_ptr + (packed & REC_CELL_MASK));
-        T tl = T(0);
+        T tl = T(0), tl2 = T(0);
 #pragma unroll
         for (int g = 0; g < G; ++g) {
           const T ux = wx ? twx : v[r][g];
@@ -238,20 +252,61 @@ __global__ void __launch_bounds__(Sweep3DCfg<RMAX>::NT, 1) sweep3d_kernel(const 
             val = acc;
           }
           v[r][g] = val;
-          tl = fma(AW[g], val, tl);
+          if (g & 1) tl2 = fma(AW[g], val, tl2);
+          else tl = fma(AW[g], val, tl);
         }
-        if (packed & REC_SOLID) {
-          atomicAdd(tl_acc + (packed & REC_CELL_MASK), widen(tl));
+        pk[r] = packed;
+        tls[r] = tl + tl2;
+      }
+      uint32_t rare_mask = 0;
+#pragma unroll
+      for (int r = 0; r < RMAX; ++r) {
+        const bool rare =
+            rare_pass || (pk[r] & (REC_WOUT_X | REC_WOUT_Y | REC_WOUT_Z | REC_LAST));
+        rare_mask |= (((pk[r] & REC_SOLID) && rare) ? 1u : 0u) << r;
+      }
+      // cells leaving into a wall, the hot-contact column, flux / record passes
+      if (rare_mask) {
+#pragma unroll
+        for (int r = 0; r < RMAX; ++r) {
+          if (!((rare_mask >> r) & 1u)) continue;
+          const uint32_t packed = pk[r];
+          const int cell = (int)(packed & REC_CELL_MASK);
           const bool last = packed & REC_LAST;
-          if ((packed & (REC_WOUT_X | REC_WOUT_Y | REC_WOUT_Z)) || last || rare_pass) {
+          if (rare_pass) {
 #pragma unroll
             for (int g = 0; g < G; ++g) scratch[g * nthr + t] = v[r][g];
-            const int cell = (int)(packed & REC_CELL_MASK);
-            phi += cell_epilogue_3d<T, G>(gm, scratch + t, nthr, cell, packed, last, o0,
-                                          cnt, sx, sy, sz, flags, kx_sum);
+            phi += cell_epilogue_3d<T, G>(gm, scratch + t, nthr, cell, packed, last, o0, cnt, sx,
+                                          sy, sz, flags, kx_sum);
+            continue;
+          }
+          if (packed & (REC_WOUT_X | REC_LAST)) {
+            T sk = T(0);
+#pragma unroll
+            for (int g = 0; g < G; ++g) sk = fma(kcoef[0][g], v[r][g], sk);
+            const double dk = widen(sk);
+            if (packed & REC_WOUT_X) atomicAdd(wacc + (size_t)cell * 6 + out_side_x, dk);
+            else phi += (sx > 0 ? dk : -dk) + (sx > 0 ? dT * kx_sum : 0.0);
+          }
+          if (packed & REC_WOUT_Y) {
+            T sk = T(0);
+#pragma unroll
+            for (int g = 0; g < G; ++g) sk = fma(kcoef[1][g], v[r][g], sk);
+            atomicAdd(wacc + (size_t)cell * 6 + out_side_y, widen(sk));
+          }
+          if (packed & REC_WOUT_Z) {
+            T sk = T(0);
+#pragma unroll
+            for (int g = 0; g < G; ++g) sk = fma(kcoef[2][g], v[r][g], sk);
+            atomicAdd(wacc + (size_t)cell * 6 + out_side_z, widen(sk));
           }
         }
       }
+      // moment atomics after all rows (a generic-address atomic between rows
+      // would keep later shared-memory loads from moving ahead of it)
+#pragma unroll
+      for (int r = 0; r < RMAX; ++r)
+        if (pk[r] & REC_SOLID) atomicAdd(tl_acc + (pk[r] & REC_CELL_MASK), widen(tls[r]));
 #pragma unroll
       for (int r = 0; r < RMAX; ++r)
 #pragma unroll
