@@ -38,6 +38,24 @@ __device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
   const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
   asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
 }
+// the same with compile-time byte offsets on both addresses
+template <int SOFF, int GOFF>
+__device__ __forceinline__ void cp_async16_off(unsigned smem, const void* gmem) {
+  asm volatile("cp.async.cg.shared.global [%0+%2], [%1+%3], 16;\n" ::"r"(smem), "l"(gmem), "n"(SOFF),
+               "n"(GOFF)
+               : "memory");
+}
+// copies k = K .. KMAX-1 of a coalesced record run: part 32 k + lane, whose
+// slot is the lane's offset for k mod KP shifted by 32 (k - k mod KP) / CH
+template <int K, int KMAX, int KP, int CH>
+struct CpRun {
+  static __device__ __forceinline__ void go(const unsigned* pslot, unsigned boff, const char* gl) {
+    if constexpr (K < KMAX) {
+      cp_async16_off<(K / KP) * KP * 32 / CH * 16, K * 512>(pslot[K % KP] + boff, gl);
+      CpRun<K + 1, KMAX, KP, CH>::go(pslot, boff, gl);
+    }
+  }
+};
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 template <int N>
 __device__ __forceinline__ void cp_async_wait() {
@@ -204,9 +222,23 @@ __global__ void __launch_bounds__(32 * WarpCfg<T, G, RMAX>::WPB, WarpCfg<T, G, R
     // Prefetch the records of diagonal s into buffer b.  With RFIXED the
     // warp's ny records are one contiguous run and part m of it is copied by
     // lane m % 32 (coalesced); otherwise every lane copies its own rows.
+    // RFIXED copies: part m = 32 k + lane of the run goes to a slot that
+    // repeats with period KP in k up to a shift of 32 KP / CH slots, so two to
+    // four lane-constant offsets and compile-time shifts address every copy
+    constexpr int KP = CH == 1 ? (RMAX >= 8 ? 2 : 1) : (RMAX >= 8 ? 4 : (RMAX == 4 ? 2 : 1));
+    unsigned pslot[KP];
+#pragma unroll
+    for (int k = 0; k < KP; ++k) {
+      const int m = k * 32 + lane;
+      const int jr = m / CH, c = m % CH;
+      pslot[k] = (unsigned)__cvta_generic_to_shared(&recbuf[wib][0][c][rec_slot<RMAX>(jr / RMAX, jr % RMAX)]);
+    }
+    const bool full_run = ny * CH >= 32 * RMAX * CH;  // every lane copies every k
     auto prefetch = [&](int s, int b) {
       const char* g0 = reinterpret_cast<const char*>(recq + (size_t)s * ny * 4);
-      if (RFIXED) {
+      if (RFIXED && full_run) {
+        CpRun<0, RMAX * CH, KP, CH>::go(pslot, (unsigned)(b * CH * 32 * RMAX * 16), g0 + lane * 16);
+      } else if (RFIXED) {
         const int n16 = ny * CH;
 #pragma unroll
         for (int k = 0; k < RMAX * CH; ++k) {
@@ -294,21 +326,20 @@ __global__ void __launch_bounds__(32 * WarpCfg<T, G, RMAX>::WPB, WarpCfg<T, G, R
             tls[r] = tl + tl2;
           }
         }
-        uint32_t rare_mask = 0;
+        constexpr uint32_t RARE = REC_WOUT_X | REC_WOUT_Y | REC_LAST;
+        uint32_t any = 0;
 #pragma unroll
-        for (int r = 0; r < RMAX; ++r) {
-          if (!(RFIXED || r >= rb)) continue;
-          const bool rare = rare_pass || (pk[r] & (REC_WOUT_X | REC_WOUT_Y | REC_LAST));
-          rare_mask |= (((pk[r] & REC_SOLID) && rare) ? 1u : 0u) << r;
-        }
+        for (int r = 0; r < RMAX; ++r)
+          if (RFIXED || r >= rb) any |= pk[r];
         // cells leaving into a wall, the hot-contact column, flux / record passes
-        if (rare_mask) {
+        if ((any & RARE) || rare_pass) {
           const T* KX = kcoef[wib][0];
           const T* KY = kcoef[wib][1];
 #pragma unroll
           for (int r = 0; r < RMAX; ++r) {
-            if (!(RFIXED || r >= rb) || !((rare_mask >> r) & 1u)) continue;
+            if (!(RFIXED || r >= rb)) continue;
             const uint32_t packed = pk[r];
+            if (!(packed & REC_SOLID) || !((packed & RARE) || rare_pass)) continue;
             const int cell = (int)(packed & REC_CELL_MASK);
             const bool last = packed & REC_LAST;
             if (rare_pass) {
@@ -340,7 +371,7 @@ __global__ void __launch_bounds__(32 * WarpCfg<T, G, RMAX>::WPB, WarpCfg<T, G, R
 #pragma unroll
         for (int r = 0; r < RMAX; ++r)
           if ((RFIXED || r >= rb) && (pk[r] & REC_SOLID))
-            atomicAdd(tl_acc + (pk[r] & REC_CELL_MASK), widen(tls[r]));
+            atomicAdd(tl_acc + (pk[r] & REC_CELL_MASK), (double)tls[r]);
       }
       s = s_next;
       __syncwarp();
