@@ -614,7 +614,8 @@ struct Variant {
 };
 
 const Variant kWarp2D_F[] = {{8, 8, true}, {8, 4, true}, {16, 4, true}, {16, 2, true},
-                             {16, 1, true}, {8, 1, true},  {4, 8, true},  {4, 4, true}};
+                             {16, 1, true}, {8, 1, true},  {6, 8, true},  {4, 8, true},
+                             {4, 4, true}};
 const Variant kWarp2D_D[] = {{4, 8, true}, {8, 4, true}, {8, 2, true}, {8, 1, true}, {2, 8, true}};
 const Variant kVariants2D_F[] = {{16, 4, false}, {8, 4, false}, {8, 8, false}, {16, 2, false},
                                  {8, 2, false}, {4, 4, false}, {16, 1, false}};
@@ -881,7 +882,8 @@ static int prepare_state(obte_ctx* ctx, int precision, int G, int R, bool warp, 
   ctx->R = R;
   ctx->warp = warp;
   ctx->k3d = k3d;
-  ctx->threads = warp ? 32 * kWarpsPerBlock : threads_for(Ny, Nz, R);
+  ctx->threads = warp ? 32 * sweep2d_warps_per_block(precision, G, R, ctx->has_s, true)
+                      : threads_for(Ny, Nz, R);
   std::vector<WorkItem> items;
   std::vector<int> ord_d0;
   build_items(ctx, 0, G, items, &ord_d0);
@@ -1530,7 +1532,8 @@ extern "C" int obte_solve_batch(obte_ctx* const* ctxs, int n, const obte_solve_o
     if (rc) return ctx->fail(rc, std::string("batch member: ") + ctxs[i]->err);
     ctxs[i]->flux_done = false;
   }
-  const int threads = v.warp ? 32 * kWarpsPerBlock : threads_for(max_ny, max_nz, v.R);
+  const int wpb = v.warp ? sweep2d_warps_per_block(prec, v.G, v.R, any_s, false) : 0;
+  const int threads = v.warp ? 32 * wpb : threads_for(max_ny, max_nz, v.R);
   const size_t smem = v.warp ? 0 : sweep_smem_bytes(prec, ctx->dim, v.G, v.R, threads);
   // contiguous geometry table and a work list sorted by cost (largest first)
   GeomDev* gds = ctx->dalloc_t<GeomDev>(n);
@@ -1553,8 +1556,10 @@ extern "C" int obte_solve_batch(obte_ctx* const* ctxs, int n, const obte_solve_o
                      ctx->stream));
   int sms = 148;
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ctx->device);
-  const int per_sm = v.warp ? 4 : std::max(1, sweep_blocks_per_sm(prec, ctx->dim, v.G, v.R, any_s, threads, smem));
-  const int blocks = v.warp ? (int)std::min<long>(((long)items.size() + kWarpsPerBlock - 1) / kWarpsPerBlock,
+  // warp kernel: 8 resident warps per SM (the register budget of the wide groups)
+  const int per_sm = v.warp ? std::max(1, 8 / std::max(1, wpb))
+                            : std::max(1, sweep_blocks_per_sm(prec, ctx->dim, v.G, v.R, any_s, threads, smem));
+  const int blocks = v.warp ? (int)std::min<long>(((long)items.size() + wpb - 1) / std::max(1, wpb),
                                                   (long)sms * per_sm)
                             : (int)std::min<long>((long)items.size(), (long)sms * per_sm);
   int max_cells = 0, max_ord = 0, max_rows = 0;

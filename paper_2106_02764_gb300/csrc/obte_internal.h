@@ -141,7 +141,7 @@ cudaError_t launch_sweep3d(const SweepLaunch& L, int precision, int G, int RMAX,
                            int threads, size_t smem, cudaStream_t st);
 bool sweep3d_exists(int precision, int G, int RMAX, bool has_s);
 size_t sweep3d_smem_bytes(int precision, int G, int RMAX, int threads);
-constexpr int kWarpsPerBlock = 4;
+int sweep2d_warps_per_block(int precision, int G, int RMAX, bool has_s, bool rfixed);
 cudaError_t launch_sweep(const SweepLaunch& L, int precision, int dim, int G, int RMAX,
                          bool has_s, int threads, int blocks, size_t smem, cudaStream_t st);
 size_t sweep_smem_bytes(int precision, int dim, int G, int RMAX, int threads);

@@ -52,10 +52,19 @@ int sweep_blocks_per_sm(int precision, int dim, int G, int RMAX, bool has_s, int
 cudaError_t launch_sweep2d_warp(const SweepLaunch& L, int precision, int G, int RMAX, bool has_s,
                                 bool rfixed, int blocks, cudaStream_t st) {
 #define X(T, GG, RR, SS, FF) \
-  if (OBTE_MATCH2D(T, GG, RR, SS, FF)) return OBTE_SWEEP2D_NAME(T, GG, RR, SS, FF)(&L, blocks, st);
+  if (OBTE_MATCH2D(T, GG, RR, SS, FF)) return OBTE_SWEEP2D_NAME(T, GG, RR, SS, FF)(&L, blocks, st, nullptr);
   OBTE_SWEEP2D_VARIANTS(X)
 #undef X
   return cudaErrorInvalidValue;
+}
+
+int sweep2d_warps_per_block(int precision, int G, int RMAX, bool has_s, bool rfixed) {
+  int w = 0;
+#define X(T, GG, RR, SS, FF) \
+  if (OBTE_MATCH2D(T, GG, RR, SS, FF)) OBTE_SWEEP2D_NAME(T, GG, RR, SS, FF)(nullptr, 0, nullptr, &w);
+  OBTE_SWEEP2D_VARIANTS(X)
+#undef X
+  return w;
 }
 
 bool sweep2d_warp_exists(int precision, int G, int RMAX, bool has_s, bool rfixed) {

@@ -30,6 +30,8 @@
 // RFIXED the host guarantees R == RMAX.
 #pragma once
 
+#include <type_traits>
+
 #include "sweep.cuh"
 
 namespace obte {
@@ -111,14 +113,19 @@ __device__ __noinline__ double cell_epilogue_2d(const GeomDev& gm, const T* __re
   return phi;
 }
 
-// warps per block: every warp owns its own staging buffers (static shared
-// memory stays under 48 KB).  Narrow groups (G <= 4 in FP32, G <= 2 in FP64)
-// hold few row values; they are built for four resident blocks per SM
-// (<= 128 registers) so that more warps hide the latencies of a step.
+// Warps per block (every warp owns its own staging buffers; static shared
+// memory stays under 48 KB) and the resident blocks per SM the registers are
+// budgeted for.  FP32 groups narrower than 8 ordinates hold fewer row values
+// per lane and are built one warp per block with a register budget for 12
+// (G = 6) or 15 (G = 4) resident warps per SM: more warps hide the latencies
+// of a step, and single-warp blocks spread the groups evenly over the SMs.
+// NST: record buffers per warp (copies run NST - 1 steps ahead).
 template <typename T, int G, int RMAX>
 struct WarpCfg {
-  static constexpr int WPB = (sizeof(T) == 8 && RMAX >= 8) ? 2 : 4;
-  static constexpr int MINB = (G * (int)sizeof(T) <= 16) ? 4 : 1;
+  static constexpr bool NARROW = sizeof(T) == 4 && G < 8 && RMAX >= 8;
+  static constexpr int NST = 2;
+  static constexpr int WPB = NARROW ? 1 : ((sizeof(T) == 8 && RMAX >= 8) ? 2 : 4);
+  static constexpr int MINB = NARROW ? (G <= 4 ? 15 : 12) : ((G * (int)sizeof(T) <= 16) ? 4 : 1);
 };
 
 // Shared-memory slot of the record of (lane, register row r): each 16-byte
@@ -134,19 +141,23 @@ __device__ __forceinline__ int rec_slot(int lane, int r) {
   return lane * RMAX + (r ^ ((lane >> SH) & MSK));
 }
 
-template <typename T, int G, int RMAX, bool HAS_S, bool RFIXED>
+// PASS: a flux / record pass (flags SWEEP_FLUX or SWEEP_RECORD); the
+// iteration sweeps are built without the out-of-line epilogue call, so no
+// registers are saved around it in the hot loop.
+template <typename T, int G, int RMAX, bool HAS_S, bool RFIXED, bool PASS>
 __global__ void __launch_bounds__(32 * WarpCfg<T, G, RMAX>::WPB, WarpCfg<T, G, RMAX>::MINB)
     sweep2d_warp_kernel(const SweepLaunch L) {
   constexpr int WPB = WarpCfg<T, G, RMAX>::WPB;
   constexpr int CH = (4 * sizeof(T)) / 16;  // 16-byte parts per record
-  __shared__ __align__(16) uint4 recbuf[WPB][2][CH][32 * RMAX];
+  constexpr int NST = WarpCfg<T, G, RMAX>::NST;
+  __shared__ __align__(16) uint4 recbuf[WPB][NST][CH][32 * RMAX];
   __shared__ __align__(16) T scratch_all[WPB][32][G];
   __shared__ T kcoef[WPB][2][G];  // |K_gx|, |K_gy| of the warp's group (rare path only)
   const int lane = threadIdx.x & 31;
   const int wib = threadIdx.x >> 5;
   T* scratch = &scratch_all[wib][lane][0];
   const int flags = L.flags;
-  const bool rare_pass = (flags & (SWEEP_FLUX | SWEEP_RECORD)) != 0;
+  constexpr bool rare_pass = PASS;
   const unsigned FULL = 0xffffffffu;
 
   int item = blockIdx.x * WPB + wib;
@@ -211,13 +222,33 @@ __global__ void __launch_bounds__(32 * WarpCfg<T, G, RMAX>::WPB, WarpCfg<T, G, R
       if (ok) kx_sum += (double)sx * (double)ld<T>(gm.kxa, o);
     }
 
-    T v[RMAX][G];
+    // Row values.  FP32 without s(x), G even: ordinates in pairs (float2),
+    // updated by the paired FP32 instructions of sm_100+ (__ffma2_rn and
+    // friends: one instruction per two ordinates, same rounding per lane).
+    constexpr bool X2 = sizeof(T) == 4 && !HAS_S && (G % 2 == 0);
+    constexpr int GV = X2 ? G / 2 : G;
+    using VV = typename std::conditional<X2, float2, T>::type;
+    VV v[RMAX][GV];
+    auto VG = [&](int r, int g) -> T& {
+      if constexpr (X2) return (g & 1) ? v[r][g >> 1].y : v[r][g >> 1].x;
+      else return v[r][g];
+    };
+    VV A0v[GV], AXv[GV], AYv[GV], AWv[GV];
+#pragma unroll
+    for (int h = 0; h < GV; ++h) {
+      if constexpr (X2) {
+        A0v[h] = make_float2(A0[2 * h], A0[2 * h + 1]);
+        AXv[h] = make_float2(AX[2 * h], AX[2 * h + 1]);
+        AYv[h] = make_float2(AY[2 * h], AY[2 * h + 1]);
+        AWv[h] = make_float2(AW[2 * h], AW[2 * h + 1]);
+      }
+    }
     const T* front = reinterpret_cast<const T*>(gm.front);
 #pragma unroll
     for (int r = 0; r < RMAX; ++r)
 #pragma unroll
       for (int g = 0; g < G; ++g)
-        v[r][g] = (active && r >= rb && g < cnt) ? front[(size_t)(o0 + g) * ny + j0 + (r - rb)] : T(0);
+        VG(r, g) = (active && r >= rb && g < cnt) ? front[(size_t)(o0 + g) * ny + j0 + (r - rb)] : T(0);
 
     // Prefetch the records of diagonal s into buffer b.  With RFIXED the
     // warp's ny records are one contiguous run and part m of it is copied by
@@ -263,22 +294,33 @@ __global__ void __launch_bounds__(32 * WarpCfg<T, G, RMAX>::WPB, WarpCfg<T, G, R
     const int below = lane > 0 ? lane - 1 : (gm.py ? tpp - 1 : 0);
     const int out_x_side = sx > 0 ? 1 : 0, out_y_side = sy > 0 ? 3 : 2;
     double phi = 0.0;
+    // diagonals of steps d .. d + NST - 2 are in flight at the top of step d
+    // (they wrap around nx, so the copies past the last step stay in bounds)
     int s = d0;
-    prefetch(s, 0);
-
-    for (int d = 0; d < nx; ++d) {
-      const int cur = d & 1;
-      const int s_next = (s + 1 == nx) ? 0 : s + 1;
-      if (d + 1 < nx) {
-        prefetch(s_next, cur ^ 1);
-        cp_async_wait<1>();
-      } else {
-        cp_async_wait<0>();
-      }
-      __syncwarp();  // parts copied by other lanes are visible
-      T dn0[G];
+    int sf = d0;  // diagonal of the next copy
 #pragma unroll
-      for (int g = 0; g < G; ++g) dn0[g] = __shfl_sync(FULL, v[RMAX - 1][g], below);
+    for (int b = 0; b < NST - 1; ++b) {
+      prefetch(sf, b);
+      sf = (sf + 1 == nx) ? 0 : sf + 1;
+    }
+    int cur = 0, bf = NST - 1;  // buffer of step d, buffer of the next copy
+    for (int d = 0; d < nx; ++d) {
+      const int s_next = (s + 1 == nx) ? 0 : s + 1;
+      prefetch(sf, bf);
+      sf = (sf + 1 == nx) ? 0 : sf + 1;
+      bf = (bf + 1 == NST) ? 0 : bf + 1;
+      cp_async_wait<NST - 1>();
+      __syncwarp();  // parts copied by other lanes are visible
+      VV dn0[GV];
+#pragma unroll
+      for (int h = 0; h < GV; ++h) {
+        if constexpr (X2) {
+          dn0[h].x = __shfl_sync(FULL, v[RMAX - 1][h].x, below);
+          dn0[h].y = __shfl_sync(FULL, v[RMAX - 1][h].y, below);
+        } else {
+          dn0[h] = __shfl_sync(FULL, v[RMAX - 1][h], below);
+        }
+      }
       if (active) {
         uint32_t pk[RMAX];
         T tls[RMAX];
@@ -300,11 +342,34 @@ __global__ void __launch_bounds__(32 * WarpCfg<T, G, RMAX>::WPB, WarpCfg<T, G, R
             const bool below_in_lane = RFIXED ? (r > 0) : (r > rb);
             T sval = T(1);
             if (HAS_S) sval = (T)__ldg(sv_ptr + (packed & REC_CELL_MASK));
+            if constexpr (X2) {
+              // u_x = m_x T + t_x: the row value, the wall temperature
+              // (m_x = 0), or the value across the jump (t_x = +-dT)
+              const float mx = wx ? 0.f : 1.f, tx = wx ? twx : jdt;
+              const float my = wy ? 0.f : 1.f, ty = wy ? twy : 0.f;
+              const float2 mx2 = make_float2(mx, mx), tx2 = make_float2(tx, tx);
+              const float2 my2 = make_float2(my, my), ty2 = make_float2(ty, ty);
+              const float2 src2 = make_float2(src, src);
+              float2 tlp = make_float2(0.f, 0.f);
+#pragma unroll
+              for (int h = 0; h < GV; ++h) {
+                const float2 ux = __ffma2_rn(mx2, v[r][h], tx2);
+                const float2 ud = below_in_lane ? v[r > 0 ? r - 1 : 0][h] : dn0[h];
+                const float2 uy = __ffma2_rn(my2, ud, ty2);
+                float2 acc = __fmul2_rn(src2, A0v[h]);
+                acc = __ffma2_rn(AYv[h], uy, acc);
+                acc = __ffma2_rn(AXv[h], ux, acc);
+                v[r][h] = acc;
+                tlp = __ffma2_rn(AWv[h], acc, tlp);
+              }
+              pk[r] = packed;
+              tls[r] = tlp.x + tlp.y;
+            } else {
             T tl = T(0), tl2 = T(0);  // two partial chains of the T_L moment
 #pragma unroll
             for (int g = 0; g < G; ++g) {
-              const T ux = JSEL ? (wx ? twx : v[r][g]) : (wx ? twx : v[r][g]) + jdt;
-              const T ud = below_in_lane ? v[r > 0 ? r - 1 : 0][g] : dn0[g];
+              const T ux = JSEL ? (wx ? twx : VG(r, g)) : (wx ? twx : VG(r, g)) + jdt;
+              const T ud = below_in_lane ? VG(r > 0 ? r - 1 : 0, g) : dn0[g];
               const T uy = wy ? twy : ud;
               const T jx = (JSEL && jump) ? JX[JSEL ? g : 0] : T(0);
               T acc;
@@ -318,12 +383,13 @@ __global__ void __launch_bounds__(32 * WarpCfg<T, G, RMAX>::WPB, WarpCfg<T, G, R
               } else {
                 val = acc;
               }
-              v[r][g] = val;
+              VG(r, g) = val;
               if (g & 1) tl2 = fma(AW[g], val, tl2);
               else tl = fma(AW[g], val, tl);
             }
             pk[r] = packed;
             tls[r] = tl + tl2;
+            }
           }
         }
         constexpr uint32_t RARE = REC_WOUT_X | REC_WOUT_Y | REC_LAST;
@@ -342,9 +408,9 @@ __global__ void __launch_bounds__(32 * WarpCfg<T, G, RMAX>::WPB, WarpCfg<T, G, R
             if (!(packed & REC_SOLID) || !((packed & RARE) || rare_pass)) continue;
             const int cell = (int)(packed & REC_CELL_MASK);
             const bool last = packed & REC_LAST;
-            if (rare_pass) {
+            if constexpr (PASS) {
 #pragma unroll
-              for (int g = 0; g < G; ++g) scratch[g] = v[r][g];
+              for (int g = 0; g < G; ++g) scratch[g] = VG(r, g);
               phi += cell_epilogue_2d<T, G>(gm, scratch, cell, packed, last, o0, cnt, sx, sy,
                                             flags, kx_sum);
               continue;
@@ -352,7 +418,7 @@ __global__ void __launch_bounds__(32 * WarpCfg<T, G, RMAX>::WPB, WarpCfg<T, G, R
             if (packed & (REC_WOUT_X | REC_LAST)) {
               T sk = T(0);
 #pragma unroll
-              for (int g = 0; g < G; ++g) sk = fma(KX[g], v[r][g], sk);
+              for (int g = 0; g < G; ++g) sk = fma(KX[g], VG(r, g), sk);
               const double dk = widen(sk);
               if (packed & REC_WOUT_X) atomicAdd(wacc + (size_t)cell * 6 + out_x_side, dk);
               else phi += (sx > 0 ? dk : -dk) + (sx > 0 ? dT * kx_sum : 0.0);
@@ -360,7 +426,7 @@ __global__ void __launch_bounds__(32 * WarpCfg<T, G, RMAX>::WPB, WarpCfg<T, G, R
             if (packed & REC_WOUT_Y) {
               T sy_k = T(0);
 #pragma unroll
-              for (int g = 0; g < G; ++g) sy_k = fma(KY[g], v[r][g], sy_k);
+              for (int g = 0; g < G; ++g) sy_k = fma(KY[g], VG(r, g), sy_k);
               atomicAdd(wacc + (size_t)cell * 6 + out_y_side, widen(sy_k));
             }
           }
@@ -374,15 +440,18 @@ __global__ void __launch_bounds__(32 * WarpCfg<T, G, RMAX>::WPB, WarpCfg<T, G, R
             atomicAdd(tl_acc + (pk[r] & REC_CELL_MASK), (double)tls[r]);
       }
       s = s_next;
+      cur = (cur + 1 == NST) ? 0 : cur + 1;
       __syncwarp();
     }
+    cp_async_wait<0>();  // copies past the last step land before the buffers are reused
+    __syncwarp();
 
     T* frontw = reinterpret_cast<T*>(gm.front);
 #pragma unroll
     for (int r = 0; r < RMAX; ++r)
 #pragma unroll
       for (int g = 0; g < G; ++g)
-        if (active && r >= rb && g < cnt) frontw[(size_t)(o0 + g) * ny + j0 + (r - rb)] = v[r][g];
+        if (active && r >= rb && g < cnt) frontw[(size_t)(o0 + g) * ny + j0 + (r - rb)] = VG(r, g);
 
     for (int o = 16; o > 0; o >>= 1) phi += __shfl_xor_sync(FULL, phi, o);
     if (lane == 0 && phi != 0.0) atomicAdd(gm.phi_acc, phi);

@@ -6,6 +6,7 @@
 
 #define OBTE_SWEEP2D_WF(X) \
   X(float, 8, 8, false, true) \
+  X(float, 6, 8, false, true) \
   X(float, 4, 8, false, true) \
   X(float, 4, 4, false, true) \
   X(float, 8, 4, false, true) \
@@ -44,16 +45,25 @@
 #define OBTE_SWEEP2D_VARIANTS(X) OBTE_SWEEP2D_WF(X) OBTE_SWEEP2D_WS(X) OBTE_SWEEP2D_WD(X) OBTE_SWEEP2D_WB(X)
 
 #define OBTE_SWEEP2D_NAME(T, G, R, S, F) obte_sweep2d_##T##_##G##_##R##_##S##_##F
-// blocks == 0: one warp per work item; blocks > 0: that many persistent blocks
+// blocks == 0: one warp per work item; blocks > 0: that many persistent
+// blocks; L == nullptr: only report the warps per block in *wpb
 #define OBTE_SWEEP2D_DECLARE(T, G, R, S, F) \
-  cudaError_t OBTE_SWEEP2D_NAME(T, G, R, S, F)(const SweepLaunch* L, int blocks, cudaStream_t st);
+  cudaError_t OBTE_SWEEP2D_NAME(T, G, R, S, F)(const SweepLaunch* L, int blocks, cudaStream_t st, int* wpb);
 OBTE_SWEEP2D_VARIANTS(OBTE_SWEEP2D_DECLARE)
 
 #define OBTE_SWEEP2D_DEFINE(T, G, R, S, F)                                                      \
-  cudaError_t OBTE_SWEEP2D_NAME(T, G, R, S, F)(const SweepLaunch* L, int blocks, cudaStream_t st) { \
+  cudaError_t OBTE_SWEEP2D_NAME(T, G, R, S, F)(const SweepLaunch* L, int blocks, cudaStream_t st, \
+                                               int* wpb_out) {                                 \
     constexpr int wpb = obte::WarpCfg<T, G, R>::WPB;                                            \
+    if (!L) {                                                                                  \
+      *wpb_out = wpb;                                                                          \
+      return cudaSuccess;                                                                      \
+    }                                                                                          \
     const int need = (L->n_items + wpb - 1) / wpb;                                             \
     const int b = (blocks > 0 && blocks < need) ? blocks : need;                               \
-    obte::sweep2d_warp_kernel<T, G, R, S, F><<<b, 32 * wpb, 0, st>>>(*L);                       \
+    if (L->flags & (SWEEP_FLUX | SWEEP_RECORD))                                                \
+      obte::sweep2d_warp_kernel<T, G, R, S, F, true><<<b, 32 * wpb, 0, st>>>(*L);               \
+    else                                                                                       \
+      obte::sweep2d_warp_kernel<T, G, R, S, F, false><<<b, 32 * wpb, 0, st>>>(*L);              \
     return cudaGetLastError();                                                                 \
   }
