@@ -80,6 +80,7 @@ struct obte_ctx {
   int* aa_int = nullptr;
   void* rec4 = nullptr;
   int* rec_idx = nullptr;
+  double* tlq = nullptr;
   double* blk_part = nullptr;  // per-block partials of the finalize / Anderson reductions
   double* Tw = nullptr;
   double* wall_acc = nullptr;
@@ -151,6 +152,7 @@ struct obte_ctx {
     aa_int = nullptr;
     rec4 = nullptr;
     rec_idx = nullptr;
+    tlq = nullptr;
     blk_part = nullptr;
     s_d = nullptr;
     wall_den_d = nullptr;
@@ -717,8 +719,10 @@ static int prepare_state(obte_ctx* ctx, int precision, int G, int R, bool warp, 
     // (re)allocate everything that depends on the precision
     ctx->dfree(ctx->rec4);
     ctx->dfree(ctx->rec_idx);
+    ctx->dfree(ctx->tlq);
     ctx->rec4 = nullptr;
     ctx->rec_idx = nullptr;
+    ctx->tlq = nullptr;
     ctx->rec_w_alloc = 0;
     for (void* p : {(void*)ctx->aa_xd, (void*)ctx->aa_fd, ctx->aa_xt, ctx->aa_ft, (void*)ctx->aa_small,
                     (void*)ctx->aa_int})
@@ -767,11 +771,18 @@ static int prepare_state(obte_ctx* ctx, int precision, int G, int R, bool warp, 
   if (rec_w && ctx->rec_w_alloc != rec_w) {
     ctx->dfree(ctx->rec4);
     ctx->dfree(ctx->rec_idx);
+    ctx->dfree(ctx->tlq);
+    ctx->tlq = nullptr;
     const size_t e = precision == 0 ? 8 : 4;
     ctx->rec4 = ctx->dalloc((size_t)nq * rec_w * e * (size_t)ctx->n_cells);
     ctx->rec_idx = ctx->dalloc_t<int>((size_t)nq * ctx->n_cells);
     NEED(ctx->rec4);
     NEED(ctx->rec_idx);
+    if (rec_w == 4) {  // skewed T_L partials of the 2D warp kernel
+      ctx->tlq = ctx->dalloc_t<double>((size_t)nq * ctx->n_cells);
+      NEED(ctx->tlq);
+      CK(cudaMemsetAsync(ctx->tlq, 0, sizeof(double) * nq * (size_t)ctx->n_cells, ctx->stream));
+    }
     ctx->rec_w_alloc = rec_w;
   }
   if (!ctx->blk_part) {
@@ -847,6 +858,7 @@ static int prepare_state(obte_ctx* ctx, int precision, int G, int R, bool warp, 
   g.twc = ctx->twc;
   g.rec4 = rec_w ? ctx->rec4 : nullptr;
   g.rec_idx = rec_w ? ctx->rec_idx : nullptr;
+  g.tlq = rec_w == 4 ? ctx->tlq : nullptr;
   g.blk_part = ctx->blk_part;
   g.rec_w = rec_w;
   g.front = ctx->front;
@@ -1286,6 +1298,7 @@ static int run_flux_pass(obte_ctx* ctx) {
   CK(sweep_once(ctx, SWEEP_FLUX));
   // the pass does not advance the iterate: drop its moment accumulations
   CK(cudaMemsetAsync(ctx->TL_acc, 0, sizeof(double) * ctx->n_cells, ctx->stream));
+  if (ctx->tlq) CK(cudaMemsetAsync(ctx->tlq, 0, sizeof(double) * 4 * (size_t)ctx->n_cells, ctx->stream));
   CK(cudaMemsetAsync(ctx->wall_acc, 0, sizeof(double) * 6 * (size_t)ctx->n_cells, ctx->stream));
   CK(cudaMemsetAsync(ctx->scal, 0, sizeof(double), ctx->stream));
   int one = 1;
@@ -1451,6 +1464,7 @@ extern "C" int obte_kappa_grad_s(obte_ctx* ctx, double* out, size_t max_field_by
     CK(launch_grad_contract2(ctx->code_d, ctx->TL, ctx->n_cells, rec, (int)b.size(), revl_d, a_d,
                              jscale, grad_d, ctx->precision, ctx->stream));
     CK(cudaMemsetAsync(ctx->TL_acc, 0, sizeof(double) * ctx->n_cells, ctx->stream));
+    if (ctx->tlq) CK(cudaMemsetAsync(ctx->tlq, 0, sizeof(double) * 4 * (size_t)ctx->n_cells, ctx->stream));
     CK(cudaMemsetAsync(ctx->wall_acc, 0, sizeof(double) * 6 * (size_t)ctx->n_cells, ctx->stream));
     CK(cudaMemsetAsync(ctx->scal, 0, sizeof(double), ctx->stream));
     CK(cudaStreamSynchronize(ctx->stream));
@@ -1885,6 +1899,7 @@ extern "C" int obte_kappa_grad_s_noalloc(obte_ctx* ctx, double* out) {
     CK(launch_grad_contract2(ctx->code_d, ctx->TL, ctx->n_cells, rec, (int)b.size(), revl_d, a_d,
                              jscale, grad_d, ctx->precision, ctx->stream));
     CK(cudaMemsetAsync(ctx->TL_acc, 0, sizeof(double) * ctx->n_cells, ctx->stream));
+    if (ctx->tlq) CK(cudaMemsetAsync(ctx->tlq, 0, sizeof(double) * 4 * (size_t)ctx->n_cells, ctx->stream));
     CK(cudaMemsetAsync(ctx->wall_acc, 0, sizeof(double) * 6 * (size_t)ctx->n_cells, ctx->stream));
     CK(cudaMemsetAsync(ctx->scal, 0, sizeof(double), ctx->stream));
     CK(cudaStreamSynchronize(ctx->stream));  // host vectors above are copy sources

@@ -30,8 +30,18 @@ __global__ void finalize_kernel(const GeomDev* geoms) {
   const int stride = gridDim.x * blockDim.x;
   for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < n_cells; c += stride) {
     if (!(code[c] & CODE_SOLID)) continue;
-    const double t = TL_acc[c];
+    double t = TL_acc[c];
     TL_acc[c] = 0.0;
+    if (g.tlq) {  // skewed per-quadrant partials of the 2D warp kernel
+      const int x = c % g.nx, y = c / g.nx;
+      for (int q = 0; q < 4; ++q) {
+        const int ip = (q & 1) ? g.nx - 1 - x : x;
+        const int jp = (q & 2) ? g.ny - 1 - y : y;
+        const size_t k = ((size_t)q * g.nx + (ip + jp) % g.nx) * g.ny + jp;
+        t += g.tlq[k];
+        g.tlq[k] = 0.0;
+      }
+    }
     if (!isfinite(t)) nonfin = 1;
     dmax = fmax(dmax, fabs(t - TL[c]));
     TL[c] = t;
@@ -237,7 +247,8 @@ __global__ void build_records_kernel(const GeomDev* geoms) {
       T* r = rec + (size_t)g.rec_w * k;
       const T pk = sizeof(T) == 4 ? (T)__uint_as_float(packed) : (T)__longlong_as_double((long long)packed);
       r[0] = src[c];
-      r[1] = twc[(size_t)c * 6 + ((q & 1) ? 1 : 0)];
+      // x field: the upwind wall temperature, or +-dT on the jump column
+      r[1] = (packed & REC_JUMP) ? (T)((q & 1) ? -g.dT : g.dT) : twc[(size_t)c * 6 + ((q & 1) ? 1 : 0)];
       r[2] = twc[(size_t)c * 6 + ((q & 2) ? 3 : 2)];
       if (g.rec_w == 4) {
         r[3] = pk;

@@ -71,11 +71,17 @@ struct GeomDev {
   // at diagonal s = (i' + j' + k') mod nx:
   //   rec4[((q * nx + s) * rows + row) * rec_w + f]: rec_w = 4 (2D warp kernel)
   //     {s_i T_L,i, T_w in-x side, T_w in-y side, packed};  rec_w = 8 (3D)
+  //     (the in-x field holds sign(p_x) dT instead on the jump column, REC_JUMP;
+  //     wall fields of sides without a wall hold 0)
   //     {s_i T_L,i, T_w in-x, in-y, in-z sides, packed, 0, 0, 0}
   //   packed = cell (bits 0-21) | REC_* flags of octant q (bits 22-31)
   //   rec_idx[c * n_octants + q] = record index (q * nx + s) * rows + row of cell c
+  //   tlq[(q * nx + s) * rows + row]: T_L partial sums of the running sweep in
+  //     the same skewed order (2D warp kernel; FP64); the finalisation adds
+  //     them to TL_acc's
   void* rec4;
   int* rec_idx;
+  double* tlq;
   int rec_w;              // values per record: 4 (2D warp kernel), 8 (3D kernel); 0: none
   void* front;            // [n_ord][rows] row values carried between iterations
   double* phi_acc;        // [1] hot-face flux of the running sweep

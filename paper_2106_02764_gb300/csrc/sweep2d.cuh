@@ -17,8 +17,10 @@
 // the quadrant's wall / jump / column flags) at [s][j'], kept current by the
 // finalisation, so a lane's R rows of one step are R contiguous records.  They are
 // prefetched one step ahead with cp.async into lane-private shared memory.
-// The T_L moment of every solid cell goes to its FP64 accumulator (one atomic
-// per cell and warp, after all rows of the step).
+// The T_L partials of a step go, transposed through shared memory, to skewed
+// per-quadrant FP64 accumulators [s][j'], so that one atomic instruction of
+// the warp covers 32 consecutive rows (or, when the warp's rows do not fill
+// 32 lanes, to the cell's accumulator directly).
 //
 // Cells are updated branch-free (pores too: a pore's value is never read by a
 // solid cell, whose faces towards a pore are walls); only the atomics and the
@@ -153,6 +155,7 @@ __global__ void __launch_bounds__(32 * WarpCfg<T, G, RMAX>::WPB, WarpCfg<T, G, R
   __shared__ __align__(16) uint4 recbuf[WPB][NST][CH][32 * RMAX];
   __shared__ __align__(16) T scratch_all[WPB][32][G];
   __shared__ T kcoef[WPB][2][G];  // |K_gx|, |K_gy| of the warp's group (rare path only)
+  __shared__ __align__(16) T tlbuf[WPB][32 * RMAX];  // a step's T_L partials, transposed
   const int lane = threadIdx.x & 31;
   const int wib = threadIdx.x >> 5;
   T* scratch = &scratch_all[wib][lane][0];
@@ -187,6 +190,7 @@ __global__ void __launch_bounds__(32 * WarpCfg<T, G, RMAX>::WPB, WarpCfg<T, G, R
     const int j0 = lane * R;
     const T* __restrict__ recq = reinterpret_cast<const T*>(gm.rec4) + (size_t)q * nx * ny * 4;
     double* tl_acc = gm.TL_acc;
+    double* tlq = gm.tlq ? gm.tlq + (size_t)q * nx * ny : nullptr;
     const double* __restrict__ sv_ptr = gm.s;
     double* wacc = gm.wall_acc;
 
@@ -202,7 +206,6 @@ __global__ void __launch_bounds__(32 * WarpCfg<T, G, RMAX>::WPB, WarpCfg<T, G, R
       kcoef[wib][0][lane] = ok ? ld<T>(gm.kxa, o0 + lane) : T(0);
       kcoef[wib][1][lane] = ok ? ld<T>(gm.kya, o0 + lane) : T(0);
     }
-    const T sdT = (T)((double)sx * dT);  // jump of the x upwind value at i' = 0
 #pragma unroll
     for (int g = 0; g < G; ++g) {
       const bool ok = g < cnt;
@@ -294,6 +297,16 @@ __global__ void __launch_bounds__(32 * WarpCfg<T, G, RMAX>::WPB, WarpCfg<T, G, R
     const int below = lane > 0 ? lane - 1 : (gm.py ? tpp - 1 : 0);
     const int out_x_side = sx > 0 ? 1 : 0, out_y_side = sy > 0 ? 3 : 2;
     double phi = 0.0;
+    // Moments of a full 32-lane warp go through shared memory so that one
+    // atomic instruction covers 32 consecutive rows of the skewed
+    // accumulator (8 sectors instead of 32).
+    const bool tr_atom = RFIXED && full_run && tlq != nullptr;
+    // hot-face flux: each row crosses the hot column once per sweep, so its
+    // sum_g K_gx T_g is kept per row in the sweep precision and widened once
+    T hot[RMAX];
+#pragma unroll
+    for (int r = 0; r < RMAX; ++r) hot[r] = T(0);
+    int n_hot = 0;
     // diagonals of steps d .. d + NST - 2 are in flight at the top of step d
     // (they wrap around nx, so the copies past the last step stay in bounds)
     int s = d0;
@@ -338,15 +351,15 @@ __global__ void __launch_bounds__(32 * WarpCfg<T, G, RMAX>::WPB, WarpCfg<T, G, R
             const uint32_t packed = rec_bits(CH == 1 ? rc0[3] : rc1[1]);
             const bool wx = packed & REC_WIN_X, wy = packed & REC_WIN_Y;
             const bool jump = packed & REC_JUMP;
-            const T jdt = (jump && !JSEL) ? sdT : T(0);
             const bool below_in_lane = RFIXED ? (r > 0) : (r > rb);
             T sval = T(1);
             if (HAS_S) sval = (T)__ldg(sv_ptr + (packed & REC_CELL_MASK));
             if constexpr (X2) {
               // u_x = m_x T + t_x: the row value, the wall temperature
-              // (m_x = 0), or the value across the jump (t_x = +-dT)
-              const float mx = wx ? 0.f : 1.f, tx = wx ? twx : jdt;
-              const float my = wy ? 0.f : 1.f, ty = wy ? twy : 0.f;
+              // (m_x = 0, t_x = T_w), or the value across the jump
+              // (t_x = +-dT); the record's x field holds t_x, its y field t_y
+              const float mx = wx ? 0.f : 1.f, tx = twx;
+              const float my = wy ? 0.f : 1.f, ty = twy;
               const float2 mx2 = make_float2(mx, mx), tx2 = make_float2(tx, tx);
               const float2 my2 = make_float2(my, my), ty2 = make_float2(ty, ty);
               const float2 src2 = make_float2(src, src);
@@ -368,7 +381,7 @@ __global__ void __launch_bounds__(32 * WarpCfg<T, G, RMAX>::WPB, WarpCfg<T, G, R
             T tl = T(0), tl2 = T(0);  // two partial chains of the T_L moment
 #pragma unroll
             for (int g = 0; g < G; ++g) {
-              const T ux = JSEL ? (wx ? twx : VG(r, g)) : (wx ? twx : VG(r, g)) + jdt;
+              const T ux = JSEL ? (wx ? twx : VG(r, g)) : (wx ? T(0) : VG(r, g)) + twx;
               const T ud = below_in_lane ? VG(r > 0 ? r - 1 : 0, g) : dn0[g];
               const T uy = wy ? twy : ud;
               const T jx = (JSEL && jump) ? JX[JSEL ? g : 0] : T(0);
@@ -419,9 +432,12 @@ __global__ void __launch_bounds__(32 * WarpCfg<T, G, RMAX>::WPB, WarpCfg<T, G, R
               T sk = T(0);
 #pragma unroll
               for (int g = 0; g < G; ++g) sk = fma(KX[g], VG(r, g), sk);
-              const double dk = widen(sk);
-              if (packed & REC_WOUT_X) atomicAdd(wacc + (size_t)cell * 6 + out_x_side, dk);
-              else phi += (sx > 0 ? dk : -dk) + (sx > 0 ? dT * kx_sum : 0.0);
+              if (packed & REC_WOUT_X) {
+                atomicAdd(wacc + (size_t)cell * 6 + out_x_side, widen(sk));
+              } else {
+                hot[r] = sk;
+                ++n_hot;
+              }
             }
             if (packed & REC_WOUT_Y) {
               T sy_k = T(0);
@@ -434,10 +450,21 @@ __global__ void __launch_bounds__(32 * WarpCfg<T, G, RMAX>::WPB, WarpCfg<T, G, R
         // the moment atomics come after all rows: a generic-address atomic
         // between two rows would keep the next row's shared-memory loads from
         // being scheduled ahead of it
+        if (tr_atom) {
 #pragma unroll
-        for (int r = 0; r < RMAX; ++r)
-          if ((RFIXED || r >= rb) && (pk[r] & REC_SOLID))
-            atomicAdd(tl_acc + (pk[r] & REC_CELL_MASK), (double)tls[r]);
+          for (int r = 0; r < RMAX; ++r) tlbuf[wib][lane * RMAX + r] = (pk[r] & REC_SOLID) ? tls[r] : T(0);
+        } else {
+#pragma unroll
+          for (int r = 0; r < RMAX; ++r)
+            if ((RFIXED || r >= rb) && (pk[r] & REC_SOLID))
+              atomicAdd(tl_acc + (pk[r] & REC_CELL_MASK), X2 ? widen(tls[r]) : (double)tls[r]);
+        }
+      }
+      if (tr_atom) {
+        __syncwarp();
+        double* row = tlq + (size_t)s * ny + lane;
+#pragma unroll
+        for (int r = 0; r < RMAX; ++r) atomicAdd(row + 32 * r, widen(tlbuf[wib][32 * r + lane]));
       }
       s = s_next;
       cur = (cur + 1 == NST) ? 0 : cur + 1;
@@ -453,6 +480,12 @@ __global__ void __launch_bounds__(32 * WarpCfg<T, G, RMAX>::WPB, WarpCfg<T, G, R
       for (int g = 0; g < G; ++g)
         if (active && r >= rb && g < cnt) frontw[(size_t)(o0 + g) * ny + j0 + (r - rb)] = VG(r, g);
 
+#pragma unroll
+    for (int r = 0; r < RMAX; ++r) {
+      const double dk = widen(hot[r]);
+      phi += sx > 0 ? dk : -dk;
+    }
+    if (sx > 0) phi += (double)n_hot * dT * kx_sum;
     for (int o = 16; o > 0; o >>= 1) phi += __shfl_xor_sync(FULL, phi, o);
     if (lane == 0 && phi != 0.0) atomicAdd(gm.phi_acc, phi);
     if (!L.item_counter) return;
