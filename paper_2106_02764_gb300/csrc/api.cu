@@ -98,6 +98,7 @@ struct obte_ctx {
   int G = 0, R = 0, threads = 0;
   bool warp = false;
   bool k3d = false;
+  int items_pad = 1;  // 4: items padded for the warp kernel's block-combined moments
   std::vector<WorkItem> items_h;
   WorkItem* items_d = nullptr;
   double kappa = NAN;
@@ -686,8 +687,12 @@ std::map<std::tuple<int, int, int, int, int, int>, Variant>& tune_cache() {
 // Work items: runs of at most G ordinates of one octant.  Items of one octant
 // start their wavefront at evenly spaced columns (d0) so that, at a given
 // step, they update different cells.
+//
+// pad > 1: every octant's items are padded with empty items (count 0) to a
+// multiple of pad, and each run of pad consecutive items shares its start
+// column (the 2D warp kernel's block-combined moments).
 static void build_items(obte_ctx* ctx, int geom, int G, std::vector<WorkItem>& items,
-                        std::vector<int>* ord_d0 = nullptr) {
+                        std::vector<int>* ord_d0 = nullptr, int pad = 1) {
   const int O = ctx->O;
   const int nx = ctx->n[0];
   if (ord_d0) ord_d0->assign(O, 0);
@@ -697,12 +702,15 @@ static void build_items(obte_ctx* ctx, int geom, int G, std::vector<WorkItem>& i
     int e = o;
     while (e < O && ctx->octant[e] == q) ++e;
     const int n_it = (e - o + G - 1) / G;
-    int k = 0;
-    for (int a = o; a < e; a += G, ++k) {
-      const int d0 = (int)(((long)k * nx) / std::max(1, n_it)) % nx;
-      items.push_back({geom, q, a, std::min(G, e - a), d0});
+    const int n_pad = ((n_it + pad - 1) / pad) * pad;
+    const int n_run = n_pad / pad;  // runs sharing a start column
+    for (int k = 0; k < n_pad; ++k) {
+      const int d0 = (int)(((long)(k / pad) * nx) / std::max(1, n_run)) % nx;
+      const int a = o + k * G;
+      const int cnt = a < e ? std::min(G, e - a) : 0;
+      items.push_back({geom, q, a < e ? a : e, cnt, d0});
       if (ord_d0)
-        for (int b = a; b < std::min(e, a + G); ++b) (*ord_d0)[b] = d0;
+        for (int b = a; b < a + cnt; ++b) (*ord_d0)[b] = d0;
     }
     o = e;
   }
@@ -898,7 +906,13 @@ static int prepare_state(obte_ctx* ctx, int precision, int G, int R, bool warp, 
                       : threads_for(Ny, Nz, R);
   std::vector<WorkItem> items;
   std::vector<int> ord_d0;
-  build_items(ctx, 0, G, items, &ord_d0);
+  // block-combined moments: warp kernel with four warps per block over full
+  // 32-lane rows
+  ctx->items_pad = (warp && sweep2d_warps_per_block(precision, G, R, ctx->has_s, true) == 4 &&
+                    Ny == 32 * R)
+                       ? 4
+                       : 1;
+  build_items(ctx, 0, G, items, &ord_d0, ctx->items_pad);
   const bool same = ctx->items_d && items.size() == ctx->items_h.size() &&
                     std::memcmp(items.data(), ctx->items_h.data(), sizeof(WorkItem) * items.size()) == 0;
   if (!same) {
@@ -924,7 +938,7 @@ static cudaError_t sweep_once(obte_ctx* ctx, int flags) {
   L.geoms = ctx->gd;
   L.items = ctx->items_d;
   L.n_items = (int)ctx->items_h.size();
-  L.flags = flags;
+  L.flags = flags | (ctx->warp && ctx->items_pad == 4 ? SWEEP_BLOCK_COMBINE : 0);
   L.item_counter = nullptr;
   if (ctx->warp)
     return launch_sweep2d_warp(L, ctx->precision, ctx->G, ctx->R, ctx->has_s, true, 0, ctx->stream);

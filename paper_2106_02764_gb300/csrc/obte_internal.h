@@ -39,6 +39,10 @@ enum : int {
   SWEEP_HAS_S = 1 << 0,   // per-cell scattering scale: divide per update
   SWEEP_FLUX = 1 << 1,    // also accumulate J per cell, section fluxes, bin fluxes
   SWEEP_RECORD = 1 << 2,  // write every ordinate field to the record buffer
+  // 2D warp kernel: the four warps of a block hold four groups of one octant
+  // with the same start column, so their T_L partials of a step can be added
+  // in shared memory before the atomics (items padded to blocks of four)
+  SWEEP_BLOCK_COMBINE = 1 << 3,
 };
 
 // One geometry as seen by the device kernels (kernel frame: x = gradient axis).

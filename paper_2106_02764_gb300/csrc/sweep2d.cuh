@@ -155,7 +155,8 @@ __global__ void __launch_bounds__(32 * WarpCfg<T, G, RMAX>::WPB, WarpCfg<T, G, R
   __shared__ __align__(16) uint4 recbuf[WPB][NST][CH][32 * RMAX];
   __shared__ __align__(16) T scratch_all[WPB][32][G];
   __shared__ T kcoef[WPB][2][G];  // |K_gx|, |K_gy| of the warp's group (rare path only)
-  __shared__ __align__(16) T tlbuf[WPB][32 * RMAX];  // a step's T_L partials, transposed
+  // a step's T_L partials of every warp, by row (two step parities)
+  __shared__ __align__(16) T tlbuf[2][WPB][32 * RMAX];
   const int lane = threadIdx.x & 31;
   const int wib = threadIdx.x >> 5;
   T* scratch = &scratch_all[wib][lane][0];
@@ -301,6 +302,12 @@ __global__ void __launch_bounds__(32 * WarpCfg<T, G, RMAX>::WPB, WarpCfg<T, G, R
     // atomic instruction covers 32 consecutive rows of the skewed
     // accumulator (8 sectors instead of 32).
     const bool tr_atom = RFIXED && full_run && tlq != nullptr;
+    // SWEEP_BLOCK_COMBINE: the block's warps hold groups of one octant with
+    // one start column, so row j's partials of the four warps are added in
+    // shared memory (FP32, fixed order) and each warp issues the atomics of a
+    // quarter of the rows: a block barrier per step, a quarter of the atomics
+    const bool comb = WPB == 4 && tr_atom && (flags & SWEEP_BLOCK_COMBINE) && !L.item_counter;
+    int par = 0;
     // hot-face flux: each row crosses the hot column once per sweep, so its
     // sum_g K_gx T_g is kept per row in the sweep precision and widened once
     T hot[RMAX];
@@ -452,7 +459,8 @@ __global__ void __launch_bounds__(32 * WarpCfg<T, G, RMAX>::WPB, WarpCfg<T, G, R
         // being scheduled ahead of it
         if (tr_atom) {
 #pragma unroll
-          for (int r = 0; r < RMAX; ++r) tlbuf[wib][lane * RMAX + r] = (pk[r] & REC_SOLID) ? tls[r] : T(0);
+          for (int r = 0; r < RMAX; ++r)
+            tlbuf[par][wib][lane * RMAX + r] = (pk[r] & REC_SOLID) ? tls[r] : T(0);
         } else {
 #pragma unroll
           for (int r = 0; r < RMAX; ++r)
@@ -460,11 +468,25 @@ __global__ void __launch_bounds__(32 * WarpCfg<T, G, RMAX>::WPB, WarpCfg<T, G, R
               atomicAdd(tl_acc + (pk[r] & REC_CELL_MASK), X2 ? widen(tls[r]) : (double)tls[r]);
         }
       }
-      if (tr_atom) {
+      if (comb) {
+        __syncthreads();
+        // warp wib: rows wib * 8 RMAX + 32 k + lane, k < RMAX / 4
+        constexpr int RQ = (RMAX + 3) / 4;
+#pragma unroll
+        for (int k = 0; k < RQ; ++k) {
+          const int j = wib * 8 * RMAX + 32 * k + lane;
+          if (RMAX % 4 == 0 || j < 32 * RMAX) {
+            const T t01 = tlbuf[par][0][j] + tlbuf[par][1][j];
+            const T t23 = tlbuf[par][2][j] + tlbuf[par][3][j];
+            atomicAdd(tlq + (size_t)s * ny + j, (double)(t01 + t23));
+          }
+        }
+        par ^= 1;
+      } else if (tr_atom) {
         __syncwarp();
         double* row = tlq + (size_t)s * ny + lane;
 #pragma unroll
-        for (int r = 0; r < RMAX; ++r) atomicAdd(row + 32 * r, widen(tlbuf[wib][32 * r + lane]));
+        for (int r = 0; r < RMAX; ++r) atomicAdd(row + 32 * r, (double)tlbuf[par][wib][32 * r + lane]);
       }
       s = s_next;
       cur = (cur + 1 == NST) ? 0 : cur + 1;
