@@ -71,7 +71,7 @@ __device__ __forceinline__ double state_d(const GeomDev& g, long i) {
 
 template <typename T>
 __global__ void aa_residual_kernel(const GeomDev* geoms) {
-  const GeomDev& g = geoms[blockIdx.y];
+  const GeomDev g = geoms[blockIdx.y];
   if (g.aa_m <= 0 || *(volatile int*)g.done) return;
   const int S = g.aa_m + 1;            // history slots
   const int k = g.aa_k[0];             // Anderson step (0 = first sweep)
@@ -181,7 +181,7 @@ __global__ void aa_residual_kernel(const GeomDev* geoms) {
 // for gamma and writes the mixing coefficients; the step counter advances
 // (aa_k[1] keeps the step being mixed).
 __global__ void aa_solve_kernel(const GeomDev* geoms, int nblocks) {
-  const GeomDev& g = geoms[blockIdx.x];
+  const GeomDev g = geoms[blockIdx.x];
   if (g.aa_m <= 0 || *(volatile int*)g.done) return;
   __shared__ double dv[8];
   const unsigned FULL = 0xffffffffu;
@@ -300,7 +300,7 @@ __global__ void aa_solve_kernel(const GeomDev* geoms, int nblocks) {
 // to the sweep inputs (s T_L, wall temperatures, records, row values).
 template <typename T>
 __global__ void aa_mix_kernel(const GeomDev* geoms) {
-  const GeomDev& g = geoms[blockIdx.y];
+  const GeomDev g = geoms[blockIdx.y];
   if (g.aa_m <= 0 || *(volatile int*)g.done) return;
   const int S = g.aa_m + 1;
   const int k = g.aa_k[1];  // the step being mixed

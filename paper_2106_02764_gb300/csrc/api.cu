@@ -952,7 +952,7 @@ static cudaError_t sweep_once(obte_ctx* ctx, int flags) {
 
 static int aa_blocks(int n_cells, int n_ord, int rows) {
   const long n = std::max((long)n_cells, (long)n_ord * rows);
-  return (int)std::max(1L, std::min((n + 255) / 256, 1216L));
+  return (int)std::max(1L, std::min((n / 4 + 255) / 256, 456L));
 }
 
 static int finalize_blocks(int n_cells) {

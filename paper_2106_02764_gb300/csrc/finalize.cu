@@ -15,7 +15,7 @@ namespace {
 // partial slot.  Grid: x = blocks per geometry, y = geometry.
 template <typename T>
 __global__ void finalize_kernel(const GeomDev* geoms) {
-  const GeomDev& g = geoms[blockIdx.y];
+  const GeomDev g = geoms[blockIdx.y];
   if (*(volatile int*)g.done) return;
   __shared__ double red[32];
   double dmax = 0.0;
@@ -33,14 +33,20 @@ __global__ void finalize_kernel(const GeomDev* geoms) {
     double t = TL_acc[c];
     TL_acc[c] = 0.0;
     if (g.tlq) {  // skewed per-quadrant partials of the 2D warp kernel
-      const int x = c % g.nx, y = c / g.nx;
-      for (int q = 0; q < 4; ++q) {
-        const int ip = (q & 1) ? g.nx - 1 - x : x;
-        const int jp = (q & 2) ? g.ny - 1 - y : y;
-        const size_t k = ((size_t)q * g.nx + (ip + jp) % g.nx) * g.ny + jp;
-        t += g.tlq[k];
-        g.tlq[k] = 0.0;
+      const int nx = g.nx, ny = g.ny;
+      const int x = c % nx, y = c / nx;
+      size_t k[4];
+      double p[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {  // all loads first: the zeroing stores come after
+        const int ip = (q & 1) ? nx - 1 - x : x;
+        const int jp = (q & 2) ? ny - 1 - y : y;
+        k[q] = ((size_t)q * nx + (ip + jp) % nx) * ny + jp;
+        p[q] = g.tlq[k[q]];
       }
+      t += (p[0] + p[1]) + (p[2] + p[3]);
+#pragma unroll
+      for (int q = 0; q < 4; ++q) g.tlq[k[q]] = 0.0;
     }
     if (!isfinite(t)) nonfin = 1;
     dmax = fmax(dmax, fabs(t - TL[c]));
@@ -75,7 +81,7 @@ __global__ void finalize_kernel(const GeomDev* geoms) {
 // partials, kappa from the hot-face flux, and the stopping test of
 // Algorithm 1.
 __global__ void finalize_tail_kernel(const GeomDev* geoms, int nblocks) {
-  const GeomDev& g = geoms[blockIdx.x];
+  const GeomDev g = geoms[blockIdx.x];
   if (*(volatile int*)g.done) return;
   double m = 0.0;
   for (int b = threadIdx.x; b < nblocks; b += 32) m = fmax(m, g.blk_part[b]);
