@@ -30,6 +30,8 @@ def main(argv=None):
     ap.add_argument("--kernel", default="auto", choices=["auto", "warp", "block", "block3d"])
     ap.add_argument("--group-size", type=int, default=0)
     ap.add_argument("--rows-per-thread", type=int, default=0)
+    ap.add_argument("--fourier-tol", type=float, default=0.0)
+    ap.add_argument("--fourier-max-iter", type=int, default=0)
     ap.add_argument("--time", action="store_true")
     a = ap.parse_args(argv)
     build.build()
@@ -37,7 +39,8 @@ def main(argv=None):
     kw = dict(precision=a.precision, accel=a.accel, kernel=a.kernel, group_size=a.group_size,
               rows_per_thread=a.rows_per_thread)
     if a.time:
-        kw.update(tol=1e-6, max_iter=3000, check_every=8, profile=True)
+        kw.update(tol=1e-6, max_iter=3000, check_every=8, profile=True, fourier_tol=a.fourier_tol,
+                  fourier_max_iter=a.fourier_max_iter)
     else:
         kw.update(tol=0.0, max_iter=a.iters, check_every=1, use_graph=False, fourier_max_iter=5)
     t0 = time.perf_counter()
@@ -56,7 +59,8 @@ def main(argv=None):
         n = max(1, st["n_sweeps"])
         out.update(sweep_ms_per_launch=st["time_sweep_ms"] / n,
                    finalize_ms_per_launch=st["time_finalize_ms"] / n,
-                   iter_ms=st["time_iter_ms"], fourier_ms=st["time_fourier_ms"])
+                   iter_ms=st["time_iter_ms"], fourier_ms=st["time_fourier_ms"],
+                   fourier_iterations=st["fourier_iterations"])
     print(json.dumps(out))
 
 
