@@ -230,32 +230,34 @@ template <typename T>
 __global__ void __launch_bounds__(1024) fourier_cg_block_kernel(const CGArgs* jobs) {
   const CGArgs& a = jobs[blockIdx.x];
   __shared__ double red[32];
+  __shared__ double bval[2];
+  __shared__ T sc[2];   // alpha, beta in the vector precision
+  __shared__ int sf;    // run
   const int n = a.nx * a.ny * a.nz;
   const int t0 = threadIdx.x, st = blockDim.x;
   T* x = reinterpret_cast<T*>(a.x);
   T* r = reinterpret_cast<T*>(a.r);
   T* p = reinterpret_cast<T*>(a.p);
   T* q = reinterpret_cast<T*>(a.q);
-  __shared__ double bval[2];
-  auto bsum = [&](double v) -> double {  // block sum, valid in every thread
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  // block sum, valid in thread 0: per thread and per warp in the vector
+  // precision, FP64 across warps; the CG scalars are formed by thread 0 (the
+  // FP64 pipe is narrow, a division in every thread would bind it)
+  auto bsum = [&](T u) -> double {
+    for (int o = 16; o > 0; o >>= 1) u += __shfl_xor_sync(0xffffffffu, u, o);
     __syncthreads();
-    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = (double)u;
     __syncthreads();
-    if (threadIdx.x == 0) {
-      double s = 0.0;
+    double s = 0.0;
+    if (threadIdx.x == 0)
       for (int i = 0; i < (int)((blockDim.x + 31) >> 5); ++i) s += red[i];
-      bval[0] = s;
-    }
-    __syncthreads();
-    return bval[0];
+    return s;
   };
   for (int c = t0; c < n; c += st) {
     const int xi = c % a.nx;
     x[c] = (a.code[c] & CODE_SOLID) ? (T)(-a.dT * ((xi + 0.5) / a.nx - 0.5)) : T(0);
   }
   __syncthreads();
-  double rr_l = 0.0, bb_l = 0.0;
+  T rr_l = T(0), bb_l = T(0);
   for (int c = t0; c < n; c += st) {
     const uint8_t code = a.code[c];
     T rc = T(0);
@@ -265,18 +267,20 @@ __global__ void __launch_bounds__(1024) fourier_cg_block_kernel(const CGArgs* jo
       if (xi == 0 && !(code & CODE_WALL_XM)) b += a.wx * a.dT;
       if (xi == a.nx - 1 && !(code & CODE_WALL_XP)) b -= a.wx * a.dT;
       rc = (T)b - apply_A<T>(a, x, c, code, xi, yi, zi);
-      bb_l += b * b;
+      bb_l += (T)(b * b);
     }
     r[c] = rc;
     p[c] = rc;
-    rr_l += (double)rc * (double)rc;
+    rr_l += rc * rc;
   }
-  double rr = bsum(rr_l);
+  double rr = bsum(rr_l);  // thread 0
   const double bb = bsum(bb_l);
   const double stop = a.tol * a.tol * bb;
   int it = 0;
-  while (it < a.max_iter && rr > stop && bb > 0.0) {
-    double pq_l = 0.0;
+  if (threadIdx.x == 0) sf = (it < a.max_iter && rr > stop && bb > 0.0) ? 1 : 0;
+  __syncthreads();
+  while (sf) {
+    T pq_l = T(0);
     for (int c = t0; c < n; c += st) {
       const uint8_t code = a.code[c];
       T qc = T(0);
@@ -285,34 +289,46 @@ __global__ void __launch_bounds__(1024) fourier_cg_block_kernel(const CGArgs* jo
         qc = apply_A<T>(a, p, c, code, xi, yi, zi);
       }
       q[c] = qc;
-      pq_l += (double)p[c] * (double)qc;
+      pq_l += p[c] * qc;
     }
     const double pq = bsum(pq_l);
-    if (!(pq > 0.0)) break;
-    const double alpha = rr / pq;
-    double rn_l = 0.0;
+    if (threadIdx.x == 0) {
+      sf = pq > 0.0 ? 1 : 0;
+      sc[0] = (T)(pq > 0.0 ? rr / pq : 0.0);
+    }
+    __syncthreads();
+    if (!sf) break;
+    const T al = sc[0];
+    T rn_l = T(0);
     for (int c = t0; c < n; c += st) {
-      x[c] += (T)alpha * p[c];
-      const T rc = r[c] - (T)alpha * q[c];
+      x[c] += al * p[c];
+      const T rc = r[c] - al * q[c];
       r[c] = rc;
-      rn_l += (double)rc * (double)rc;
+      rn_l += rc * rc;
     }
     const double rn = bsum(rn_l);
-    const double beta = rn / rr;
-    rr = rn;
-    for (int c = t0; c < n; c += st) p[c] = r[c] + (T)beta * p[c];
+    if (threadIdx.x == 0) {
+      sc[1] = (T)(rn / rr);
+      rr = rn;
+      ++it;
+      sf = (it < a.max_iter && rr > stop) ? 1 : 0;
+    }
     __syncthreads();
-    ++it;
+    const T be = sc[1];
+    for (int c = t0; c < n; c += st) p[c] = r[c] + be * p[c];
+    __syncthreads();
   }
-  double sum_l = 0.0, cnt_l = 0.0;
+  T sum_l = T(0), cnt_l = T(0);
   for (int c = t0; c < n; c += st)
     if (a.code[c] & CODE_SOLID) {
-      sum_l += (double)x[c];
-      cnt_l += 1.0;
+      sum_l += x[c];
+      cnt_l += T(1);
     }
   const double sum = bsum(sum_l);
   const double cnt = bsum(cnt_l);
-  const double mean = cnt > 0 ? sum / cnt : 0.0;
+  if (threadIdx.x == 0) bval[0] = cnt > 0 ? sum / cnt : 0.0;
+  __syncthreads();
+  const double mean = bval[0];
   for (int c = t0; c < n; c += st) a.T_out[c] = (a.code[c] & CODE_SOLID) ? (double)x[c] - mean : 0.0;
   if (t0 == 0) *a.iters_out = it;
 }
