@@ -26,6 +26,8 @@
 // the sweep precision, widened exactly) are predicated on solid cells.
 #pragma once
 
+#include <type_traits>
+
 #include "sweep.cuh"
 
 namespace obte {
@@ -105,6 +107,13 @@ __global__ void __launch_bounds__(Sweep3DCfg<RMAX>::NT, 1) sweep3d_kernel(const 
   const int flags = L.flags;
   const bool rare_pass = (flags & (SWEEP_FLUX | SWEEP_RECORD)) != 0;
   auto XA = [&](int b, int r, int g, int th) -> T& { return xall[((b * RMAX + r) * G + g) * NT + th]; };
+  // FP32 without s(x), G even: ordinates in pairs (float2) through the paired
+  // FP32 instructions; the exchange buffer then holds pairs, [b][r][h][thread]
+  constexpr bool X2 = sizeof(T) == 4 && !HAS_S && (G % 2 == 0);
+  constexpr int GV = X2 ? G / 2 : G;
+  using VV = typename std::conditional<X2, float2, T>::type;
+  VV* xall2 = reinterpret_cast<VV*>(smem_raw);
+  auto XP = [&](int b, int r, int h, int th) -> VV& { return xall2[((b * RMAX + r) * GV + h) * NT + th]; };
 
   const int item = blockIdx.x;
   if (item >= L.n_items) return;
@@ -160,17 +169,32 @@ __global__ void __launch_bounds__(Sweep3DCfg<RMAX>::NT, 1) sweep3d_kernel(const 
   const int out_side_x = sx > 0 ? 1 : 0, out_side_y = sy > 0 ? 3 : 2, out_side_z = sz > 0 ? 5 : 4;
   double* wacc = gm.wall_acc;
 
-  T v[RMAX][G];
+  VV v[RMAX][GV];
+  auto VG = [&](int r, int g) -> T& {
+    if constexpr (X2) return (g & 1) ? v[r][g >> 1].y : v[r][g >> 1].x;
+    else return v[r][g];
+  };
+  VV A0v[GV], AXv[GV], AYv[GV], AZv[GV], AWv[GV];
+#pragma unroll
+  for (int h = 0; h < GV; ++h) {
+    if constexpr (X2) {
+      A0v[h] = make_float2(A0[2 * h], A0[2 * h + 1]);
+      AXv[h] = make_float2(AX[2 * h], AX[2 * h + 1]);
+      AYv[h] = make_float2(AY[2 * h], AY[2 * h + 1]);
+      AZv[h] = make_float2(AZ[2 * h], AZ[2 * h + 1]);
+      AWv[h] = make_float2(AW[2 * h], AW[2 * h + 1]);
+    }
+  }
   const T* front = reinterpret_cast<const T*>(gm.front);
 #pragma unroll
   for (int r = 0; r < RMAX; ++r)
 #pragma unroll
     for (int g = 0; g < G; ++g)
-      v[r][g] = (active && g < cnt) ? front[(size_t)(o0 + g) * rows + row0 + r] : T(0);
+      VG(r, g) = (active && g < cnt) ? front[(size_t)(o0 + g) * rows + row0 + r] : T(0);
 #pragma unroll
   for (int r = 0; r < RMAX; ++r)
 #pragma unroll
-    for (int g = 0; g < G; ++g) XA(1, r, g, t) = v[r][g];
+    for (int h = 0; h < GV; ++h) XP(1, r, h, t) = v[r][h];
 
   int tb = -1;  // thread owning the row below j0 (same plane)
   if (active) {
@@ -217,9 +241,12 @@ __global__ void __launch_bounds__(Sweep3DCfg<RMAX>::NT, 1) sweep3d_kernel(const 
     T rn[RMAX][5];
     if (d + 1 < nx) load_recs(s_next, rn);
     if (active) {
-      T dny[G];
+      VV dny[GV];
 #pragma unroll
-      for (int g = 0; g < G; ++g) dny[g] = (tb >= 0) ? XA(prv, RMAX - 1, g, tb) : T(0);
+      for (int h = 0; h < GV; ++h) {
+        if constexpr (X2) dny[h] = (tb >= 0) ? XP(prv, RMAX - 1, h, tb) : make_float2(0.f, 0.f);
+        else dny[h] = (tb >= 0) ? XP(prv, RMAX - 1, h, tb) : T(0);
+      }
       uint32_t pk[RMAX];
       T tls[RMAX];
       // branch-free update of all rows (top row first: the row below in y
@@ -233,12 +260,39 @@ __global__ void __launch_bounds__(Sweep3DCfg<RMAX>::NT, 1) sweep3d_kernel(const 
         const bool jump = packed & REC_JUMP;
         T sval = T(1);
         if (HAS_S) sval = (T)__ldg(sv_ptr + (packed & REC_CELL_MASK));
+        if constexpr (X2) {
+          // u = m T + t per direction: the upwind value, the wall
+          // temperature (m = 0), or the value across the jump (the record's
+          // x field holds +-dT on the jump column)
+          const float mx = wx ? 0.f : 1.f, my = wy ? 0.f : 1.f, mz = wz ? 0.f : 1.f;
+          const float2 mx2 = make_float2(mx, mx), tx2 = make_float2(twx, twx);
+          const float2 my2 = make_float2(my, my), ty2 = make_float2(twy, twy);
+          const float2 mz2 = make_float2(mz, mz), tz2 = make_float2(twz, twz);
+          const float2 src2 = make_float2(src, src);
+          float2 tlp = make_float2(0.f, 0.f);
+#pragma unroll
+          for (int h = 0; h < GV; ++h) {
+            const float2 ux = __ffma2_rn(mx2, v[r][h], tx2);
+            const float2 ud = r > 0 ? v[r > 0 ? r - 1 : 0][h] : dny[h];
+            const float2 uy = __ffma2_rn(my2, ud, ty2);
+            const float2 uzv = (tz >= 0) ? XP(prv, r, h, tz) : make_float2(0.f, 0.f);
+            const float2 uz = __ffma2_rn(mz2, uzv, tz2);
+            float2 acc = __fmul2_rn(src2, A0v[h]);
+            acc = __ffma2_rn(AXv[h], ux, acc);
+            acc = __ffma2_rn(AYv[h], uy, acc);
+            acc = __ffma2_rn(AZv[h], uz, acc);
+            v[r][h] = acc;
+            tlp = __ffma2_rn(AWv[h], acc, tlp);
+          }
+          pk[r] = packed;
+          tls[r] = tlp.x + tlp.y;
+        } else {
         T tl = T(0), tl2 = T(0);
 #pragma unroll
         for (int g = 0; g < G; ++g) {
-          const T ux = wx ? twx : v[r][g];
-          const T uy = wy ? twy : (r > 0 ? v[r > 0 ? r - 1 : 0][g] : dny[g]);
-          const T uz = wz ? twz : ((tz >= 0) ? XA(prv, r, g, tz) : T(0));
+          const T ux = wx ? twx : VG(r, g);
+          const T uy = wy ? twy : (r > 0 ? VG(r > 0 ? r - 1 : 0, g) : dny[g]);
+          const T uz = wz ? twz : ((tz >= 0) ? XP(prv, r, g, tz) : T(0));
           const T jx = jump ? JX[g] : T(0);
           T acc;
           if (HAS_S) acc = src + jx;
@@ -251,12 +305,13 @@ __global__ void __launch_bounds__(Sweep3DCfg<RMAX>::NT, 1) sweep3d_kernel(const 
           } else {
             val = acc;
           }
-          v[r][g] = val;
+          VG(r, g) = val;
           if (g & 1) tl2 = fma(AW[g], val, tl2);
           else tl = fma(AW[g], val, tl);
         }
         pk[r] = packed;
         tls[r] = tl + tl2;
+        }
       }
       uint32_t rare_mask = 0;
 #pragma unroll
@@ -275,7 +330,7 @@ __global__ void __launch_bounds__(Sweep3DCfg<RMAX>::NT, 1) sweep3d_kernel(const 
           const bool last = packed & REC_LAST;
           if (rare_pass) {
 #pragma unroll
-            for (int g = 0; g < G; ++g) scratch[g * nthr + t] = v[r][g];
+            for (int g = 0; g < G; ++g) scratch[g * nthr + t] = VG(r, g);
             phi += cell_epilogue_3d<T, G>(gm, scratch + t, nthr, cell, packed, last, o0, cnt, sx,
                                           sy, sz, flags, kx_sum);
             continue;
@@ -283,7 +338,7 @@ __global__ void __launch_bounds__(Sweep3DCfg<RMAX>::NT, 1) sweep3d_kernel(const 
           if (packed & (REC_WOUT_X | REC_LAST)) {
             T sk = T(0);
 #pragma unroll
-            for (int g = 0; g < G; ++g) sk = fma(kcoef[0][g], v[r][g], sk);
+            for (int g = 0; g < G; ++g) sk = fma(kcoef[0][g], VG(r, g), sk);
             const double dk = widen(sk);
             if (packed & REC_WOUT_X) atomicAdd(wacc + (size_t)cell * 6 + out_side_x, dk);
             else phi += (sx > 0 ? dk : -dk) + (sx > 0 ? dT * kx_sum : 0.0);
@@ -291,13 +346,13 @@ __global__ void __launch_bounds__(Sweep3DCfg<RMAX>::NT, 1) sweep3d_kernel(const 
           if (packed & REC_WOUT_Y) {
             T sk = T(0);
 #pragma unroll
-            for (int g = 0; g < G; ++g) sk = fma(kcoef[1][g], v[r][g], sk);
+            for (int g = 0; g < G; ++g) sk = fma(kcoef[1][g], VG(r, g), sk);
             atomicAdd(wacc + (size_t)cell * 6 + out_side_y, widen(sk));
           }
           if (packed & REC_WOUT_Z) {
             T sk = T(0);
 #pragma unroll
-            for (int g = 0; g < G; ++g) sk = fma(kcoef[2][g], v[r][g], sk);
+            for (int g = 0; g < G; ++g) sk = fma(kcoef[2][g], VG(r, g), sk);
             atomicAdd(wacc + (size_t)cell * 6 + out_side_z, widen(sk));
           }
         }
@@ -310,7 +365,7 @@ __global__ void __launch_bounds__(Sweep3DCfg<RMAX>::NT, 1) sweep3d_kernel(const 
 #pragma unroll
       for (int r = 0; r < RMAX; ++r)
 #pragma unroll
-        for (int g = 0; g < G; ++g) XA(cur, r, g, t) = v[r][g];
+        for (int h = 0; h < GV; ++h) XP(cur, r, h, t) = v[r][h];
     }
 #pragma unroll
     for (int r = 0; r < RMAX; ++r)
@@ -325,7 +380,7 @@ __global__ void __launch_bounds__(Sweep3DCfg<RMAX>::NT, 1) sweep3d_kernel(const 
   for (int r = 0; r < RMAX; ++r)
 #pragma unroll
     for (int g = 0; g < G; ++g)
-      if (active && g < cnt) frontw[(size_t)(o0 + g) * rows + row0 + r] = v[r][g];
+      if (active && g < cnt) frontw[(size_t)(o0 + g) * rows + row0 + r] = VG(r, g);
   const double ps = block_sum(phi, red);
   if (t == 0 && ps != 0.0) atomicAdd(gm.phi_acc, ps);
 }
