@@ -19,8 +19,7 @@
 // prefetched one step ahead with cp.async into lane-private shared memory.
 // The T_L partials of a step go, transposed through shared memory, to skewed
 // per-quadrant FP64 accumulators [s][j'], so that one atomic instruction of
-// the warp covers 32 consecutive rows (or, when the warp's rows do not fill
-// 32 lanes, to the cell's accumulator directly).
+// the warp covers 32 consecutive rows.
 //
 // Cells are updated branch-free (pores too: a pore's value is never read by a
 // solid cell, whose faces towards a pore are walls); only the atomics and the
@@ -298,15 +297,16 @@ __global__ void __launch_bounds__(32 * WarpCfg<T, G, RMAX>::WPB, WarpCfg<T, G, R
     const int below = lane > 0 ? lane - 1 : (gm.py ? tpp - 1 : 0);
     const int out_x_side = sx > 0 ? 1 : 0, out_y_side = sy > 0 ? 3 : 2;
     double phi = 0.0;
-    // Moments of a full 32-lane warp go through shared memory so that one
+    // The warp's T_L partials go by row through shared memory so that one
     // atomic instruction covers 32 consecutive rows of the skewed
     // accumulator (8 sectors instead of 32).
-    const bool tr_atom = RFIXED && full_run && tlq != nullptr;
+    const bool tr_atom = tlq != nullptr;
     // SWEEP_BLOCK_COMBINE: the block's warps hold groups of one octant with
     // one start column, so row j's partials of the four warps are added in
     // shared memory (FP32, fixed order) and each warp issues the atomics of a
     // quarter of the rows: a block barrier per step, a quarter of the atomics
-    const bool comb = WPB == 4 && tr_atom && (flags & SWEEP_BLOCK_COMBINE) && !L.item_counter;
+    const bool comb = WPB == 4 && RFIXED && full_run && tr_atom && (flags & SWEEP_BLOCK_COMBINE) &&
+                      !L.item_counter;
     int par = 0;
     // hot-face flux: each row crosses the hot column once per sweep, so its
     // sum_g K_gx T_g is kept per row in the sweep precision and widened once
@@ -460,7 +460,7 @@ __global__ void __launch_bounds__(32 * WarpCfg<T, G, RMAX>::WPB, WarpCfg<T, G, R
         if (tr_atom) {
 #pragma unroll
           for (int r = 0; r < RMAX; ++r)
-            tlbuf[par][wib][lane * RMAX + r] = (pk[r] & REC_SOLID) ? tls[r] : T(0);
+            if (RFIXED || r >= rb) tlbuf[par][wib][j0 + r - rb] = (pk[r] & REC_SOLID) ? tls[r] : T(0);
         } else {
 #pragma unroll
           for (int r = 0; r < RMAX; ++r)
@@ -486,7 +486,9 @@ __global__ void __launch_bounds__(32 * WarpCfg<T, G, RMAX>::WPB, WarpCfg<T, G, R
         __syncwarp();
         double* row = tlq + (size_t)s * ny + lane;
 #pragma unroll
-        for (int r = 0; r < RMAX; ++r) atomicAdd(row + 32 * r, (double)tlbuf[par][wib][32 * r + lane]);
+        for (int r = 0; r < RMAX; ++r)
+          if (RFIXED && full_run ? true : 32 * r + lane < ny)
+            atomicAdd(row + 32 * r, (double)tlbuf[par][wib][32 * r + lane]);
       }
       s = s_next;
       cur = (cur + 1 == NST) ? 0 : cur + 1;
