@@ -322,6 +322,10 @@ def main():
         e2e = {"value": e2e_updates / (statistics.median(e2e_ms) * 1e-3), "unit": UNIT,
                "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
                "ms_per_step": statistics.median(e2e_ms)}
+        # measured FMA throughput (context for the derived ALU peak)
+        from paper_2106_02764_gb300.binding import measure_fma_rate
+        fma32 = measure_fma_rate("mixed", local) / 1e12
+        fma64 = measure_fma_rate("fp64", local) / 1e12
         cpu = None
         if not a.no_cpu_baseline:
             cpu = cpu_oracle_rate(wl, a.cpu_seconds)
@@ -342,7 +346,9 @@ def main():
                          "frac": achieved / peak, "traffic": traffic_from_profile("cfg2_mixed"),
                          "kernel": "sweep2d_warp_kernel<float,G,R> (2D warp-per-group sweep)",
                          "flop_per_launch": flops_launch, "avg_launch_ms": sweep_ms,
-                         "peak_note": "FP32 FMA pipes: 152 SMs x 128 lanes x 2 flop x 2070 MHz (max clock)"},
+                         "peak_note": "FP32 FMA pipes: 152 SMs x 128 lanes x 2 flop x 2070 MHz (max clock)",
+                         "measured_fma_tflops": {"fp32": fma32, "fp64": fma64},
+                         "frac_of_measured_fp32": achieved / fma32 if fma32 > 0 else None},
             "cpu_baseline": cpu,
             "e2e": e2e,
             "clocks": clk,

@@ -214,6 +214,14 @@ int obte_kappa_grad_s_noalloc(obte_ctx* ctx, double* out);
  * Runs with obte_get_flux's extra sweep. */
 int obte_get_kappa_bins(obte_ctx* ctx, double* out);
 
+/* Measured FMA throughput of a device, in flop/s (2 per FMA): precision
+ * OBTE_MIXED times FP32 FMAs, OBTE_FP64 FP64 FMAs, in a kernel of independent
+ * FMA chains over every SM (about 10 ms).  The ALU roof of the sweep, for the
+ * roofline beside the peak derived from unit counts and clocks.  Needs no
+ * context; allocates nothing.  The paper has no counterpart (a measurement
+ * utility). */
+int obte_measure_fma_rate(int precision, int device, double* flops_per_s);
+
 const char* obte_last_error(const obte_ctx* ctx);
 void obte_destroy(obte_ctx* ctx);
 

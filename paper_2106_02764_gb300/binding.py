@@ -79,6 +79,7 @@ SIGNATURES = [
     ("obte_kappa_grad_s", C.c_int, [C.c_void_p, C.c_void_p, C.c_size_t]),
     ("obte_get_kappa_bins", C.c_int, [C.c_void_p, C.c_void_p]),
     ("obte_kappa_grad_s_noalloc", C.c_int, [C.c_void_p, C.c_void_p]),
+    ("obte_measure_fma_rate", C.c_int, [C.c_int, C.c_int, C.POINTER(C.c_double)]),
     ("obte_last_error", C.c_char_p, [C.c_void_p]),
     ("obte_destroy", None, [C.c_void_p]),
 ]
@@ -301,3 +302,15 @@ def solve_batch(solvers, allow_not_converged=False, **kw):
     if rc != OBTE_OK and not (rc == OBTE_NOT_CONVERGED and allow_not_converged):
         raise ObteError(rc, lib.obte_last_error(solvers[0].ctx).decode())
     return [s.stats for s in solvers]
+
+
+def measure_fma_rate(precision="mixed", device=0) -> float:
+    """Measured FMA throughput of a device in flop/s (FP32 for "mixed", FP64
+    for "fp64"): the ALU roof of the transport sweep."""
+    lib = load_library()
+    out = C.c_double()
+    p = OBTE_MIXED if precision in ("mixed", OBTE_MIXED) else OBTE_FP64
+    rc = lib.obte_measure_fma_rate(p, int(device), C.byref(out))
+    if rc != OBTE_OK:
+        raise ObteError(rc, "FMA rate measurement failed")
+    return out.value
