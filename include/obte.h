@@ -216,7 +216,7 @@ int obte_get_kappa_bins(obte_ctx* ctx, double* out);
 
 /* Measured FMA throughput of a device, in flop/s (2 per FMA): precision
  * OBTE_MIXED times FP32 FMAs, OBTE_FP64 FP64 FMAs, in a kernel of independent
- * FMA chains over every SM (about 10 ms).  The ALU roof of the sweep, for the
+ * FMA chains over every SM (a few ms).  The ALU roof of the sweep, for the
  * roofline beside the peak derived from unit counts and clocks.  Needs no
  * context; allocates nothing.  The paper has no counterpart (a measurement
  * utility). */

@@ -207,3 +207,15 @@ def test_3d_periodic_cube_porefree():
     for precision in ("fp64", "mixed"):
         s, st = gpu(wl, precision)
         _check(wl, pr, ref, s, precision)
+
+
+def test_fma_rate_measurement():
+    """The measured FMA throughput is positive and below the unit-count peak
+    (152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz = 80.5 TFLOP/s, with a
+    margin for a box with more SMs or a higher boost clock); FP64 is far
+    slower than FP32 on this part."""
+    from paper_2106_02764_gb300.binding import measure_fma_rate
+    f32 = measure_fma_rate("mixed") / 1e12
+    f64 = measure_fma_rate("fp64") / 1e12
+    assert 1.0 < f32 < 1.3 * 80.5
+    assert 0.0 < f64 < f32
