@@ -635,7 +635,8 @@ static cudaError_t launch_fourier_cg_cluster(const CGArgs& a, int n, int precisi
     }
     int rpc_arg = rpc;
     void* args[] = {const_cast<CGArgs*>(&a), &rpc_arg};
-    return cudaLaunchKernelExC(&cfg, kern, args);
+    if (cudaLaunchKernelExC(&cfg, kern, args) == cudaSuccess) return cudaSuccess;
+    cudaGetLastError();  // launch refused: try the next size, then the grid form
   }
   return cudaErrorNotSupported;
 }
