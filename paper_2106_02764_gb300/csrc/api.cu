@@ -1620,10 +1620,17 @@ extern "C" int obte_solve_batch(obte_ctx* const* ctxs, int n, const obte_solve_o
   }
   CGArgs* jobs_d = nullptr;
   if (!jobs.empty()) {
+    // largest first: clusters of the big meshes start in the first wave
+    std::stable_sort(jobs.begin(), jobs.end(), [](const CGArgs& x, const CGArgs& y) {
+      return (long)x.nx * x.ny * x.nz > (long)y.nx * y.ny * y.nz;
+    });
     jobs_d = ctx->dalloc_t<CGArgs>(jobs.size());
     NEED(jobs_d);
     CK(cudaMemcpyAsync(jobs_d, jobs.data(), sizeof(CGArgs) * jobs.size(), cudaMemcpyHostToDevice, ctx->stream));
-    CK(launch_fourier_cg_blocks(jobs_d, (int)jobs.size(), prec, ctx->stream));
+    const cudaError_t ec = launch_fourier_cg_cluster_jobs(jobs_d, jobs.data(), (int)jobs.size(), prec,
+                                                          ctx->stream);
+    if (ec == cudaErrorNotSupported) CK(launch_fourier_cg_blocks(jobs_d, (int)jobs.size(), prec, ctx->stream));
+    else CK(ec);
   }
   for (int i = 0; i < n; ++i) {
     obte_ctx* c = ctxs[i];

@@ -12,6 +12,8 @@
 // removed at the end.  CG starts from the linear profile -dT (x + 1/2) / nx.
 #include <cooperative_groups.h>
 
+#include <algorithm>
+
 #include "obte_internal.h"
 
 namespace cg = cooperative_groups;
@@ -345,7 +347,7 @@ __global__ void __launch_bounds__(1024) fourier_cg_block_kernel(const CGArgs* jo
 // CTA; two slots used alternately, so a barrier per reduction suffices).  No
 // grid-wide synchronisation and no global-memory traffic in the iteration.
 template <typename T>
-__global__ void __launch_bounds__(1024, 1) fourier_cg_cluster_kernel(CGArgs a, int rpc) {
+__device__ __forceinline__ void cluster_cg(const CGArgs& a, int rpc) {
   cg::cluster_group cl = cg::this_cluster();
   const int rank = (int)cl.block_rank();
   const int ncl = (int)cl.num_blocks();
@@ -556,6 +558,21 @@ __global__ void __launch_bounds__(1024, 1) fourier_cg_cluster_kernel(CGArgs a, i
   cl.sync();  // no CTA leaves while others may still read its shared memory
 }
 
+template <typename T>
+__global__ void __launch_bounds__(1024, 1) fourier_cg_cluster_kernel(CGArgs a, int rpc) {
+  cluster_cg<T>(a, rpc);
+}
+
+// many geometries: cluster c of the grid solves jobs[c] (rows cut evenly)
+template <typename T>
+__global__ void __launch_bounds__(1024, 1) fourier_cg_cluster_jobs_kernel(const CGArgs* jobs) {
+  cg::cluster_group cl = cg::this_cluster();
+  const int ncl = (int)cl.num_blocks();
+  const CGArgs a = jobs[blockIdx.x / ncl];
+  const int rows = a.ny * a.nz;
+  cluster_cg<T>(a, (rows + ncl - 1) / ncl);
+}
+
 }  // namespace
 
 CGArgs make_cg_args(const GeomDev& g, double hx, double hy, double hz, int max_iter, double tol,
@@ -637,6 +654,50 @@ static cudaError_t launch_fourier_cg_cluster(const CGArgs& a, int n, int precisi
     void* args[] = {const_cast<CGArgs*>(&a), &rpc_arg};
     if (cudaLaunchKernelExC(&cfg, kern, args) == cudaSuccess) return cudaSuccess;
     cudaGetLastError();  // launch refused: try the next size, then the grid form
+  }
+  return cudaErrorNotSupported;
+}
+
+cudaError_t launch_fourier_cg_cluster_jobs(const CGArgs* jobs_dev, const CGArgs* jobs_host, int n_jobs,
+                                           int precision, cudaStream_t st) {
+  if (precision == 0 || n_jobs < 1) return cudaErrorNotSupported;
+  void* kern = (void*)fourier_cg_cluster_jobs_kernel<float>;
+  for (int ncl : {8, 4}) {
+    size_t smem = 0;
+    bool fits = true;
+    for (int j = 0; j < n_jobs; ++j) {
+      const CGArgs& a = jobs_host[j];
+      if (a.nx > 1024) fits = false;
+      const int rpc = (a.ny * a.nz + ncl - 1) / ncl;
+      smem = std::max(smem, 4 * sizeof(float) * (size_t)rpc * a.nx + (size_t)rpc * a.nx);
+    }
+    if (!fits) return cudaErrorNotSupported;
+    if (smem > 200 * 1024) continue;
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
+      cudaGetLastError();
+      continue;
+    }
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(ncl * n_jobs);
+    cfg.blockDim = dim3(1024);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = ncl;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    int clusters = 0;
+    if (cudaOccupancyMaxActiveClusters(&clusters, kern, &cfg) != cudaSuccess || clusters < 1) {
+      cudaGetLastError();
+      continue;
+    }
+    const CGArgs* jd = jobs_dev;
+    void* args[] = {&jd};
+    if (cudaLaunchKernelExC(&cfg, kern, args) == cudaSuccess) return cudaSuccess;
+    cudaGetLastError();
   }
   return cudaErrorNotSupported;
 }

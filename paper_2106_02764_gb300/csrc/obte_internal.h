@@ -200,6 +200,10 @@ struct CGArgs {
 };
 CGArgs make_cg_args(const GeomDev& g, double hx, double hy, double hz, int max_iter, double tol,
                     double* T_out, int* iters_out, double* work, int blocks_max);
+// one thread-block cluster per job (FP32; every job's rows must fit the
+// cluster's shared memory); cudaErrorNotSupported when it does not apply
+cudaError_t launch_fourier_cg_cluster_jobs(const CGArgs* jobs_dev, const CGArgs* jobs_host, int n_jobs,
+                                           int precision, cudaStream_t st);
 // one block per job (geometries up to kBlockCGMaxCells cells)
 cudaError_t launch_fourier_cg_blocks(const CGArgs* jobs_dev, int n_jobs, int precision,
                                      cudaStream_t st);
