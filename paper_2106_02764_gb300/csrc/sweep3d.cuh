@@ -102,11 +102,9 @@ __global__ void __launch_bounds__(Sweep3DCfg<RMAX>::NT, 1) sweep3d_kernel(const 
   __shared__ T kcoef[3][G];  // |K_gx|, |K_gy|, |K_gz| of the group (rare path only)
   const int nthr = NT;
   const int t = threadIdx.x;
-  T* xall = reinterpret_cast<T*>(smem_raw);  // [2][RMAX][G][NT]
-  T* scratch = xall + 2 * RMAX * G * NT;     // [G][NT]
+  T* scratch = reinterpret_cast<T*>(smem_raw) + 2 * RMAX * G * NT;  // [G][NT] after the exchange
   const int flags = L.flags;
   const bool rare_pass = (flags & (SWEEP_FLUX | SWEEP_RECORD)) != 0;
-  auto XA = [&](int b, int r, int g, int th) -> T& { return xall[((b * RMAX + r) * G + g) * NT + th]; };
   // FP32 without s(x), G even: ordinates in pairs (float2) through the paired
   // FP32 instructions; the exchange buffer then holds pairs, [b][r][h][thread]
   constexpr bool X2 = sizeof(T) == 4 && !HAS_S && (G % 2 == 0);
