@@ -214,6 +214,26 @@ int obte_kappa_grad_s_noalloc(obte_ctx* ctx, double* out);
  * Runs with obte_get_flux's extra sweep. */
 int obte_get_kappa_bins(obte_ctx* ctx, double* out);
 
+/* Fourier model alone (App. B; the paper's Fourier-only run): heat
+ * conduction with the bulk conductivity kappa_bulk = sum_m kappa_m in the
+ * solid cells, adiabatic pore and film walls, and the applied jump dT across
+ * the gradient period, solved by FP64 conjugate gradients on the device (the
+ * solver's first guess run to a tight tolerance).  Needs create_mesh and
+ * set_material; leaves the transport solve's state untouched.
+ *   tol        relative CG residual, |r| <= tol |b| (0: 1e-12)
+ *   max_iter   CG iterations (0: 40 (nx + ny + nz))
+ *   kappa_out  host double: kappa_fourier in W/m/K = L / (dT A_sec) x the
+ *              conductive flux through the solid faces of the plane x = 0
+ *              (App. B, last equation; A_sec the full cross-section)
+ *   T_out      host double[nz][ny][nx] or NULL: the temperature, solid-cell
+ *              mean 0, NaN in pores
+ *   iters_out  host int or NULL: CG iterations taken
+ * Device scratch (5 doubles per cell) comes from the context's allocator and
+ * is freed before the call returns.  OBTE_NOT_CONVERGED when the residual
+ * test is not met within max_iter (the outputs are still written). */
+int obte_solve_fourier(obte_ctx* ctx, double tol, int max_iter, double* kappa_out, double* T_out,
+                       int* iters_out);
+
 /* Measured FMA throughput of a device, in flop/s (2 per FMA): precision
  * OBTE_MIXED times FP32 FMAs, OBTE_FP64 FP64 FMAs, in a kernel of independent
  * FMA chains over every SM (a few ms).  The ALU roof of the sweep, for the

@@ -79,6 +79,8 @@ SIGNATURES = [
     ("obte_kappa_grad_s", C.c_int, [C.c_void_p, C.c_void_p, C.c_size_t]),
     ("obte_get_kappa_bins", C.c_int, [C.c_void_p, C.c_void_p]),
     ("obte_kappa_grad_s_noalloc", C.c_int, [C.c_void_p, C.c_void_p]),
+    ("obte_solve_fourier", C.c_int, [C.c_void_p, C.c_double, C.c_int, C.POINTER(C.c_double),
+                                     C.c_void_p, C.POINTER(C.c_int)]),
     ("obte_measure_fma_rate", C.c_int, [C.c_int, C.c_int, C.POINTER(C.c_double)]),
     ("obte_last_error", C.c_char_p, [C.c_void_p]),
     ("obte_destroy", None, [C.c_void_p]),
@@ -277,6 +279,17 @@ class Solver:
         out = np.empty(self.shape, dtype=np.float64)
         self._check(self.lib.obte_kappa_grad_s(self.ctx, _ptr(out), C.c_size_t(int(max_field_bytes))))
         return out
+
+    def solve_fourier(self, tol=0.0, max_iter=0, allow_not_converged=False):
+        """Fourier model alone (App. B): kappa_fourier in W/m/K, the temperature
+        (solid-cell mean 0, NaN in pores) and the CG iteration count."""
+        k, it = C.c_double(), C.c_int()
+        T = np.empty(self.shape, dtype=np.float64)
+        rc = self.lib.obte_solve_fourier(self.ctx, float(tol), int(max_iter), C.byref(k), _ptr(T),
+                                         C.byref(it))
+        if not (rc == OBTE_NOT_CONVERGED and allow_not_converged):
+            self._check(rc)
+        return {"kappa": k.value, "T": T, "iterations": it.value, "converged": rc == OBTE_OK}
 
 
 def _grad_noalloc(self):

@@ -1363,6 +1363,76 @@ extern "C" int obte_get_kappa_bins(obte_ctx* ctx, double* out) {
 }
 
 // ---------------------------------------------------------------------------
+// Fourier model alone (App. B)
+// ---------------------------------------------------------------------------
+extern "C" int obte_solve_fourier(obte_ctx* ctx, double tol, int max_iter, double* kappa_out,
+                                  double* T_out, int* iters_out) {
+  if (!ctx) return OBTE_EINVAL;
+  if (!ctx->has_mesh || !ctx->has_material) return ctx->fail(OBTE_ESTATE, "create_mesh and set_material first");
+  if (!kappa_out) return ctx->fail(OBTE_EINVAL, "kappa_out is NULL");
+  if (!std::isfinite(tol) || tol < 0.0) return ctx->fail(OBTE_EINVAL, "tol must be finite and >= 0");
+  if (max_iter < 0) return ctx->fail(OBTE_EINVAL, "max_iter must be >= 0");
+  cudaSetDevice(ctx->device);
+  if (tol == 0.0) tol = 1e-12;
+  if (max_iter == 0) max_iter = 40 * (ctx->n[0] + ctx->n[1] + ctx->n[2]);
+  const size_t n = (size_t)ctx->n_cells;
+  const size_t nwork = fourier_work_doubles(ctx->n_cells, kFourierBlocksMax);
+  // one scratch array: the block-form job, T, the CG vectors, the flux sum, the count
+  const size_t job_bytes = (sizeof(CGArgs) + 15) / 16 * 16;
+  char* buf = static_cast<char*>(ctx->dalloc(job_bytes + sizeof(double) * (n + nwork + 1) + 16));
+  NEED(buf);
+  CGArgs* job_d = reinterpret_cast<CGArgs*>(buf);
+  double* Tf = reinterpret_cast<double*>(buf + job_bytes);
+  double* work = Tf + n;
+  double* flux_d = work + nwork;
+  int* it_d = reinterpret_cast<int*>(flux_d + 1);
+  GeomDev g{};
+  g.code = ctx->code_d;
+  g.nx = ctx->n[0];
+  g.ny = ctx->n[1];
+  g.nz = ctx->n[2];
+  g.dim = ctx->dim;
+  g.n_cells = ctx->n_cells;
+  g.py = ctx->periodic[1];
+  g.pz = ctx->dim == 3 ? ctx->periodic[2] : 0;
+  g.dT = ctx->dT;
+  double flux = 0.0;
+  int its = 0;
+  std::vector<double> Th(T_out ? n : 0);
+  auto run = [&]() -> int {
+    if (ctx->n_cells <= 4096) {  // one block, no grid-wide synchronisation
+      const CGArgs job = make_cg_args(g, ctx->h[0], ctx->h[1], ctx->h[2], max_iter, tol, Tf, it_d, work,
+                                      kFourierBlocksMax);
+      CK(cudaMemcpyAsync(job_d, &job, sizeof(CGArgs), cudaMemcpyHostToDevice, ctx->stream));
+      CK(launch_fourier_cg_blocks(job_d, 1, 0, ctx->stream));
+    } else {
+      CK(launch_fourier_cg(g, ctx->h[0], ctx->h[1], ctx->h[2], 0, max_iter, tol, Tf, it_d, work,
+                           kFourierBlocksMax, ctx->stream));
+    }
+    CK(launch_fourier_hot_flux(ctx->code_d, Tf, ctx->n[0], ctx->n[1] * ctx->n[2], ctx->dT, flux_d,
+                               ctx->stream));
+    CK(cudaMemcpyAsync(&flux, flux_d, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaMemcpyAsync(&its, it_d, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+    if (T_out) CK(cudaMemcpyAsync(Th.data(), Tf, sizeof(double) * n, cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    return OBTE_OK;
+  };
+  const int rc = run();
+  if (rc) cudaStreamSynchronize(ctx->stream);  // nothing in flight uses the scratch when it is freed
+  ctx->dfree(buf);
+  if (rc) return rc;
+  double kappa_bulk = 0.0;
+  for (double k : ctx->kappa_m) kappa_bulk += k;
+  // kappa_fourier = L / (dT A_sec) sum_faces kappa_bulk (T_image + dT - T_cell) / h_x
+  *kappa_out = ctx->kappa_scale * kappa_bulk / ctx->h[0] * flux;
+  if (iters_out) *iters_out = its;
+  if (T_out)
+    to_user(ctx, [&](int c, long ui) { T_out[ui] = (ctx->code_h[c] & CODE_SOLID) ? Th[c] : NAN; });
+  if (its >= max_iter) return ctx->fail(OBTE_NOT_CONVERGED, "Fourier CG: residual test not met within max_iter");
+  return OBTE_OK;
+}
+
+// ---------------------------------------------------------------------------
 // d kappa / d s
 // ---------------------------------------------------------------------------
 extern "C" int obte_kappa_grad_s(obte_ctx* ctx, double* out, size_t max_field_bytes) {

@@ -573,6 +573,24 @@ __global__ void __launch_bounds__(1024, 1) fourier_cg_cluster_jobs_kernel(const 
   cluster_cg<T>(a, (rows + ncl - 1) / ncl);
 }
 
+// Conductive flux through the solid faces of the plane x = 0 (App. B, the
+// kappa_fourier equation), in units of kappa_bulk / h_x: the sum over the
+// rows whose x = 0 cell is solid with a solid periodic image at x = nx - 1 of
+// (T_image + dT - T_cell).  One block, fixed summation order.
+__global__ void __launch_bounds__(256) fourier_hot_flux_kernel(const uint8_t* code, const double* T,
+                                                                int nx, int rows, double dT,
+                                                                double* out) {
+  __shared__ double red[8];
+  double s = 0.0;
+  for (int row = threadIdx.x; row < rows; row += blockDim.x) {
+    const size_t c0 = (size_t)row * nx, c1 = c0 + nx - 1;
+    const uint8_t k = code[c0];
+    if ((k & CODE_SOLID) && !(k & CODE_WALL_XM)) s += T[c1] + dT - T[c0];
+  }
+  s = block_reduce(s, red);
+  if (threadIdx.x == 0) *out = s;
+}
+
 }  // namespace
 
 CGArgs make_cg_args(const GeomDev& g, double hx, double hy, double hz, int max_iter, double tol,
@@ -725,4 +743,10 @@ cudaError_t launch_fourier_cg(const GeomDev& g, double hx, double hy, double hz,
   if (blocks < 1) blocks = 1;
   void* args[] = {&a};
   return cudaLaunchCooperativeKernel(kern, blocks, threads, args, 0, st);
+}
+
+cudaError_t launch_fourier_hot_flux(const uint8_t* code, const double* T, int nx, int rows, double dT,
+                                   double* out, cudaStream_t st) {
+  fourier_hot_flux_kernel<<<1, 256, 0, st>>>(code, T, nx, rows, dT, out);
+  return cudaGetLastError();
 }

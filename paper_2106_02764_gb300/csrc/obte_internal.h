@@ -212,3 +212,6 @@ cudaError_t launch_fourier_cg(const GeomDev& g, double hx, double hy, double hz,
                               int max_iter, double tol, double* T_out, int* iters_out,
                               double* work, int blocks_max, cudaStream_t st);
 size_t fourier_work_doubles(int n_cells, int blocks_max);
+// sum over the hot-contact rows of (T_image + dT - T_cell), one block
+cudaError_t launch_fourier_hot_flux(const uint8_t* code, const double* T, int nx, int rows, double dT,
+                                   double* out, cudaStream_t st);
