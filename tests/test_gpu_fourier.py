@@ -10,7 +10,7 @@ pore-free closed form; and the Eucken-Maxwell limit over a porosity sweep
 import numpy as np
 import pytest
 
-from gpu_common import SMALL, golden, rect_2d, solid_vector, transposed
+from gpu_common import SMALL, golden, rect_2d, transposed
 from paper_2106_02764_gb300 import inputs as I
 
 pytestmark = pytest.mark.gpu
