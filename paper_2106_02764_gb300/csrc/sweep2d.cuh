@@ -153,7 +153,7 @@ __global__ void __launch_bounds__(32 * WarpCfg<T, G, RMAX>::WPB, WarpCfg<T, G, R
   constexpr int NST = WarpCfg<T, G, RMAX>::NST;
   __shared__ __align__(16) uint4 recbuf[WPB][NST][CH][32 * RMAX];
   __shared__ __align__(16) T scratch_all[WPB][32][G];
-  __shared__ T kcoef[WPB][2][G];  // |K_gx|, |K_gy| of the warp's group (rare path only)
+  __shared__ __align__(16) T kcoef[WPB][2][G];  // |K_gx|, |K_gy| of the warp's group (rare path only)
   // a step's T_L partials of every warp, by row (two step parities)
   __shared__ __align__(16) T tlbuf[2][WPB][32 * RMAX];
   const int lane = threadIdx.x & 31;
@@ -294,6 +294,25 @@ __global__ void __launch_bounds__(32 * WarpCfg<T, G, RMAX>::WPB, WarpCfg<T, G, R
       cp_async_commit();
     };
 
+    // sum_g K_g T_g of register row r (wall and hot-face fluxes): paired
+    // FP32 products in two chains
+    auto kdot = [&](const T* K, const VV* K2r, int r) -> T {
+      if constexpr (X2) {
+        const float2* K2 = K2r;
+        float2 a = make_float2(0.f, 0.f), b = a;
+#pragma unroll
+        for (int h = 0; h < GV; ++h) {
+          if (h & 1) b = __ffma2_rn(K2[h], v[r][h], b);
+          else a = __ffma2_rn(K2[h], v[r][h], a);
+        }
+        return (a.x + b.x) + (a.y + b.y);
+      } else {
+        T sk = T(0);
+#pragma unroll
+        for (int g = 0; g < G; ++g) sk = fma(K[g], VG(r, g), sk);
+        return sk;
+      }
+    };
     const int below = lane > 0 ? lane - 1 : (gm.py ? tpp - 1 : 0);
     const int out_x_side = sx > 0 ? 1 : 0, out_y_side = sy > 0 ? 3 : 2;
     double phi = 0.0;
@@ -421,6 +440,16 @@ __global__ void __launch_bounds__(32 * WarpCfg<T, G, RMAX>::WPB, WarpCfg<T, G, R
         if ((any & RARE) || rare_pass) {
           const T* KX = kcoef[wib][0];
           const T* KY = kcoef[wib][1];
+          // the coefficients once per step (a generic-address atomic between
+          // rows would otherwise force them to be reloaded)
+          VV KXr[GV], KYr[GV];
+          if constexpr (X2) {
+#pragma unroll
+            for (int h = 0; h < GV; ++h) {
+              KXr[h] = reinterpret_cast<const float2*>(KX)[h];
+              KYr[h] = reinterpret_cast<const float2*>(KY)[h];
+            }
+          }
 #pragma unroll
           for (int r = 0; r < RMAX; ++r) {
             if (!(RFIXED || r >= rb)) continue;
@@ -436,9 +465,7 @@ __global__ void __launch_bounds__(32 * WarpCfg<T, G, RMAX>::WPB, WarpCfg<T, G, R
               continue;
             }
             if (packed & (REC_WOUT_X | REC_LAST)) {
-              T sk = T(0);
-#pragma unroll
-              for (int g = 0; g < G; ++g) sk = fma(KX[g], VG(r, g), sk);
+              const T sk = kdot(KX, KXr, r);
               if (packed & REC_WOUT_X) {
                 atomicAdd(wacc + (size_t)cell * 6 + out_x_side, widen(sk));
               } else {
@@ -447,9 +474,7 @@ __global__ void __launch_bounds__(32 * WarpCfg<T, G, RMAX>::WPB, WarpCfg<T, G, R
               }
             }
             if (packed & REC_WOUT_Y) {
-              T sy_k = T(0);
-#pragma unroll
-              for (int g = 0; g < G; ++g) sy_k = fma(KY[g], VG(r, g), sy_k);
+              const T sy_k = kdot(KY, KYr, r);
               atomicAdd(wacc + (size_t)cell * 6 + out_y_side, widen(sy_k));
             }
           }
