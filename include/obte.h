@@ -82,7 +82,7 @@ typedef struct {
   int min_iter;         /* never stop before this many iterations              */
   int check_every;      /* iterations per CUDA-graph launch between host checks */
   int fourier_max_iter; /* CG iterations for the Fourier first guess (0: auto) */
-  double fourier_tol;   /* relative CG residual (0: auto)                      */
+  double fourier_tol;   /* relative CG residual (0: 1e-3)                      */
   int group_size;       /* ordinates per thread block (0: autotuned)           */
   int rows_per_thread;  /* mesh rows per thread (0: autotuned)                 */
   int use_graph;        /* 1: capture check_every iterations in a CUDA graph   */
