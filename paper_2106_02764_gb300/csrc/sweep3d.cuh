@@ -99,7 +99,7 @@ __global__ void __launch_bounds__(Sweep3DCfg<RMAX>::NT, 1) sweep3d_kernel(const 
   constexpr int NT = Sweep3DCfg<RMAX>::NT;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ double red[32];
-  __shared__ T kcoef[3][G];  // |K_gx|, |K_gy|, |K_gz| of the group (rare path only)
+  __shared__ __align__(16) T kcoef[3][G];  // |K_gx|, |K_gy|, |K_gz| of the group (rare path only)
   const int nthr = NT;
   const int t = threadIdx.x;
   T* scratch = reinterpret_cast<T*>(smem_raw) + 2 * RMAX * G * NT;  // [G][NT] after the exchange
@@ -206,6 +206,36 @@ __global__ void __launch_bounds__(Sweep3DCfg<RMAX>::NT, 1) sweep3d_kernel(const 
   }
   double phi = 0.0;
   int s = d0;
+  // Film walls beyond the last plane: every cell of plane nz - 1 leaves into
+  // the wall, every step.  Their wall fluxes are taken one step late from the
+  // published row values by ny helper threads (one row each) instead of by
+  // the tpp threads of that plane (R rows each), which would pace the step.
+  const bool defer_z = !rare_pass && !gm.pz && nz > 1;
+  const bool z_owner = defer_z && kp == nz - 1;
+  auto top_plane_walls = [&](int buf, int sd) {
+    const int jj = t;  // row of plane nz - 1
+    if (jj >= ny) return;
+    const int th = (nz - 1) * tpp + jj / RMAX, r = jj % RMAX;
+    const int row = jj + ny * (nz - 1);
+    const uint32_t packed = rec3_bits<T>(__ldg(recq + ((size_t)sd * rows + row) * 8 + 4));
+    if (!(packed & REC_SOLID) || !(packed & REC_WOUT_Z)) return;
+    T sk;
+    if constexpr (X2) {
+      const float2* K2 = reinterpret_cast<const float2*>(kcoef[2]);
+      float2 a = make_float2(0.f, 0.f), b = a;
+#pragma unroll
+      for (int h = 0; h < GV; ++h) {
+        if (h & 1) b = __ffma2_rn(K2[h], XP(buf, r, h, th), b);
+        else a = __ffma2_rn(K2[h], XP(buf, r, h, th), a);
+      }
+      sk = (a.x + b.x) + (a.y + b.y);
+    } else {
+      sk = T(0);
+#pragma unroll
+      for (int g = 0; g < G; ++g) sk = fma(kcoef[2][g], XP(buf, r, g, th), sk);
+    }
+    atomicAdd(wacc + (size_t)(packed & REC_CELL_MASK) * 6 + out_side_z, widen(sk));
+  };
 
   // records of the first step
   T rc[RMAX][5];
@@ -238,6 +268,7 @@ __global__ void __launch_bounds__(Sweep3DCfg<RMAX>::NT, 1) sweep3d_kernel(const 
     const int s_next = (s + 1 == nx) ? 0 : s + 1;
     T rn[RMAX][5];
     if (d + 1 < nx) load_recs(s_next, rn);
+    if (defer_z && d > 0) top_plane_walls(prv, s == 0 ? nx - 1 : s - 1);
     if (active) {
       VV dny[GV];
 #pragma unroll
@@ -315,7 +346,7 @@ __global__ void __launch_bounds__(Sweep3DCfg<RMAX>::NT, 1) sweep3d_kernel(const 
 #pragma unroll
       for (int r = 0; r < RMAX; ++r) {
         const bool rare =
-            rare_pass || (pk[r] & (REC_WOUT_X | REC_WOUT_Y | REC_WOUT_Z | REC_LAST));
+            rare_pass || (pk[r] & (REC_WOUT_X | REC_WOUT_Y | (z_owner ? 0u : (uint32_t)REC_WOUT_Z) | REC_LAST));
         rare_mask |= (((pk[r] & REC_SOLID) && rare) ? 1u : 0u) << r;
       }
       // cells leaving into a wall, the hot-contact column, flux / record passes
@@ -347,7 +378,7 @@ __global__ void __launch_bounds__(Sweep3DCfg<RMAX>::NT, 1) sweep3d_kernel(const 
             for (int g = 0; g < G; ++g) sk = fma(kcoef[1][g], VG(r, g), sk);
             atomicAdd(wacc + (size_t)cell * 6 + out_side_y, widen(sk));
           }
-          if (packed & REC_WOUT_Z) {
+          if ((packed & REC_WOUT_Z) && !z_owner) {
             T sk = T(0);
 #pragma unroll
             for (int g = 0; g < G; ++g) sk = fma(kcoef[2][g], VG(r, g), sk);
@@ -373,6 +404,9 @@ __global__ void __launch_bounds__(Sweep3DCfg<RMAX>::NT, 1) sweep3d_kernel(const 
     __syncthreads();
   }
 
+  // the last step's plane nz - 1 (its values were published before the
+  // loop's final barrier; s is one past the last diagonal)
+  if (defer_z) top_plane_walls((nx - 1) & 1, s == 0 ? nx - 1 : s - 1);
   T* frontw = reinterpret_cast<T*>(gm.front);
 #pragma unroll
   for (int r = 0; r < RMAX; ++r)
