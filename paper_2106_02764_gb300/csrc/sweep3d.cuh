@@ -205,6 +205,10 @@ __global__ void __launch_bounds__(Sweep3DCfg<RMAX>::NT, 1) sweep3d_kernel(const 
     else if (gm.pz) tz = (nz - 1) * tpp + jb;
   }
   double phi = 0.0;
+  // hot-face flux of the thread's rows, in the sweep precision (each row
+  // crosses the hot column once per sweep), widened once at the end
+  T hot_sum = T(0);
+  int n_hot = 0;
   int s = d0;
   // Film walls beyond the last plane: every cell of plane nz - 1 leaves into
   // the wall, every step.  Their wall fluxes are taken one step late from the
@@ -237,6 +241,25 @@ __global__ void __launch_bounds__(Sweep3DCfg<RMAX>::NT, 1) sweep3d_kernel(const 
     atomicAdd(wacc + (size_t)(packed & REC_CELL_MASK) * 6 + out_side_z, widen(sk));
   };
 
+  // sum_g K_g T_g of register row r (wall and hot-face fluxes): paired FP32
+  // products in two chains
+  auto kdot = [&](const T* K, int r) -> T {
+    if constexpr (X2) {
+      const float2* K2 = reinterpret_cast<const float2*>(K);
+      float2 a = make_float2(0.f, 0.f), b = a;
+#pragma unroll
+      for (int h = 0; h < GV; ++h) {
+        if (h & 1) b = __ffma2_rn(K2[h], v[r][h], b);
+        else a = __ffma2_rn(K2[h], v[r][h], a);
+      }
+      return (a.x + b.x) + (a.y + b.y);
+    } else {
+      T sk = T(0);
+#pragma unroll
+      for (int g = 0; g < G; ++g) sk = fma(K[g], VG(r, g), sk);
+      return sk;
+    }
+  };
   // records of the first step
   T rc[RMAX][5];
   auto load_recs = [&](int sd, T (&dst)[RMAX][5]) {
@@ -365,23 +388,20 @@ __global__ void __launch_bounds__(Sweep3DCfg<RMAX>::NT, 1) sweep3d_kernel(const 
             continue;
           }
           if (packed & (REC_WOUT_X | REC_LAST)) {
-            T sk = T(0);
-#pragma unroll
-            for (int g = 0; g < G; ++g) sk = fma(kcoef[0][g], VG(r, g), sk);
-            const double dk = widen(sk);
-            if (packed & REC_WOUT_X) atomicAdd(wacc + (size_t)cell * 6 + out_side_x, dk);
-            else phi += (sx > 0 ? dk : -dk) + (sx > 0 ? dT * kx_sum : 0.0);
+            const T sk = kdot(kcoef[0], r);
+            if (packed & REC_WOUT_X) {
+              atomicAdd(wacc + (size_t)cell * 6 + out_side_x, widen(sk));
+            } else {
+              hot_sum += sk;
+              ++n_hot;
+            }
           }
           if (packed & REC_WOUT_Y) {
-            T sk = T(0);
-#pragma unroll
-            for (int g = 0; g < G; ++g) sk = fma(kcoef[1][g], VG(r, g), sk);
+            const T sk = kdot(kcoef[1], r);
             atomicAdd(wacc + (size_t)cell * 6 + out_side_y, widen(sk));
           }
           if ((packed & REC_WOUT_Z) && !z_owner) {
-            T sk = T(0);
-#pragma unroll
-            for (int g = 0; g < G; ++g) sk = fma(kcoef[2][g], VG(r, g), sk);
+            const T sk = kdot(kcoef[2], r);
             atomicAdd(wacc + (size_t)cell * 6 + out_side_z, widen(sk));
           }
         }
@@ -407,6 +427,11 @@ __global__ void __launch_bounds__(Sweep3DCfg<RMAX>::NT, 1) sweep3d_kernel(const 
   // the last step's plane nz - 1 (its values were published before the
   // loop's final barrier; s is one past the last diagonal)
   if (defer_z) top_plane_walls((nx - 1) & 1, s == 0 ? nx - 1 : s - 1);
+  {
+    const double dk = widen(hot_sum);
+    phi += sx > 0 ? dk : -dk;
+    if (sx > 0) phi += (double)n_hot * dT * kx_sum;
+  }
   T* frontw = reinterpret_cast<T*>(gm.front);
 #pragma unroll
   for (int r = 0; r < RMAX; ++r)
