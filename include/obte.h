@@ -150,6 +150,33 @@ int obte_create_mesh(obte_ctx* ctx, int dim, int nx, int ny, int nz, double lx, 
 int obte_set_material(obte_ctx* ctx, int n_mfp, const double* kappa_m, const double* lambda_m,
                       int n_dir, const double* dirs, const double* w, int angular_dim);
 
+/* General aMFP material (Sec. 5: the Material module turns mode data into
+ * per-ordinate quantities; App. A: F_ml = Lambda_m s_l with the weights D_ml
+ * and S_ml interpolated from the modes).  Every ordinate o carries its own
+ * vectorial MFP and weight, so MFPs may depend on direction (anisotropic
+ * materials) and weights need not factor into bin x direction.
+ *  lambda   host double[n_ord]: Lambda_o (m) > 0
+ *  dirs     host double[n_ord][3]: s_o (in 2D only x, y are used; projected
+ *           directions may have |s| < 1)
+ *  weight   host double[n_ord]: W_o >= 0, the C/tau of the modes the ordinate
+ *           stands for (any common scale), not all zero
+ *  bin      host int[n_ord] in [0, n_bins) or NULL (one bin): the MFP bin of
+ *           each ordinate, for obte_get_kappa_bins and the adjoint's pairing
+ * Lattice-temperature weights a_o = W_o / sum W (E2); flux weights K_o =
+ * W_o Lambda_o s_o, the form for which every ordinate's transport conserves
+ * energy (sum_o K_o . grad T_o = -sum_o W_o (T_o - T_L) = 0).  The
+ * bin-separable obte_set_material is the case W_o = d_ang (kappa_m /
+ * Lambda_m^2) w_s.  Bulk conductivity along axis a: sum_o W_o Lambda_o^2
+ * s_oa^2 (the first guess and obte_solve_fourier use these as an axis-aligned
+ * tensor).  The set must be mirror-symmetric like obte_set_material's
+ * (OBTE_EINVAL otherwise); obte_kappa_grad_s also needs for every ordinate a
+ * reversed one (same bin, Lambda and weight, opposite direction).
+ * OBTE_ENONFINITE for non-finite input; OBTE_EINVAL for lambda <= 0, a
+ * negative weight, an all-zero weight vector, a bin out of range, or no
+ * ordinate moving along the gradient axis. */
+int obte_set_material_ordinates(obte_ctx* ctx, int n_ord, const double* lambda, const double* dirs,
+                                const double* weight, const int* bin, int n_bins);
+
 /* Per-cell scattering scale s_i > 0 multiplying the collision term of every
  * ordinate in cell i (not in the paper; used for sensitivities).
  * s: host double[nz][ny][nx] or NULL (all ones). */
@@ -215,8 +242,9 @@ int obte_kappa_grad_s_noalloc(obte_ctx* ctx, double* out);
 int obte_get_kappa_bins(obte_ctx* ctx, double* out);
 
 /* Fourier model alone (App. B; the paper's Fourier-only run): heat
- * conduction with the bulk conductivity kappa_bulk = sum_m kappa_m in the
- * solid cells, adiabatic pore and film walls, and the applied jump dT across
+ * conduction with the bulk conductivity (kappa_bulk = sum_m kappa_m for
+ * obte_set_material, the axis-aligned tensor of obte_set_material_ordinates)
+ * in the solid cells, adiabatic pore and film walls, and the applied jump dT across
  * the gradient period, solved by FP64 conjugate gradients on the device (the
  * solver's first guess run to a tight tolerance).  Needs create_mesh and
  * set_material; leaves the transport solve's state untouched.

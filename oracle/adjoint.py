@@ -118,10 +118,11 @@ def kappa_grad_s(prob: bte.Problem, sol: bte.Solution = None, tr=None, rtol=1e-1
 
 
 def reversed_ordinate(ords: bte.Ordinates):
-    """Index of the ordinate with the same MFP and the opposite direction."""
+    """Index of the ordinate with the same MFP bin and MFP and the opposite
+    direction."""
     rev = np.empty(ords.n, dtype=np.int64)
     for o in range(ords.n):
-        cand = np.nonzero((ords.m_of == ords.m_of[o]) &
+        cand = np.nonzero((ords.m_of == ords.m_of[o]) & (ords.lam == ords.lam[o]) &
                           np.all(np.abs(ords.p + ords.p[o]) < 1e-12, axis=1))[0]
         if len(cand) != 1:
             raise ValueError("quadrature is not symmetric under p -> -p")
@@ -136,8 +137,9 @@ def adjoint_jump(prob: bte.Problem):
     me, od = prob.mesh, prob.ords
     g = me.grad_axis
     scale = me.lengths[g] / (me.delta_T * me.n_sec)
-    # recover d_ang and sum kappa/Lambda^2 from the ordinate table:
-    # K_o / (a_o Lambda_o p_o) = d_ang * sum_m kappa_m / Lambda_m^2 for every o
+    # recover the total weight from the ordinate table: K_o / (a_o Lambda_o p_o)
+    # = sum_o W_o for every o (d_ang sum_m kappa_m / Lambda_m^2 for the
+    # bin x direction material)
     o = int(np.argmax(np.abs(od.p[:, g])))
     ratio = od.K[o, g] / (od.a[o] * od.lam[o] * od.p[o, g])
     return -scale * ratio * me.h[g]

@@ -19,7 +19,9 @@ What is computed (the discrete system, App. A of the paper):
   (E2)  T_Li = sum_o a_o T_oi with a_o = abar_m w_s,
         abar_m = (kappa_m / Lambda_m^2) / sum_m' (kappa_m' / Lambda_m'^2)
         (lattice temperature from energy conservation, Sec. 2; C/tau per bin
-        is proportional to kappa_m / Lambda_m^2 for a gray bin).
+        is proportional to kappa_m / Lambda_m^2 for a gray bin).  A general
+        per-ordinate material (Ordinates.from_ordinates) gives each ordinate
+        its own Lambda_o and weight W_o: a_o = W_o / sum W, K_o = W_o F_o.
   (E3)  T_wf = sum_{o: K_o.n_f > 0} (K_o.n_f) T_o,i(f) / sum_{o: K_o.n_f > 0} K_o.n_f
         with K_o = d_ang kappa_m w_s p_s / Lambda_m the flux weight
         (thermalising wall, R_mu_nu of Sec. 2; S_ml of App. A).
@@ -162,8 +164,40 @@ class Ordinates:
         self.a = np.repeat(abar, S) * self.w
         self.K = angular_dim * (km * self.w / self.lam)[:, None] * self.p
         self.kappa_bulk = float(kappa_m.sum())
+        # bulk conductivity along each axis (isotropic for these sets)
+        self.kappa_axes = np.full(3, self.kappa_bulk)
         self.m_of = np.repeat(np.arange(M), S)
         self.s_of = np.tile(np.arange(S), M)
+
+    @classmethod
+    def from_ordinates(cls, lam, dirs, weight, bins, dim):
+        """General aMFP material (Sec. 5, App. A): ordinate o carries its own
+        vectorial MFP F_o = Lambda_o s_o and a weight W_o >= 0 standing for the
+        C/tau of the modes interpolated onto it (D_ml of App. A before
+        normalisation).  Then a_o = W_o / sum W (E2) and K_o = W_o Lambda_o s_o
+        (S_ml of App. A, in the form for which sum_o K_o . grad T_o =
+        -sum_o W_o (T_o - T_L) = 0 holds for the transport of every ordinate,
+        i.e. energy is conserved).  The bin-separable set above is the case
+        W_o = d_ang (kappa_m / Lambda_m^2) w_s."""
+        self = cls.__new__(cls)
+        lam = np.asarray(lam, float)
+        W = np.asarray(weight, float)
+        bins = np.asarray(bins, np.int64)
+        n = len(lam)
+        p = np.zeros((n, 3))
+        p[:, :dim] = np.asarray(dirs, float).reshape(n, 3)[:, :dim]
+        self.n, self.M, self.S = n, int(bins.max()) + 1, None
+        self.lam, self.p = lam, p
+        self.w = W / W.sum()
+        self.a = W / W.sum()
+        self.K = (W * lam)[:, None] * p
+        # kappa_aa = sum_o K_oa Lambda_o p_oa: the response of the flux to a
+        # uniform gradient along a (diagonal of the bulk tensor)
+        self.kappa_axes = np.array([float((self.K[:, a] * lam * p[:, a]).sum()) for a in range(3)])
+        self.kappa_bulk = float(self.kappa_axes[0])
+        self.m_of = bins
+        self.s_of = np.arange(n)
+        return self
 
 
 @dataclasses.dataclass
@@ -175,8 +209,12 @@ class Problem:
     @classmethod
     def from_workload(cls, wl, s=None):
         mesh = Mesh(wl.mask, wl.lengths, wl.periodic, wl.delta_T, wl.dim, wl.grad_axis)
-        ords = Ordinates(wl.kappa_m, wl.lambda_m, wl.quad.dirs, wl.quad.weights,
-                         wl.quad.angular_dim, wl.dim)
+        if getattr(wl, "ords", None) is not None:
+            o = wl.ords
+            ords = Ordinates.from_ordinates(o["lambda"], o["dirs"], o["weight"], o["bin"], wl.dim)
+        else:
+            ords = Ordinates(wl.kappa_m, wl.lambda_m, wl.quad.dirs, wl.quad.weights,
+                             wl.quad.angular_dim, wl.dim)
         field = s if s is not None else wl.s
         if field is None:
             sv = np.ones(mesh.nc)
@@ -322,7 +360,7 @@ def initial_guess(tr: Transport, T_F=None):
     from .fourier import solve_fourier
     me = tr.prob.mesh
     if T_F is None:
-        T_F = solve_fourier(me, tr.prob.ords.kappa_bulk)["T"]
+        T_F = solve_fourier(me, tr.prob.ords.kappa_axes)["T"]
     T_w = T_F[me.walls[:, 0]] if me.nw else np.zeros(0)
     return T_F.copy(), T_w.copy()
 
@@ -415,10 +453,11 @@ def heat_flux(prob: Problem, Ts: dict):
 def kappa_bulk_discrete(prob: Problem):
     """Pore-free closed form of the upwind scheme: the exact discrete solution
     is T_o = T_L - Lambda_m p_x a (linear T_L of slope a = -dT/L_x), whose
-    upwinded face flux gives kappa_bulk + (h_x / 2) sum_o |K_ox|."""
+    upwinded face flux gives kappa_bulk + (h_x / 2) sum_o |K_ox| (kappa_bulk:
+    the bulk tensor's entry along the gradient axis)."""
     me, od = prob.mesh, prob.ords
     g = me.grad_axis
-    return od.kappa_bulk + 0.5 * me.h[g] * np.abs(od.K[:, g]).sum()
+    return od.kappa_axes[g] + 0.5 * me.h[g] * np.abs(od.K[:, g]).sum()
 
 
 def to_grid(prob: Problem, v, fill=np.nan):

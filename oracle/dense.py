@@ -16,7 +16,10 @@ import numpy as np
 
 
 def dense_solve(mask, lengths, periodic, delta_T, dim, kappa_m, lambda_m, dirs,
-                weights, angular_dim, s=None, grad_axis=0, transpose_rhs=None):
+                weights, angular_dim, s=None, grad_axis=0, transpose_rhs=None, ordinates=None):
+    """``ordinates``: a general per-ordinate material {lambda, dirs, weight}
+    (Sec. 5) replacing the bin x direction one; a_o = W_o / sum W and
+    K_o = W_o Lambda_o s_o."""
     mask = np.asarray(mask).astype(bool)
     if mask.ndim == 2:
         mask = mask[None]
@@ -27,21 +30,30 @@ def dense_solve(mask, lengths, periodic, delta_T, dim, kappa_m, lambda_m, dirs,
     cells = [(x, y, z) for z in range(nz) for y in range(ny) for x in range(nx) if mask[z, y, x]]
     cid = {c: i for i, c in enumerate(cells)}
     nc = len(cells)
-    M, S = len(kappa_m), len(weights)
-    O = M * S
     sc = np.ones(nc) if s is None else np.array(
         [np.asarray(s).reshape(mask.shape)[z, y, x] for (x, y, z) in cells])
 
-    # ordinate data, o = m * S + s
     lam, pv, aw, Kv = [], [], [], []
-    tot = sum(kappa_m[m] / lambda_m[m] ** 2 for m in range(M))
-    for m in range(M):
-        for q in range(S):
-            p = [dirs[q][a] if a < dim else 0.0 for a in range(3)]
-            lam.append(lambda_m[m])
+    if ordinates is None:
+        # ordinate data, o = m * S + s
+        M, S = len(kappa_m), len(weights)
+        tot = sum(kappa_m[m] / lambda_m[m] ** 2 for m in range(M))
+        for m in range(M):
+            for q in range(S):
+                p = [dirs[q][a] if a < dim else 0.0 for a in range(3)]
+                lam.append(lambda_m[m])
+                pv.append(p)
+                aw.append(kappa_m[m] / lambda_m[m] ** 2 / tot * weights[q])
+                Kv.append([angular_dim * kappa_m[m] * weights[q] * p[a] / lambda_m[m] for a in range(3)])
+    else:
+        Wtot = float(sum(ordinates["weight"]))
+        for lo, do, wo in zip(ordinates["lambda"], ordinates["dirs"], ordinates["weight"]):
+            p = [float(do[a]) if a < dim else 0.0 for a in range(3)]
+            lam.append(float(lo))
             pv.append(p)
-            aw.append(kappa_m[m] / lambda_m[m] ** 2 / tot * weights[q])
-            Kv.append([angular_dim * kappa_m[m] * weights[q] * p[a] / lambda_m[m] for a in range(3)])
+            aw.append(float(wo) / Wtot)
+            Kv.append([float(wo) * float(lo) * p[a] for a in range(3)])
+    O = len(lam)
 
     def neighbour(c, a, sgn):
         """(solid neighbour or None, jump, is_wall)."""
@@ -155,4 +167,4 @@ def dense_from_workload(wl, s=None, **kw):
     return dense_solve(wl.mask, wl.lengths, wl.periodic, wl.delta_T, wl.dim,
                        list(wl.kappa_m), list(wl.lambda_m), [list(d) for d in q.dirs],
                        list(q.weights), q.angular_dim, s=s if s is not None else wl.s,
-                       grad_axis=wl.grad_axis, **kw)
+                       grad_axis=wl.grad_axis, ordinates=getattr(wl, "ords", None), **kw)

@@ -16,7 +16,8 @@ The solution is fixed to solid-cell mean 0 by a bordered system.
 
 kappa_fourier = -(L / (dT A)) sum_{hot-contact faces} g . S (App. B, last
 equation), i.e. the conductive flux through the solid faces of the plane
-x = 0 divided by the full cross-section.
+x = 0 divided by the full cross-section.  An anisotropic material enters as
+the diagonal of its bulk tensor (axis-aligned: kappa_a / h_a^2 per axis).
 """
 from __future__ import annotations
 
@@ -25,13 +26,20 @@ import scipy.sparse as sp
 import scipy.sparse.linalg as spla
 
 
+def _axes(kappa_bulk):
+    """kappa along each axis: a scalar (isotropic) or three diagonal entries."""
+    return np.broadcast_to(np.asarray(kappa_bulk, float), (3,))
+
+
 def assemble(mesh, kappa_bulk):
-    """Primary-flux stiffness (negative semidefinite) and jump right-hand side."""
+    """Primary-flux stiffness (negative semidefinite) and jump right-hand side.
+    kappa_bulk: scalar or the diagonal of an axis-aligned bulk tensor."""
+    kap = _axes(kappa_bulk)
     rows, cols, vals = [], [], []
     rhs = np.zeros(mesh.nc)
     diag = np.zeros(mesh.nc)
     for a in mesh.axes:
-        G = kappa_bulk / mesh.h[a] ** 2
+        G = kap[a] / mesh.h[a] ** 2
         for side in (0, 1):
             j = mesh.nbr[:, a, side]
             ok = j >= 0
@@ -66,5 +74,5 @@ def kappa_fourier(mesh, kappa_bulk, T):
     g = mesh.grad_axis
     cells, img = mesh.hot_faces()
     jump = mesh.jump[cells, g, 0]
-    flux = kappa_bulk * (T[img] + jump - T[cells]) / mesh.h[g]
+    flux = _axes(kappa_bulk)[g] * (T[img] + jump - T[cells]) / mesh.h[g]
     return mesh.lengths[g] / (mesh.delta_T * mesh.n_sec) * flux.sum()

@@ -68,6 +68,8 @@ SIGNATURES = [
                                    C.c_int, C.c_double]),
     ("obte_set_material", C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_int,
                                     C.c_void_p, C.c_void_p, C.c_int]),
+    ("obte_set_material_ordinates", C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p,
+                                              C.c_void_p, C.c_void_p, C.c_int]),
     ("obte_set_scattering_scale", C.c_int, [C.c_void_p, C.c_void_p]),
     ("obte_solve", C.c_int, [C.c_void_p, C.POINTER(SolveOpts), C.POINTER(SolveStats)]),
     ("obte_solve_batch", C.c_int, [C.POINTER(C.c_void_p), C.c_int, C.POINTER(SolveOpts),
@@ -206,6 +208,22 @@ class Solver:
         self.n_mfp = len(k)
         return self
 
+    def set_material_ordinates(self, lam, dirs, weight, bins=None, n_bins=None):
+        """General aMFP material: per-ordinate MFP, direction and weight
+        (C/tau of the modes it stands for), optional MFP bin per ordinate."""
+        l, w = _f64(lam), _f64(weight)
+        d = _f64(dirs).reshape(-1, 3)
+        if bins is None:
+            bp, nb = None, 1
+        else:
+            b = np.ascontiguousarray(np.asarray(bins, dtype=np.int32))
+            nb = int(n_bins if n_bins is not None else b.max() + 1)
+            bp = b.ctypes.data_as(C.c_void_p)
+        self._check(self.lib.obte_set_material_ordinates(self.ctx, len(l), _ptr(l), _ptr(d), _ptr(w),
+                                                         bp, nb))
+        self.n_mfp = nb
+        return self
+
     def set_scattering_scale(self, s):
         if s is None:
             self._check(self.lib.obte_set_scattering_scale(self.ctx, None))
@@ -218,7 +236,11 @@ class Solver:
     def from_workload(cls, wl, device=0, stream=None):
         s = cls(device, stream)
         s.create_mesh(wl.mask, wl.lengths, wl.periodic, wl.grad_axis, wl.delta_T, wl.dim)
-        s.set_material(wl.kappa_m, wl.lambda_m, wl.quad.dirs, wl.quad.weights, wl.quad.angular_dim)
+        if getattr(wl, "ords", None) is not None:
+            o = wl.ords
+            s.set_material_ordinates(o["lambda"], o["dirs"], o["weight"], o["bin"])
+        else:
+            s.set_material(wl.kappa_m, wl.lambda_m, wl.quad.dirs, wl.quad.weights, wl.quad.angular_dim)
         if wl.s is not None:
             s.set_scattering_scale(wl.s)
         return s

@@ -64,6 +64,9 @@ struct obte_ctx {
   int* octant_d = nullptr;
   int* ord_d0_d = nullptr;
   double kappa_scale = 0.0, sum_k_over_l2 = 0.0;
+  double w_total = 0.0;                           // sum of the E2 weights before normalisation
+  double kappa_axes[3] = {0, 0, 0};               // bulk conductivity along each kernel axis
+  std::vector<double> lam_o;                      // Lambda per sorted ordinate
 
   // solve state
   int precision = -1;
@@ -433,6 +436,132 @@ extern "C" int obte_set_scattering_scale(obte_ctx* ctx, const double* s) {
 // ---------------------------------------------------------------------------
 enum { TB_BX, TB_BY, TB_BZ, TB_DIAG, TB_INV, TB_AW, TB_KXA, TB_KYA, TB_KZA };
 
+static int upload_material(obte_ctx* ctx);
+
+// One ordinate of the material as the table builder takes it (kernel frame).
+struct OrdIn {
+  int bin;       // MFP bin (per-bin kappa spectrum, reversed-ordinate pairing)
+  double lam;    // Lambda_o
+  double p[3];   // direction (unit, or projected onto the plane)
+  double aw;     // E2 weight a_o (sums to 1)
+  double kf;     // flux weight K_o = kf p
+};
+
+// Sorted ordinate table, per-ordinate coefficients and device copies.
+// Ordinates go by octant, octants in reversed pairs (q, q^full); inside an
+// octant in input order, and the reversed octant's list is reordered so that
+// its k-th ordinate reverses the k-th of q (same bin, Lambda and a_o,
+// opposite direction) when every ordinate has such a partner.
+static int build_material(obte_ctx* ctx, const std::vector<OrdIn>& in, int n_bins, double w_total,
+                          const double kappa_axes[3]) {
+  const int dim = ctx->dim;
+  const int n = (int)in.size();
+  auto oct_of = [&](int o) {
+    int q = 0;
+    if (in[o].p[0] < 0) q |= 1;
+    if (in[o].p[1] < 0) q |= 2;
+    if (dim == 3 && in[o].p[2] < 0) q |= 4;
+    return q;
+  };
+  const int full = dim == 3 ? 7 : 3;
+  std::vector<int> oct_order;
+  for (int q = 0; q <= full; ++q) {
+    const int qb = q ^ full;
+    if (q < qb) {
+      oct_order.push_back(q);
+      oct_order.push_back(qb);
+    }
+  }
+  std::vector<std::vector<int>> in_oct(8);
+  for (int o = 0; o < n; ++o) in_oct[oct_of(o)].push_back(o);
+  auto reverses = [&](int t, int o) {
+    if (in[t].bin != in[o].bin) return false;
+    for (int a = 0; a < 3; ++a)
+      if (std::fabs(in[t].p[a] + in[o].p[a]) > 1e-12) return false;
+    if (std::fabs(in[t].lam - in[o].lam) > 1e-12 * in[o].lam) return false;
+    return std::fabs(in[t].aw - in[o].aw) <= 1e-300 + 1e-12 * in[o].aw;
+  };
+  for (int i = 0; i + 1 < (int)oct_order.size(); i += 2) {
+    const int q = oct_order[i], qb = oct_order[i + 1];
+    if (in_oct[q].size() != in_oct[qb].size()) continue;
+    std::map<int, std::vector<int>> by_bin;  // candidates of the reversed octant, by bin
+    for (int t : in_oct[qb]) by_bin[in[t].bin].push_back(t);
+    std::vector<int> rv;
+    std::vector<char> used(n, 0);
+    bool ok = true;
+    for (int o : in_oct[q]) {
+      int r = -1;
+      for (int t : by_bin[in[o].bin])
+        if (!used[t] && reverses(t, o)) {
+          r = t;
+          break;
+        }
+      if (r < 0) {
+        ok = false;
+        break;
+      }
+      used[r] = 1;
+      rv.push_back(r);
+    }
+    if (ok) in_oct[qb] = rv;  // paired order
+  }
+  std::vector<int> order;
+  ctx->octant.clear();
+  for (int q : oct_order)
+    for (int o : in_oct[q]) {
+      order.push_back(o);
+      ctx->octant.push_back(q);
+    }
+  const int O = n;
+  ctx->O = O;
+  ctx->M = n_bins;
+  ctx->w_total = w_total;
+  for (int a = 0; a < 3; ++a) ctx->kappa_axes[a] = kappa_axes[a];
+  ctx->ord_m.assign(O, 0);
+  ctx->ord_s.assign(O, 0);
+  ctx->lam_o.assign(O, 0.0);
+  for (auto* v : {&ctx->bx, &ctx->by, &ctx->bz, &ctx->diag, &ctx->inv, &ctx->aw, &ctx->kxa,
+                  &ctx->kya, &ctx->kza})
+    v->assign(O, 0.0);
+  for (int a = 0; a < 3; ++a) ctx->pk[a].assign(O, 0.0);
+  double den_side[6] = {0, 0, 0, 0, 0, 0};
+  for (int o = 0; o < O; ++o) {
+    const OrdIn& d = in[order[o]];
+    ctx->ord_m[o] = d.bin;
+    ctx->ord_s[o] = order[o];
+    ctx->lam_o[o] = d.lam;
+    for (int a = 0; a < 3; ++a) ctx->pk[a][o] = d.p[a];
+    double beta[3] = {0, 0, 0};
+    for (int a = 0; a < dim; ++a) beta[a] = d.lam * std::fabs(d.p[a]) / ctx->h[a];
+    const double D = beta[0] + beta[1] + beta[2];
+    ctx->bx[o] = beta[0];
+    ctx->by[o] = beta[1];
+    ctx->bz[o] = beta[2];
+    ctx->diag[o] = D;
+    ctx->inv[o] = 1.0 / (1.0 + D);
+    ctx->aw[o] = d.aw;
+    ctx->kxa[o] = d.kf * std::fabs(d.p[0]);
+    ctx->kya[o] = d.kf * std::fabs(d.p[1]);
+    ctx->kza[o] = dim == 3 ? d.kf * std::fabs(d.p[2]) : 0.0;
+    for (int a = 0; a < dim; ++a) {
+      const double k = d.kf * d.p[a];
+      if (k > 0) den_side[2 * a + 1] += k;   // leaves through the + face
+      if (k < 0) den_side[2 * a] += -k;      // leaves through the - face
+    }
+  }
+  for (int a = 0; a < dim; ++a) {
+    const double s0 = den_side[2 * a], s1 = den_side[2 * a + 1];
+    if (std::fabs(s0 - s1) > 1e-10 * std::max(s0, s1))
+      return ctx->fail(OBTE_EINVAL, "direction set is not mirror-symmetric: walls would not conserve energy");
+  }
+  ctx->wall_den_h.assign(std::max(1, ctx->n_walls), 1.0);
+  for (int f = 0; f < ctx->n_walls; ++f) {
+    const double d = den_side[ctx->wall_side_h[f]];
+    ctx->wall_den_h[f] = d > 0 ? d : 1.0;
+  }
+  return OBTE_OK;
+}
+
 extern "C" int obte_set_material(obte_ctx* ctx, int n_mfp, const double* kappa_m,
                                  const double* lambda_m, int n_dir, const double* dirs,
                                  const double* w, int angular_dim) {
@@ -457,116 +586,83 @@ extern "C" int obte_set_material(obte_ctx* ctx, int n_mfp, const double* kappa_m
   double sk = 0;
   for (int m = 0; m < n_mfp; ++m) sk += kappa_m[m] / (lambda_m[m] * lambda_m[m]);
   if (!(sk > 0)) return ctx->fail(OBTE_EINVAL, "sum kappa_m / lambda_m^2 must be positive");
+  if ((long)n_mfp * n_dir > (1L << 30)) return ctx->fail(OBTE_EINVAL, "too many ordinates");
 
-  const int dim = ctx->dim;
-  ctx->M = n_mfp;
   ctx->S = n_dir;
-  ctx->O = n_mfp * n_dir;
   ctx->d_ang = angular_dim;
   ctx->kappa_m.assign(kappa_m, kappa_m + n_mfp);
   ctx->lambda_m.assign(lambda_m, lambda_m + n_mfp);
   ctx->sum_k_over_l2 = sk;
+  // ordinate (m, s), m-major: Lambda_m s_s with a_o = w_s (kappa_m / Lambda_m^2)
+  // / sum (kappa / Lambda^2) (E2) and K_o = d_ang kappa_m w_s s_s / Lambda_m
+  std::vector<OrdIn> in((size_t)n_mfp * n_dir);
+  for (int m = 0; m < n_mfp; ++m)
+    for (int s = 0; s < n_dir; ++s) {
+      OrdIn& d = in[(size_t)m * n_dir + s];
+      // kernel-frame direction (2D: user z dropped before the permutation)
+      const double u[3] = {dirs[3 * s], dirs[3 * s + 1], ctx->dim == 3 ? dirs[3 * s + 2] : 0.0};
+      for (int i = 0; i < 3; ++i) d.p[i] = u[ctx->perm[i]];
+      const double lam = lambda_m[m];
+      d.bin = m;
+      d.lam = lam;
+      d.aw = w[s] * (kappa_m[m] / (lam * lam)) / sk;
+      d.kf = angular_dim * kappa_m[m] * w[s] / lam;
+    }
+  double kb = 0.0;
+  for (int m = 0; m < n_mfp; ++m) kb += kappa_m[m];
+  const double kax[3] = {kb, kb, kb};  // isotropic: d_ang sum_s w_s p p^T = I
+  const int rc = build_material(ctx, in, n_mfp, angular_dim * sk, kax);
+  if (rc) return rc;
+  return upload_material(ctx);
+}
 
-  // kernel-frame directions (2D: user z dropped before the permutation)
-  std::vector<double> pdir((size_t)n_dir * 3);
-  for (int s = 0; s < n_dir; ++s) {
-    double u[3] = {dirs[3 * s], dirs[3 * s + 1], dim == 3 ? dirs[3 * s + 2] : 0.0};
-    for (int i = 0; i < 3; ++i) pdir[3 * s + i] = u[ctx->perm[i]];
+// General aMFP material: per-ordinate vectorial MFP and weight (Sec. 5, App. A)
+extern "C" int obte_set_material_ordinates(obte_ctx* ctx, int n_ord, const double* lambda,
+                                           const double* dirs, const double* weight, const int* bin,
+                                           int n_bins) {
+  if (!ctx) return OBTE_EINVAL;
+  if (!ctx->has_mesh) return ctx->fail(OBTE_ESTATE, "create_mesh first");
+  if (n_ord < 1 || !lambda || !dirs || !weight) return ctx->fail(OBTE_EINVAL, "empty material");
+  if (bin && n_bins < 1) return ctx->fail(OBTE_EINVAL, "n_bins must be >= 1");
+  if (!bin) n_bins = 1;
+  double W = 0.0;
+  for (int o = 0; o < n_ord; ++o) {
+    if (!std::isfinite(lambda[o]) || !std::isfinite(weight[o]))
+      return ctx->fail(OBTE_ENONFINITE, "material is not finite");
+    for (int a = 0; a < 3; ++a)
+      if (!std::isfinite(dirs[3 * o + a])) return ctx->fail(OBTE_ENONFINITE, "directions not finite");
+    if (!(lambda[o] > 0) || weight[o] < 0) return ctx->fail(OBTE_EINVAL, "need lambda > 0, weight >= 0");
+    if (bin && (bin[o] < 0 || bin[o] >= n_bins)) return ctx->fail(OBTE_EINVAL, "bin out of range");
+    W += weight[o];
   }
-  // octant of a direction; ordering puts reversed octants next to each other
-  auto oct_of = [&](int s) {
-    int q = 0;
-    if (pdir[3 * s] < 0) q |= 1;
-    if (pdir[3 * s + 1] < 0) q |= 2;
-    if (dim == 3 && pdir[3 * s + 2] < 0) q |= 4;
-    return q;
-  };
-  const int full = dim == 3 ? 7 : 3;
-  std::vector<int> oct_order;
-  for (int q = 0; q <= full; ++q) {
-    const int qb = q ^ full;
-    if (q < qb) {
-      oct_order.push_back(q);
-      oct_order.push_back(qb);
-    }
+  if (!(W > 0)) return ctx->fail(OBTE_EINVAL, "the weights must not all be zero");
+  std::vector<OrdIn> in(n_ord);
+  double kax[3] = {0, 0, 0};
+  for (int o = 0; o < n_ord; ++o) {
+    OrdIn& d = in[o];
+    const double u[3] = {dirs[3 * o], dirs[3 * o + 1], ctx->dim == 3 ? dirs[3 * o + 2] : 0.0};
+    for (int i = 0; i < 3; ++i) d.p[i] = u[ctx->perm[i]];
+    d.bin = bin ? bin[o] : 0;
+    d.lam = lambda[o];
+    d.aw = weight[o] / W;                 // a_o = W_o / sum W (E2)
+    d.kf = weight[o] * lambda[o];         // K_o = W_o Lambda_o s_o
+    for (int a = 0; a < 3; ++a) kax[a] += d.kf * lambda[o] * d.p[a] * d.p[a];
   }
-  // within an octant, order directions by their reversed direction's canonical
-  // index so that the k-th ordinate of octant q reverses to the k-th of q^full
-  std::vector<std::vector<int>> dir_in_oct(8);
-  for (int s = 0; s < n_dir; ++s) dir_in_oct[oct_of(s)].push_back(s);
-  auto find_rev = [&](int s) {
-    for (int t = 0; t < n_dir; ++t) {
-      bool same = true;
-      for (int a = 0; a < 3; ++a)
-        if (std::fabs(pdir[3 * t + a] + pdir[3 * s + a]) > 1e-12) same = false;
-      if (same && std::fabs(w[t] - w[s]) <= 1e-15 + 1e-12 * w[s]) return t;
-    }
-    return -1;
-  };
-  for (int i = 0; i + 1 < (int)oct_order.size(); i += 2) {
-    const int q = oct_order[i], qb = oct_order[i + 1];
-    std::vector<int> rv;
-    bool ok = true;
-    for (int s : dir_in_oct[q]) {
-      const int r = find_rev(s);
-      if (r < 0 || oct_of(r) != qb) ok = false;
-      rv.push_back(r);
-    }
-    if (ok && rv.size() == dir_in_oct[qb].size()) dir_in_oct[qb] = rv;  // paired order
-  }
-  ctx->ord_m.clear();
-  ctx->ord_s.clear();
-  ctx->octant.clear();
-  for (int q : oct_order)
-    for (int m = 0; m < n_mfp; ++m)
-      for (int s : dir_in_oct[q]) {
-        ctx->ord_m.push_back(m);
-        ctx->ord_s.push_back(s);
-        ctx->octant.push_back(q);
-      }
+  ctx->S = 0;
+  ctx->d_ang = 0;
+  ctx->kappa_m.clear();
+  ctx->lambda_m.clear();
+  ctx->sum_k_over_l2 = 0.0;
+  if (!(kax[0] > 0)) return ctx->fail(OBTE_EINVAL, "no ordinate moves along the gradient axis");
+  const int rc = build_material(ctx, in, n_bins, W, kax);
+  if (rc) return rc;
+  return upload_material(ctx);
+}
+
+// device copies of the ordinate table (FP64 and FP32), bins, octants and
+// wall denominators
+static int upload_material(obte_ctx* ctx) {
   const int O = ctx->O;
-  for (auto* v : {&ctx->bx, &ctx->by, &ctx->bz, &ctx->diag, &ctx->inv, &ctx->aw, &ctx->kxa,
-                  &ctx->kya, &ctx->kza})
-    v->assign(O, 0.0);
-  for (int a = 0; a < 3; ++a) ctx->pk[a].assign(O, 0.0);
-  double den_side[6] = {0, 0, 0, 0, 0, 0};
-  for (int o = 0; o < O; ++o) {
-    const int m = ctx->ord_m[o], s = ctx->ord_s[o];
-    const double lam = lambda_m[m];
-    double p[3] = {pdir[3 * s], pdir[3 * s + 1], pdir[3 * s + 2]};
-    for (int a = 0; a < 3; ++a) ctx->pk[a][o] = p[a];
-    double beta[3] = {0, 0, 0};
-    for (int a = 0; a < dim; ++a) beta[a] = lam * std::fabs(p[a]) / ctx->h[a];
-    const double D = beta[0] + beta[1] + beta[2];
-    ctx->bx[o] = beta[0];
-    ctx->by[o] = beta[1];
-    ctx->bz[o] = beta[2];
-    ctx->diag[o] = D;
-    ctx->inv[o] = 1.0 / (1.0 + D);
-    // E2 weight a_o = w_s (kappa_m / Lambda_m^2) / sum (kappa / Lambda^2)
-    ctx->aw[o] = w[s] * (kappa_m[m] / (lam * lam)) / sk;
-    // flux weight K_o = d_ang kappa_m w_s p_s / Lambda_m
-    const double kf = angular_dim * kappa_m[m] * w[s] / lam;
-    ctx->kxa[o] = kf * std::fabs(p[0]);
-    ctx->kya[o] = kf * std::fabs(p[1]);
-    ctx->kza[o] = dim == 3 ? kf * std::fabs(p[2]) : 0.0;
-    for (int a = 0; a < dim; ++a) {
-      const double k = kf * p[a];
-      if (k > 0) den_side[2 * a + 1] += k;   // leaves through the + face
-      if (k < 0) den_side[2 * a] += -k;      // leaves through the - face
-    }
-  }
-  for (int a = 0; a < dim; ++a) {
-    const double s0 = den_side[2 * a], s1 = den_side[2 * a + 1];
-    if (std::fabs(s0 - s1) > 1e-10 * std::max(s0, s1))
-      return ctx->fail(OBTE_EINVAL, "direction set is not mirror-symmetric: walls would not conserve energy");
-  }
-  ctx->wall_den_h.assign(std::max(1, ctx->n_walls), 1.0);
-  for (int f = 0; f < ctx->n_walls; ++f) {
-    const double d = den_side[ctx->wall_side_h[f]];
-    ctx->wall_den_h[f] = d > 0 ? d : 1.0;
-  }
-
   cudaSetDevice(ctx->device);
   const std::vector<double>* tabs[9] = {&ctx->bx, &ctx->by, &ctx->bz, &ctx->diag, &ctx->inv,
                                         &ctx->aw, &ctx->kxa, &ctx->kya, &ctx->kza};
@@ -961,6 +1057,17 @@ static int finalize_blocks(int n_cells) {
   return std::max(1, std::min(b, 296));
 }
 
+// Grid spacings for the heat-conduction stencil (first guess, Fourier model):
+// an axis-aligned anisotropic bulk tensor enters as kappa_a / h_a^2, i.e. as
+// spacings h_a sqrt(kappa_x / kappa_a) at conductivity kappa_x.
+static void cg_spacing(const obte_ctx* ctx, double he[3]) {
+  he[0] = ctx->h[0];
+  for (int a = 1; a < 3; ++a) {
+    const double r = ctx->kappa_axes[a] / ctx->kappa_axes[0];
+    he[a] = (r > 0 && std::isfinite(r)) ? ctx->h[a] / std::sqrt(r) : ctx->h[a];
+  }
+}
+
 static int init_from_fourier(obte_ctx* ctx, const obte_solve_opts& op, int* fiters_out) {
   const int prec = ctx->precision;
   int fmax = op.fourier_max_iter > 0 ? op.fourier_max_iter : 4 * (ctx->n[0] + ctx->n[1] + ctx->n[2]);
@@ -969,16 +1076,18 @@ static int init_from_fourier(obte_ctx* ctx, const obte_solve_opts& op, int* fite
   // looser can stop at the linear starting profile (no CG step at all on a
   // 256 x 256 mesh with a 25 % pore) and cost transport iterations
   double ftol = op.fourier_tol > 0 ? op.fourier_tol : kFourierTolDefault;
+  double he[3];
+  cg_spacing(ctx, he);
   if (ctx->n_cells <= 4096) {
     // small mesh: one block solves it, no grid-wide synchronisation
     if (!ctx->cg_job) ctx->cg_job = ctx->dalloc_t<CGArgs>(1);
     NEED(ctx->cg_job);
-    const CGArgs job = make_cg_args(ctx->gh, ctx->h[0], ctx->h[1], ctx->h[2], fmax, ftol, ctx->TF,
+    const CGArgs job = make_cg_args(ctx->gh, he[0], he[1], he[2], fmax, ftol, ctx->TF,
                                     ctx->fiters, ctx->fwork, kFourierBlocksMax);
     CK(cudaMemcpyAsync(ctx->cg_job, &job, sizeof(CGArgs), cudaMemcpyHostToDevice, ctx->stream));
     CK(launch_fourier_cg_blocks(ctx->cg_job, 1, prec, ctx->stream));
   } else {
-    CK(launch_fourier_cg(ctx->gh, ctx->h[0], ctx->h[1], ctx->h[2], prec, fmax, ftol, ctx->TF,
+    CK(launch_fourier_cg(ctx->gh, he[0], he[1], he[2], prec, fmax, ftol, ctx->TF,
                          ctx->fiters, ctx->fwork, kFourierBlocksMax, ctx->stream));
   }
   CK(launch_init_state_oct(ctx->gd, ctx->gh, 0, ctx->TF, prec, ctx->octant_d, ctx->stream));
@@ -1401,17 +1510,19 @@ extern "C" int obte_solve_fourier(obte_ctx* ctx, double tol, int max_iter, doubl
   g.py = ctx->periodic[1];
   g.pz = ctx->dim == 3 ? ctx->periodic[2] : 0;
   g.dT = ctx->dT;
+  double he[3];
+  cg_spacing(ctx, he);
   double flux = 0.0;
   int its = 0;
   std::vector<double> Th(T_out ? n : 0);
   auto run = [&]() -> int {
     if (ctx->n_cells <= 4096) {  // one block, no grid-wide synchronisation
-      const CGArgs job = make_cg_args(g, ctx->h[0], ctx->h[1], ctx->h[2], max_iter, tol, Tf, it_d, work,
+      const CGArgs job = make_cg_args(g, he[0], he[1], he[2], max_iter, tol, Tf, it_d, work,
                                       kFourierBlocksMax);
       CK(cudaMemcpyAsync(job_d, &job, sizeof(CGArgs), cudaMemcpyHostToDevice, ctx->stream));
       CK(launch_fourier_cg_blocks(job_d, 1, 0, ctx->stream));
     } else {
-      CK(launch_fourier_cg(g, ctx->h[0], ctx->h[1], ctx->h[2], 0, max_iter, tol, Tf, it_d, work,
+      CK(launch_fourier_cg(g, he[0], he[1], he[2], 0, max_iter, tol, Tf, it_d, work,
                            kFourierBlocksMax, ctx->stream));
     }
     CK(launch_fourier_hot_flux(ctx->code_d, Tf, ctx->n[0], ctx->n[1] * ctx->n[2], ctx->dT, flux_d,
@@ -1426,10 +1537,8 @@ extern "C" int obte_solve_fourier(obte_ctx* ctx, double tol, int max_iter, doubl
   if (rc) cudaStreamSynchronize(ctx->stream);  // nothing in flight uses the scratch when it is freed
   ctx->dfree(buf);
   if (rc) return rc;
-  double kappa_bulk = 0.0;
-  for (double k : ctx->kappa_m) kappa_bulk += k;
-  // kappa_fourier = L / (dT A_sec) sum_faces kappa_bulk (T_image + dT - T_cell) / h_x
-  *kappa_out = ctx->kappa_scale * kappa_bulk / ctx->h[0] * flux;
+  // kappa_fourier = L / (dT A_sec) sum_faces kappa_xx (T_image + dT - T_cell) / h_x
+  *kappa_out = ctx->kappa_scale * ctx->kappa_axes[0] / ctx->h[0] * flux;
   if (iters_out) *iters_out = its;
   if (T_out)
     to_user(ctx, [&](int c, long ui) { T_out[ui] = (ctx->code_h[c] & CODE_SOLID) ? Th[c] : NAN; });
@@ -1448,9 +1557,9 @@ extern "C" int obte_kappa_grad_s(obte_ctx* ctx, double* out, size_t max_field_by
   // reversed ordinate of every sorted ordinate (same bin, opposite direction)
   std::vector<int> rev(O, -1);
   {
-    std::map<std::tuple<int, long long, long long, long long>, int> idx;
+    std::map<std::tuple<int, double, long long, long long, long long>, int> idx;
     auto keyf = [&](int o, double sgn) {
-      return std::make_tuple(ctx->ord_m[o], llround(sgn * ctx->pk[0][o] * 1e12),
+      return std::make_tuple(ctx->ord_m[o], ctx->lam_o[o], llround(sgn * ctx->pk[0][o] * 1e12),
                              llround(sgn * ctx->pk[1][o] * 1e12), llround(sgn * ctx->pk[2][o] * 1e12));
     };
     for (int o = 0; o < O; ++o) idx[keyf(o, 1.0)] = o;
@@ -1499,9 +1608,10 @@ extern "C" int obte_kappa_grad_s(obte_ctx* ctx, double* out, size_t max_field_by
   NEED(a_d);
   NEED(grad_d);
   CK(cudaMemsetAsync(grad_d, 0, sizeof(double) * ctx->n_cells, ctx->stream));
-  // adjoint jump: -(L_x / (dT N_sec)) d_ang h_x sum kappa_m / Lambda_m^2; the
+  // adjoint jump: -(L_x / (dT N_sec)) h_x W, W the sum of the E2 weights before
+  // normalisation (d_ang sum kappa_m / Lambda_m^2 for the bin-separable set); the
   // adjoint field of o is jscale * T_rev(o) (up to a constant that cancels)
-  const double jadj = -ctx->kappa_scale * ctx->d_ang * ctx->h[0] * ctx->sum_k_over_l2;
+  const double jadj = -ctx->kappa_scale * ctx->h[0] * ctx->w_total;
   const double jscale = jadj / ctx->dT;
   std::vector<int> slot(O);
   std::vector<WorkItem> all_items = ctx->items_h;
@@ -1685,10 +1795,14 @@ extern "C" int obte_solve_batch(obte_ctx* const* ctxs, int n, const obte_solve_o
     const int fmax = op.fourier_max_iter > 0 ? op.fourier_max_iter : 4 * (c->n[0] + c->n[1] + c->n[2]);
     const double ftol = op.fourier_tol > 0 ? op.fourier_tol : kFourierTolDefault;
     if (c->n_cells <= kBlockCGMaxCells) {
-      jobs.push_back(make_cg_args(c->gh, c->h[0], c->h[1], c->h[2], fmax, ftol, c->TF, c->fiters,
+      double he[3];
+      cg_spacing(c, he);
+      jobs.push_back(make_cg_args(c->gh, he[0], he[1], he[2], fmax, ftol, c->TF, c->fiters,
                                   c->fwork, kFourierBlocksMax));
     } else {
-      cudaError_t e = launch_fourier_cg(c->gh, c->h[0], c->h[1], c->h[2], prec, fmax, ftol, c->TF,
+      double he[3];
+      cg_spacing(c, he);
+      cudaError_t e = launch_fourier_cg(c->gh, he[0], he[1], he[2], prec, fmax, ftol, c->TF,
                                         c->fiters, c->fwork, kFourierBlocksMax, ctx->stream);
       if (e != cudaSuccess) return ctx->cuda_fail(e, "batch Fourier");
     }
@@ -1885,9 +1999,9 @@ extern "C" int obte_kappa_grad_s_noalloc(obte_ctx* ctx, double* out) {
   const int O = ctx->O;
   std::vector<int> rev(O, -1);
   {
-    std::map<std::tuple<int, long long, long long, long long>, int> idx;
+    std::map<std::tuple<int, double, long long, long long, long long>, int> idx;
     auto keyf = [&](int o, double sgn) {
-      return std::make_tuple(ctx->ord_m[o], llround(sgn * ctx->pk[0][o] * 1e12),
+      return std::make_tuple(ctx->ord_m[o], ctx->lam_o[o], llround(sgn * ctx->pk[0][o] * 1e12),
                              llround(sgn * ctx->pk[1][o] * 1e12), llround(sgn * ctx->pk[2][o] * 1e12));
     };
     for (int o = 0; o < O; ++o) idx[keyf(o, 1.0)] = o;
@@ -1947,7 +2061,7 @@ extern "C" int obte_kappa_grad_s_noalloc(obte_ctx* ctx, double* out) {
   }
   // the scratch keeps the previous call's contents: start the sum at zero
   CK(cudaMemsetAsync(grad_d, 0, sizeof(double) * ctx->n_cells, ctx->stream));
-  const double jadj = -ctx->kappa_scale * ctx->d_ang * ctx->h[0] * ctx->sum_k_over_l2;
+  const double jadj = -ctx->kappa_scale * ctx->h[0] * ctx->w_total;
   const double jscale = jadj / ctx->dT;
   std::vector<int> slot(O);
   int one = 1, zero = 0;

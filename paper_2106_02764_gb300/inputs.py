@@ -162,6 +162,9 @@ class Workload:
     quad: Quadrature
     s: Optional[np.ndarray] = None  # per-cell scattering scale [nz, ny, nx]
     grad_axis: int = 0
+    # general per-ordinate material (lambda [O], dirs [O,3], weight [O], bin [O]);
+    # when set it replaces the bin x direction material above
+    ords: Optional[dict] = None
 
     @property
     def n_solid(self) -> int:
@@ -169,6 +172,8 @@ class Workload:
 
     @property
     def n_ordinates(self) -> int:
+        if self.ords is not None:
+            return len(self.ords["lambda"])
         return len(self.kappa_m) * len(self.quad.weights)
 
     @property
@@ -299,6 +304,38 @@ def small_film(n=8, nz=4, porosity=0.15, n_bins=3, n_phi=8, n_mu=4,
     return Workload(f"small-film-{n}x{n}x{nz}", 3, (n, n, nz), (length, length, thickness),
                     mask, (1, 1, 0), 1.0, *mfp_bins(n_bins),
                     sphere_quadrature(n_phi, n_mu))
+
+
+def anisotropic_material(kappa_m, lambda_m, quad: Quadrature, eps_lambda: float = 0.3,
+                         eps_weight: float = 0.5) -> dict:
+    """Synthetic per-ordinate material: the general aMFP input (Sec. 5), where
+    the Material module gives every ordinate its own vectorial MFP and weight
+    from mode data; no mode data exist here, so an anisotropy is imposed on
+    MFP bins (kappa_m, lambda_m) and the directions of ``quad``.  Ordinate
+    (m, s), phi_s the azimuth of s:
+        Lambda = lambda_m (1 + eps_lambda cos 2 phi_s)
+        weight = d_ang w_s (kappa_m / lambda_m^2) (1 + eps_weight sin^2 phi_s)
+    (weight: the C/tau of the ordinate's modes, scaled so that at
+    eps_lambda = eps_weight = 0 the bulk conductivity is sum kappa_m).  Both
+    are even under s -> -s (time reversal, as for mode data)."""
+    kappa_m = np.asarray(kappa_m, np.float64)
+    lam_m = np.asarray(lambda_m, np.float64)
+    phi = np.arctan2(quad.dirs[:, 1], quad.dirs[:, 0])
+    M, S = len(lam_m), len(quad.weights)
+    lam = (lam_m[:, None] * (1.0 + eps_lambda * np.cos(2.0 * phi))[None, :]).ravel()
+    weight = (quad.angular_dim * (kappa_m / lam_m ** 2)[:, None] * quad.weights[None, :]
+              * (1.0 + eps_weight * np.sin(phi) ** 2)[None, :]).ravel()
+    dirs = np.tile(quad.dirs, (M, 1))
+    bins = np.repeat(np.arange(M), S)
+    return {"lambda": lam, "dirs": dirs, "weight": weight, "bin": bins}
+
+
+def anisotropic(wl: Workload, eps_lambda: float = 0.3, eps_weight: float = 0.5) -> Workload:
+    """The workload ``wl`` with its material made anisotropic (see
+    anisotropic_material; same bins and directions)."""
+    w = dataclasses.replace(wl, name=wl.name + f"-aniso{eps_lambda:g}-{eps_weight:g}")
+    w.ords = anisotropic_material(wl.kappa_m, wl.lambda_m, wl.quad, eps_lambda, eps_weight)
+    return w
 
 
 CONFIGS = {1: config1, 2: config2, 3: config3, 4: config4, 5: config5}
