@@ -68,8 +68,9 @@ def test_general_material_parity(name, precision):
     assert np.abs(TL - ref.T_L).max() <= TL_ATOL
     if precision == "fp64":
         assert abs(k - ref.kappa) < 1e-9 * abs(ref.kappa)
-    # the per-bin spectrum adds up to kappa
-    assert abs(s.kappa_bins().sum() - k) <= 1e-9 * abs(k)
+    # the per-bin spectrum (from one more sweep of the final state) adds up to
+    # kappa; in mixed precision that sweep moves kappa by float rounding
+    assert abs(s.kappa_bins().sum() - k) <= (1e-9 if precision == "fp64" else 1e-6) * abs(k)
 
 
 def test_isotropic_limit_matches_separable_entry_point():
