@@ -122,7 +122,8 @@ def reversed_ordinate(ords: bte.Ordinates):
     direction."""
     rev = np.empty(ords.n, dtype=np.int64)
     for o in range(ords.n):
-        cand = np.nonzero((ords.m_of == ords.m_of[o]) & (ords.lam == ords.lam[o]) &
+        cand = np.nonzero((ords.m_of == ords.m_of[o]) &
+                          (np.abs(ords.lam - ords.lam[o]) <= 1e-12 * ords.lam[o]) &
                           np.all(np.abs(ords.p + ords.p[o]) < 1e-12, axis=1))[0]
         if len(cand) != 1:
             raise ValueError("quadrature is not symmetric under p -> -p")

@@ -67,6 +67,7 @@ struct obte_ctx {
   double w_total = 0.0;                           // sum of the E2 weights before normalisation
   double kappa_axes[3] = {0, 0, 0};               // bulk conductivity along each kernel axis
   std::vector<double> lam_o;                      // Lambda per sorted ordinate
+  std::vector<int> rev_o;                         // reversed sorted ordinate, -1 if none
 
   // solve state
   int precision = -1;
@@ -481,6 +482,7 @@ static int build_material(obte_ctx* ctx, const std::vector<OrdIn>& in, int n_bin
     if (std::fabs(in[t].lam - in[o].lam) > 1e-12 * in[o].lam) return false;
     return std::fabs(in[t].aw - in[o].aw) <= 1e-300 + 1e-12 * in[o].aw;
   };
+  std::vector<char> paired(8, 0);
   for (int i = 0; i + 1 < (int)oct_order.size(); i += 2) {
     const int q = oct_order[i], qb = oct_order[i + 1];
     if (in_oct[q].size() != in_oct[qb].size()) continue;
@@ -503,15 +505,44 @@ static int build_material(obte_ctx* ctx, const std::vector<OrdIn>& in, int n_bin
       used[r] = 1;
       rv.push_back(r);
     }
-    if (ok) in_oct[qb] = rv;  // paired order
+    if (ok) {
+      in_oct[qb] = rv;  // paired order
+      paired[q] = paired[qb] = 1;
+    }
   }
   std::vector<int> order;
+  std::vector<int> first(8, 0);
   ctx->octant.clear();
-  for (int q : oct_order)
+  for (int q : oct_order) {
+    first[q] = (int)order.size();
     for (int o : in_oct[q]) {
       order.push_back(o);
       ctx->octant.push_back(q);
     }
+  }
+  // reversed ordinate of every sorted ordinate (-1 where the set has none):
+  // the paired octant order gives it directly; otherwise (directions on a
+  // coordinate plane) a search in the ordinate's bin
+  ctx->rev_o.assign(n, -1);
+  {
+    std::vector<int> pos(n);
+    for (int o = 0; o < n; ++o) pos[order[o]] = o;
+    std::map<int, std::vector<int>> by_bin;
+    for (int t = 0; t < n; ++t) by_bin[in[t].bin].push_back(t);
+    for (int q : oct_order)
+      for (int k = 0; k < (int)in_oct[q].size(); ++k) {
+        const int o = first[q] + k;
+        if (paired[q]) {
+          ctx->rev_o[o] = first[q ^ full] + k;
+          continue;
+        }
+        for (int t : by_bin[in[order[o]].bin])
+          if (reverses(t, order[o])) {
+            ctx->rev_o[o] = pos[t];
+            break;
+          }
+      }
+  }
   const int O = n;
   ctx->O = O;
   ctx->M = n_bins;
@@ -1555,20 +1586,10 @@ extern "C" int obte_kappa_grad_s(obte_ctx* ctx, double* out, size_t max_field_by
   cudaSetDevice(ctx->device);
   const int O = ctx->O;
   // reversed ordinate of every sorted ordinate (same bin, opposite direction)
-  std::vector<int> rev(O, -1);
-  {
-    std::map<std::tuple<int, double, long long, long long, long long>, int> idx;
-    auto keyf = [&](int o, double sgn) {
-      return std::make_tuple(ctx->ord_m[o], ctx->lam_o[o], llround(sgn * ctx->pk[0][o] * 1e12),
-                             llround(sgn * ctx->pk[1][o] * 1e12), llround(sgn * ctx->pk[2][o] * 1e12));
-    };
-    for (int o = 0; o < O; ++o) idx[keyf(o, 1.0)] = o;
-    for (int o = 0; o < O; ++o) {
-      auto it = idx.find(keyf(o, -1.0));
-      if (it == idx.end()) return ctx->fail(OBTE_EINVAL, "direction set is not symmetric under p -> -p");
-      rev[o] = it->second;
-    }
-  }
+  // (paired when the material was set: same bin, MFP and weight, opposite direction)
+  const std::vector<int>& rev = ctx->rev_o;
+  for (int o = 0; o < O; ++o)
+    if (rev[o] < 0) return ctx->fail(OBTE_EINVAL, "direction set is not symmetric under p -> -p");
   if (max_field_bytes == 0) max_field_bytes = (size_t)1 << 30;
   const size_t e = ctx->precision == 0 ? 8 : 4;
   const size_t per_ord = e * (size_t)ctx->n_cells;
@@ -1997,20 +2018,10 @@ extern "C" int obte_kappa_grad_s_noalloc(obte_ctx* ctx, double* out) {
   unsigned char* base = nullptr;
   CK(noalloc_scratch(ctx->device, &base));
   const int O = ctx->O;
-  std::vector<int> rev(O, -1);
-  {
-    std::map<std::tuple<int, double, long long, long long, long long>, int> idx;
-    auto keyf = [&](int o, double sgn) {
-      return std::make_tuple(ctx->ord_m[o], ctx->lam_o[o], llround(sgn * ctx->pk[0][o] * 1e12),
-                             llround(sgn * ctx->pk[1][o] * 1e12), llround(sgn * ctx->pk[2][o] * 1e12));
-    };
-    for (int o = 0; o < O; ++o) idx[keyf(o, 1.0)] = o;
-    for (int o = 0; o < O; ++o) {
-      auto it = idx.find(keyf(o, -1.0));
-      if (it == idx.end()) return ctx->fail(OBTE_EINVAL, "direction set is not symmetric under p -> -p");
-      rev[o] = it->second;
-    }
-  }
+  // (paired when the material was set: same bin, MFP and weight, opposite direction)
+  const std::vector<int>& rev = ctx->rev_o;
+  for (int o = 0; o < O; ++o)
+    if (rev[o] < 0) return ctx->fail(OBTE_EINVAL, "direction set is not symmetric under p -> -p");
   // scratch layout: grad | slots | work items | per batch ordinate: field + rev + weight
   auto up = [](size_t b) { return (b + 255) & ~(size_t)255; };
   const size_t e = ctx->precision == 0 ? 8 : 4;
