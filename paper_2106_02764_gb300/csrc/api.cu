@@ -752,7 +752,7 @@ const Variant kVariants2D_F[] = {{16, 4, false}, {8, 4, false}, {8, 8, false}, {
                                  {8, 2, false}, {4, 4, false}, {16, 1, false}};
 const Variant kVariants2D_D[] = {{8, 2, false}, {8, 4, false}, {4, 4, false}, {4, 8, false},
                                  {8, 1, false}};
-const Variant kVariants3D_F[] = {{8, 8, false, true}, {4, 8, false, true}, {8, 4, false, true},
+const Variant kVariants3D_F[] = {{8, 4, false, true}, {8, 8, false, true}, {4, 8, false, true},
                                  {4, 4, false, true}, {8, 2, false, true},
                                  {8, 8, false}, {4, 8, false}, {8, 4, false}, {4, 4, false},
                                  {8, 2, false}, {4, 2, false}};
