@@ -746,7 +746,7 @@ struct Variant {
 
 const Variant kWarp2D_F[] = {{8, 8, true}, {8, 4, true}, {16, 4, true}, {16, 2, true},
                              {16, 1, true}, {8, 1, true},  {6, 8, true},  {4, 8, true},
-                             {4, 4, true}};
+                             {4, 4, true},  {8, 2, true}};
 const Variant kWarp2D_D[] = {{4, 8, true}, {8, 4, true}, {8, 2, true}, {8, 1, true}, {2, 8, true}};
 const Variant kVariants2D_F[] = {{16, 4, false}, {8, 4, false}, {8, 8, false}, {16, 2, false},
                                  {8, 2, false}, {4, 4, false}, {16, 1, false}};
@@ -1017,6 +1017,8 @@ static int prepare_state(obte_ctx* ctx, int precision, int G, int R, bool warp, 
   g.kza = ctx->tab_d[p][TB_KZA];
   g.mbin = ctx->mbin_d;
   g.ord_d0 = nullptr;  // set below once the work items are known
+  g.octant_of = ctx->octant_d;
+  g.T0 = ctx->TF;
   g.done = ctx->ctrl + 0;
   g.iter = ctx->ctrl + 1;
   g.nonfinite = ctx->ctrl + 2;
@@ -1121,7 +1123,8 @@ static int init_from_fourier(obte_ctx* ctx, const obte_solve_opts& op, int* fite
     CK(launch_fourier_cg(ctx->gh, he[0], he[1], he[2], prec, fmax, ftol, ctx->TF,
                          ctx->fiters, ctx->fwork, kFourierBlocksMax, ctx->stream));
   }
-  CK(launch_init_state_oct(ctx->gd, ctx->gh, 0, ctx->TF, prec, ctx->octant_d, ctx->stream));
+  CK(launch_init_state(ctx->gd, 1, std::max((long)ctx->gh.n_cells * 6, (long)ctx->gh.n_ord * ctx->gh.rows),
+                       ctx->gh.n_walls, prec, ctx->stream));
   if (ctx->warp || ctx->k3d) CK(launch_build_records(ctx->gd, 1, prec, finalize_blocks(ctx->n_cells), ctx->stream));
   if (ctx->gh.aa_m > 0)
     CK(launch_anderson_init(ctx->gd, 1, prec, aa_blocks(ctx->n_cells, ctx->O, ctx->n[1] * ctx->n[2]), ctx->stream));
@@ -1744,6 +1747,25 @@ extern "C" int obte_solve_batch(obte_ctx* const* ctxs, int n, const obte_solve_o
       }
     if (!r_eff[i]) use_warp = false;
   }
+  // Fixed-rows classes (mixed precision without s(x)): every geometry runs the
+  // compiled fixed-R instance with the most lanes in use (R in 1, 2, 4, 8
+  // dividing N with N / R <= 32 lanes); the geometries of one class share a
+  // launch, the classes run side by side on forked streams, and a class whose
+  // rows fill the 32 lanes adds the four warps' moments in shared memory
+  bool use_cls = use_warp && prec == 1 && !any_s && op.rows_per_thread <= 0;
+  {
+    std::vector<int> r_cls(n, 0);
+    for (int i = 0; use_cls && i < n; ++i) {
+      const int ny = ctxs[i]->n[1];
+      for (int R : {1, 2, 4, 8})
+        if (ny % R == 0 && ny / R <= 32 && sweep2d_warp_exists(prec, wG, R, false, true)) {
+          r_cls[i] = R;
+          break;
+        }
+      if (!r_cls[i]) use_cls = false;
+    }
+    if (use_cls) r_eff = r_cls;
+  }
   Variant v{0, 0, false};
   if (!use_warp) {
     std::vector<Variant> common;
@@ -1774,13 +1796,67 @@ extern "C" int obte_solve_batch(obte_ctx* const* ctxs, int n, const obte_solve_o
   NEED(gds);
   std::vector<GeomDev> gh(n);
   std::vector<WorkItem> items;
-  for (int i = 0; i < n; ++i) {
-    gh[i] = ctxs[i]->gh;
-    build_items(ctxs[i], i, v.G, items);
+  struct ItemClass {
+    int R;
+    bool full;      // rows fill 32 lanes: items in blocks of four of one octant, moments combined
+    size_t off, count;
+  };
+  std::vector<ItemClass> classes;
+  for (int i = 0; i < n; ++i) gh[i] = ctxs[i]->gh;
+  if (use_cls) {
+    // per class: the geometries' items (padded as their starting state
+    // assumed), blocks of four kept together, costliest first
+    std::vector<std::pair<int, bool>> keys;
+    for (int i = 0; i < n; ++i) {
+      const std::pair<int, bool> key(r_eff[i], ctxs[i]->items_pad == 4);
+      if (std::find(keys.begin(), keys.end(), key) == keys.end()) keys.push_back(key);
+    }
+    for (const auto& key : keys) {
+      const int pad = key.second ? 4 : 1;
+      std::vector<std::vector<WorkItem>> chunks;
+      for (int i = 0; i < n; ++i) {
+        if (r_eff[i] != key.first || (ctxs[i]->items_pad == 4) != key.second) continue;
+        std::vector<WorkItem> it;
+        build_items(ctxs[i], i, v.G, it, nullptr, ctxs[i]->items_pad);
+        for (size_t a = 0; a < it.size(); a += pad)
+          chunks.emplace_back(it.begin() + a, it.begin() + std::min(it.size(), a + pad));
+      }
+      auto cost = [&](const std::vector<WorkItem>& c) {
+        long w = 0;
+        for (const WorkItem& x : c) w += (long)gh[x.geom].n_cells * x.count;
+        return w;
+      };
+      std::stable_sort(chunks.begin(), chunks.end(),
+                       [&](const std::vector<WorkItem>& a, const std::vector<WorkItem>& b) { return cost(a) > cost(b); });
+      ItemClass c{key.first, key.second, items.size(), 0};
+      for (auto& ch : chunks) items.insert(items.end(), ch.begin(), ch.end());
+      c.count = items.size() - c.off;
+      classes.push_back(c);
+    }
+  } else {
+    for (int i = 0; i < n; ++i) build_items(ctxs[i], i, v.G, items, nullptr, ctxs[i]->items_pad);
+    std::stable_sort(items.begin(), items.end(), [&](const WorkItem& a, const WorkItem& b) {
+      return (long)gh[a.geom].n_cells * a.count > (long)gh[b.geom].n_cells * b.count;
+    });
   }
-  std::stable_sort(items.begin(), items.end(), [&](const WorkItem& a, const WorkItem& b) {
-    return (long)gh[a.geom].n_cells * a.count > (long)gh[b.geom].n_cells * b.count;
-  });
+  // one stream per class, forked from and joined back into the solve's stream
+  std::vector<cudaStream_t> side(classes.size(), nullptr);
+  std::vector<cudaEvent_t> joined(classes.size(), nullptr);
+  cudaEvent_t forked = nullptr;
+  auto drop_streams = [&]() {
+    for (auto& st : side)
+      if (st) cudaStreamDestroy(st);
+    for (auto& ev : joined)
+      if (ev) cudaEventDestroy(ev);
+    if (forked) cudaEventDestroy(forked);
+  };
+  if (!classes.empty()) {
+    CK(cudaEventCreateWithFlags(&forked, cudaEventDisableTiming));
+    for (size_t c = 0; c < classes.size(); ++c) {
+      CK(cudaStreamCreateWithFlags(&side[c], cudaStreamNonBlocking));
+      CK(cudaEventCreateWithFlags(&joined[c], cudaEventDisableTiming));
+    }
+  }
   WorkItem* items_d = ctx->dalloc_t<WorkItem>(items.size());
   int* counter = ctx->dalloc_t<int>(1);
   NEED(items_d);
@@ -1842,29 +1918,56 @@ extern "C" int obte_solve_batch(obte_ctx* const* ctxs, int n, const obte_solve_o
     if (ec == cudaErrorNotSupported) CK(launch_fourier_cg_blocks(jobs_d, (int)jobs.size(), prec, ctx->stream));
     else CK(ec);
   }
-  for (int i = 0; i < n; ++i) {
-    obte_ctx* c = ctxs[i];
-    cudaError_t e = launch_init_state_oct(gds, gh[i], i, c->TF, prec, c->octant_d, ctx->stream);
-    if (e == cudaSuccess && v.warp) e = launch_build_records(gds + i, 1, prec, finalize_blocks(c->n_cells), ctx->stream);
-    if (e == cudaSuccess && gh[i].aa_m > 0)
-      e = launch_anderson_init(gds + i, 1, prec, aa_blocks(c->n_cells, c->O, c->n[1] * c->n[2]), ctx->stream);
+  {
+    // every geometry's starting state in one launch per kernel (grid y = geometry)
+    long max_work = 0;
+    int max_walls = 0;
+    bool any_aa = false;
+    for (int i = 0; i < n; ++i) {
+      max_work = std::max(max_work, std::max((long)gh[i].n_cells * 6, (long)gh[i].n_ord * gh[i].rows));
+      max_walls = std::max(max_walls, gh[i].n_walls);
+      any_aa = any_aa || gh[i].aa_m > 0;
+    }
+    cudaError_t e = launch_init_state(gds, n, max_work, max_walls, prec, ctx->stream);
+    if (e == cudaSuccess && v.warp) e = launch_build_records(gds, n, prec, finalize_blocks(max_cells), ctx->stream);
+    if (e == cudaSuccess && any_aa)
+      e = launch_anderson_init(gds, n, prec, aa_blocks(max_cells, max_ord, max_rows), ctx->stream);
     if (e != cudaSuccess) return ctx->cuda_fail(e, "batch init");
   }
   CK(cudaEventRecord(e1, ctx->stream));
   const int k = std::max(1, op.check_every);
   auto body = [&]() -> cudaError_t {
     for (int it = 0; it < k; ++it) {
-      cudaError_t e = cudaMemsetAsync(counter, 0, sizeof(int), ctx->stream);
-      if (e != cudaSuccess) return e;
-      SweepLaunch L;
-      L.geoms = gds;
-      L.items = items_d;
-      L.n_items = (int)items.size();
-      L.flags = 0;
-      L.item_counter = counter;
-      e = v.warp ? launch_sweep2d_warp(L, prec, v.G, v.R, any_s, false, blocks, ctx->stream)
-                 : launch_sweep(L, prec, ctx->dim, v.G, v.R, any_s, threads, blocks, smem, ctx->stream);
-      if (e != cudaSuccess) return e;
+      cudaError_t e = cudaSuccess;
+      if (!classes.empty()) {
+        e = cudaEventRecord(forked, ctx->stream);
+        for (size_t c = 0; c < classes.size() && e == cudaSuccess; ++c) {
+          e = cudaStreamWaitEvent(side[c], forked, 0);
+          if (e != cudaSuccess) break;
+          SweepLaunch L;
+          L.geoms = gds;
+          L.items = items_d + classes[c].off;
+          L.n_items = (int)classes[c].count;
+          L.flags = classes[c].full ? SWEEP_BLOCK_COMBINE : 0;
+          L.item_counter = nullptr;  // one warp per item, blocks of four items
+          e = launch_sweep2d_warp(L, prec, v.G, classes[c].R, false, true, 0, side[c]);
+          if (e == cudaSuccess) e = cudaEventRecord(joined[c], side[c]);
+          if (e == cudaSuccess) e = cudaStreamWaitEvent(ctx->stream, joined[c], 0);
+        }
+        if (e != cudaSuccess) return e;
+      } else {
+        e = cudaMemsetAsync(counter, 0, sizeof(int), ctx->stream);
+        if (e != cudaSuccess) return e;
+        SweepLaunch L;
+        L.geoms = gds;
+        L.items = items_d;
+        L.n_items = (int)items.size();
+        L.flags = 0;
+        L.item_counter = counter;
+        e = v.warp ? launch_sweep2d_warp(L, prec, v.G, v.R, any_s, false, blocks, ctx->stream)
+                   : launch_sweep(L, prec, ctx->dim, v.G, v.R, any_s, threads, blocks, smem, ctx->stream);
+        if (e != cudaSuccess) return e;
+      }
       e = launch_finalize(gds, n, prec, finalize_blocks(max_cells), ctx->stream);
       if (e != cudaSuccess) return e;
       if (op.accel > 0) {
@@ -1965,6 +2068,7 @@ extern "C" int obte_solve_batch(obte_ctx* const* ctxs, int n, const obte_solve_o
     else if (done != 1 && worst == OBTE_OK) worst = OBTE_NOT_CONVERGED;
   }
   cudaFreeHost(hc);
+  drop_streams();
   if (jobs_d) ctx->dfree(jobs_d);
   ctx->dfree(gds);
   ctx->dfree(items_d);

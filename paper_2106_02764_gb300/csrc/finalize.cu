@@ -30,9 +30,11 @@ __global__ void finalize_kernel(const GeomDev* geoms) {
   const int stride = gridDim.x * blockDim.x;
   for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < n_cells; c += stride) {
     if (!(code[c] & CODE_SOLID)) continue;
-    double t = TL_acc[c];
-    TL_acc[c] = 0.0;
-    if (g.tlq) {  // skewed per-quadrant partials of the 2D warp kernel
+    double t = 0.0;
+    if (!g.tlq) {  // per-cell accumulator (the 2D warp kernel uses the skewed one only)
+      t = TL_acc[c];
+      TL_acc[c] = 0.0;
+    } else {  // skewed per-quadrant partials of the 2D warp kernel
       const int nx = g.nx, ny = g.ny;
       const int x = c % nx, y = c / nx;
       size_t k[4];
@@ -110,10 +112,12 @@ __global__ void finalize_tail_kernel(const GeomDev* geoms, int nblocks) {
 // T_L, the sweep source, wall temperatures (their cell's value) and the row
 // values carried into the first sweep (the value of the cell each row visits
 // last, for every ordinate's octant).
+// Grid: x = blocks per geometry, y = geometry.
 template <typename T>
-__global__ void init_state_kernel(const GeomDev* geoms, int gi, const double* T0,
-                                  const int* octant_of) {
-  const GeomDev& g = geoms[gi];
+__global__ void init_state_kernel(const GeomDev* geoms) {
+  const GeomDev& g = geoms[blockIdx.y];
+  const double* T0 = g.T0;
+  const int* octant_of = g.octant_of;
   const int tid = blockIdx.x * blockDim.x + threadIdx.x;
   const int stride = gridDim.x * blockDim.x;
   T* src = reinterpret_cast<T*>(g.src);
@@ -290,26 +294,24 @@ cudaError_t launch_finalize(const GeomDev* geoms_dev, int n_geoms, int precision
 }
 
 template <typename T>
-__global__ void init_twc_kernel(const GeomDev* geoms, int gi) {
-  const GeomDev& g = geoms[gi];
+__global__ void init_twc_kernel(const GeomDev* geoms) {
+  const GeomDev& g = geoms[blockIdx.y];
   T* twc = reinterpret_cast<T*>(g.twc);
   for (int f = blockIdx.x * blockDim.x + threadIdx.x; f < g.n_walls; f += gridDim.x * blockDim.x)
     twc[(size_t)g.wall_cell[f] * 6 + g.wall_side[f]] = (T)g.Tw[f];
 }
 
-cudaError_t launch_init_state_oct(const GeomDev* geoms_dev, const GeomDev& gh, int gi,
-                                  const double* T0, int precision, const int* octant_of,
-                                  cudaStream_t st) {
-  const long work = std::max((long)gh.n_cells * 6, (long)gh.n_ord * gh.rows);
-  int blocks = (int)std::min<long>((work + 255) / 256, 4096);
-  if (blocks < 1) blocks = 1;
-  const int wb = std::max(1, std::min((gh.n_walls + 255) / 256, 1024));
+cudaError_t launch_init_state(const GeomDev* geoms_dev, int n_geoms, long max_work, int max_walls,
+                              int precision, cudaStream_t st) {
+  const dim3 grid((unsigned)std::max<long>(1, std::min<long>((max_work + 255) / 256, 4096)),
+                  (unsigned)n_geoms);
+  const dim3 wgrid((unsigned)std::max(1, std::min((max_walls + 255) / 256, 1024)), (unsigned)n_geoms);
   if (precision == 0) {
-    init_state_kernel<double><<<blocks, 256, 0, st>>>(geoms_dev, gi, T0, octant_of);
-    init_twc_kernel<double><<<wb, 256, 0, st>>>(geoms_dev, gi);
+    init_state_kernel<double><<<grid, 256, 0, st>>>(geoms_dev);
+    init_twc_kernel<double><<<wgrid, 256, 0, st>>>(geoms_dev);
   } else {
-    init_state_kernel<float><<<blocks, 256, 0, st>>>(geoms_dev, gi, T0, octant_of);
-    init_twc_kernel<float><<<wb, 256, 0, st>>>(geoms_dev, gi);
+    init_state_kernel<float><<<grid, 256, 0, st>>>(geoms_dev);
+    init_twc_kernel<float><<<wgrid, 256, 0, st>>>(geoms_dev);
   }
   return cudaGetLastError();
 }

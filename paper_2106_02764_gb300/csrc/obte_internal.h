@@ -101,6 +101,8 @@ struct GeomDev {
   const void* aw; const void* kxa; const void* kya; const void* kza; const void* kx;
   const int* mbin;        // [n_ord] MFP bin of each sorted ordinate
   const int* ord_d0;      // [n_ord] start step of the group holding each ordinate
+  const int* octant_of;   // [n_ord] octant of each sorted ordinate
+  const double* T0;       // [n_cells] starting temperature (the Fourier first guess)
   // control
   int* done;              // [1] converged flag
   int* iter;              // [1] iterations run
@@ -173,9 +175,10 @@ cudaError_t launch_anderson_step(const GeomDev* geoms_dev, int n_geoms, int prec
 cudaError_t launch_build_records(const GeomDev* geoms_dev, int n_geoms, int precision, int blocks,
                                  cudaStream_t st);
 constexpr int kMaxSkewCells = 1 << 22;
-cudaError_t launch_init_state_oct(const GeomDev* geoms_dev, const GeomDev& gh, int gi,
-                                  const double* T0, int precision, const int* octant_of,
-                                  cudaStream_t st);  // uses gh.ord_d0
+// state at iteration 0 from each geometry's T0, geometries geoms_dev[0 .. n_geoms);
+// max_work = max over them of max(6 n_cells, n_ord rows), max_walls likewise
+cudaError_t launch_init_state(const GeomDev* geoms_dev, int n_geoms, long max_work, int max_walls,
+                              int precision, cudaStream_t st);
 cudaError_t launch_gauge(const uint8_t* code, const double* TL, int n, double* out,
                          double* mean_out, cudaStream_t st);
 cudaError_t launch_grad_contract2(const uint8_t* code, const double* TL, int n, const void* rec,

@@ -10,6 +10,7 @@
   X(float, 4, 8, false, true) \
   X(float, 4, 4, false, true) \
   X(float, 8, 4, false, true) \
+  X(float, 8, 2, false, true) \
   X(float, 16, 4, false, true) \
   X(float, 16, 2, false, true) \
   X(float, 16, 1, false, true) \

@@ -69,3 +69,38 @@ def test_batch_anderson():
         pr, ref = oracle(w)
         assert abs(s.kappa_eff - ref.kappa) <= KAPPA_RTOL["fp64"] * ref.kappa
         assert np.abs(solid_vector(pr, s.T_L()) - ref.T_L).max() <= TL_ATOL
+
+
+def _class_geoms():
+    """Sizes that make the mixed batch run several fixed-rows classes at once:
+    32 (1 row per lane, 32 lanes: moments combined per block of four warps),
+    64 (2 rows, 32 lanes: combined), 48 (2 rows, 24 lanes), 96 (4 rows,
+    24 lanes), 24 (1 row, 24 lanes)."""
+    L = 100e-9
+    q = I.circle_quadrature(16)
+    return [
+        I.make_2d("c32", 32, L, [I.circle_pore(L, L, 0.2)], 3, q),
+        I.make_2d("c64", 64, L, [I.square_pore(L, L, 0.12, x=0.3 * L, y=0.6 * L)], 3, q),
+        I.make_2d("c48", 48, L, [I.circle_pore(L, L, 0.15, x=0.4 * L, y=0.45 * L)], 3, q),
+        I.make_2d("c96", 96, L, [I.circle_pore(L, L, 0.1)], 3, q),
+        I.make_2d("c24", 24, L, [], 3, q),
+    ]
+
+
+def test_mixed_batch_fixed_row_classes():
+    """Mixed precision: every geometry of a batch that runs several fixed-rows
+    classes side by side (forked streams, block-combined moments where rows
+    fill the lanes) agrees with the oracle and with its own single solve."""
+    from paper_2106_02764_gb300.binding import Solver, solve_batch
+    geoms = _class_geoms()
+    solvers = [Solver.from_workload(w) for w in geoms]
+    opts = dict(tol=0.0, tol_TL=0.0, max_iter=3000, check_every=50)
+    stats = solve_batch(solvers, precision="mixed", allow_not_converged=True, **opts)
+    assert sorted({st["rows_per_thread"] for st in stats}) == [1, 2, 4]
+    for w, s in zip(geoms, solvers):
+        pr, ref = oracle(w)
+        assert abs(s.kappa_eff - ref.kappa) <= KAPPA_RTOL["mixed"] * ref.kappa
+        assert np.abs(solid_vector(pr, s.T_L()) - ref.T_L).max() <= TL_ATOL
+        one = Solver.from_workload(w)
+        one.solve(precision="mixed", allow_not_converged=True, **opts)
+        assert abs(one.kappa_eff - s.kappa_eff) <= 1e-5 * one.kappa_eff
