@@ -495,12 +495,15 @@ __global__ void __launch_bounds__(32 * WarpCfg<T, G, RMAX>::WPB, WarpCfg<T, G, R
       }
       if (comb) {
         __syncthreads();
-        // warp wib: rows wib * 8 RMAX + 32 k + lane, k < RMAX / 4
-        constexpr int RQ = (RMAX + 3) / 4;
+        // warp wib adds the quarter of the 32 RMAX rows starting at
+        // wib * 8 RMAX: row wib * 8 RMAX + 32 k + lane for 32 k + lane < 8 RMAX
+        // (fewer than 32 rows for RMAX < 4: the other lanes idle)
+        constexpr int RQ = (8 * RMAX + 31) / 32;
 #pragma unroll
         for (int k = 0; k < RQ; ++k) {
-          const int j = wib * 8 * RMAX + 32 * k + lane;
-          if (RMAX % 4 == 0 || j < 32 * RMAX) {
+          const int local = 32 * k + lane;
+          const int j = wib * 8 * RMAX + local;
+          if ((8 * RMAX) % 32 == 0 || local < 8 * RMAX) {
             const T t01 = tlbuf[par][0][j] + tlbuf[par][1][j];
             const T t23 = tlbuf[par][2][j] + tlbuf[par][3][j];
             atomicAdd(tlq + (size_t)s * ny + j, (double)(t01 + t23));

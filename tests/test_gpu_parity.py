@@ -219,3 +219,18 @@ def test_fma_rate_measurement():
     f64 = measure_fma_rate("fp64") / 1e12
     assert 1.0 < f32 < 1.3 * 80.5
     assert 0.0 < f64 < f32
+
+
+@pytest.mark.parametrize("n,G,R", [(32, 8, 1), (32, 16, 1), (64, 8, 2), (64, 16, 2)])
+def test_full_lane_variants_block_combine(n, G, R):
+    """Fixed-rows variants whose rows fill the 32 lanes (N = 32 R) add the four
+    warps' moments of a block in shared memory before the atomics; every row
+    range must be added once, also with fewer than four rows per lane."""
+    from paper_2106_02764_gb300 import inputs as I
+    L = 100e-9
+    wl = I.make_2d(f"full{n}", n, L, [I.square_pore(L, L, 0.1, x=0.35 * L, y=0.6 * L)], 2,
+                   I.circle_quadrature(16))
+    pr, ref = oracle(wl)
+    s, st = gpu(wl, "mixed", group_size=G, rows_per_thread=R)
+    assert st["group_size"] == G and st["rows_per_thread"] == R and st["kernel"] == 2
+    _check(wl, pr, ref, s, "mixed")
