@@ -31,13 +31,13 @@ __global__ void finalize_kernel(const GeomDev* geoms) {
   for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < n_cells; c += stride) {
     if (!(code[c] & CODE_SOLID)) continue;
     double t = 0.0;
+    size_t k[4];  // 2D warp kernel: skewed index of the cell in each quadrant
     if (!g.tlq) {  // per-cell accumulator (the 2D warp kernel uses the skewed one only)
       t = TL_acc[c];
       TL_acc[c] = 0.0;
     } else {  // skewed per-quadrant partials of the 2D warp kernel
       const int nx = g.nx, ny = g.ny;
       const int x = c % nx, y = c / nx;
-      size_t k[4];
       double p[4];
 #pragma unroll
       for (int q = 0; q < 4; ++q) {  // all loads first: the zeroing stores come after
@@ -55,7 +55,15 @@ __global__ void finalize_kernel(const GeomDev* geoms) {
     TL[c] = t;
     const T v = (T)(sv ? sv[c] * t : t);
     src[c] = v;
-    if (recs) obte::rec_put_src<T>(g, c, v);
+    if (recs) {
+      if (g.tlq) {  // the records of the 2D warp kernel share the skewed index
+        T* rec = reinterpret_cast<T*>(g.rec4);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) rec[k[q] * 4] = v;
+      } else {
+        obte::rec_put_src<T>(g, c, v);
+      }
+    }
   }
   T* twc = reinterpret_cast<T*>(g.twc);
   for (int f = blockIdx.x * blockDim.x + threadIdx.x; f < g.n_walls; f += stride) {
