@@ -334,7 +334,19 @@ __global__ void aa_mix_kernel(const GeomDev* geoms) {
       g.TL[i] = v;
       const T sv = (T)(g.s ? g.s[i] * v : v);
       src[i] = sv;
-      if (recs) obte::rec_put_src<T>(g, (int)i, sv);
+      if (recs && g.tlq) {  // 2D warp kernel: records at the skewed index of each quadrant
+        const int nx = g.nx, ny = g.ny;
+        const int x = (int)i % nx, y = (int)i / nx;
+        T* rec = reinterpret_cast<T*>(g.rec4);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const int ip = (q & 1) ? nx - 1 - x : x;
+          const int jp = (q & 2) ? ny - 1 - y : y;
+          rec[(((size_t)q * nx + (ip + jp) % nx) * ny + jp) * 4] = sv;
+        }
+      } else if (recs) {
+        obte::rec_put_src<T>(g, (int)i, sv);
+      }
     } else {
       const long f = i - g.n_cells;
       g.Tw[f] = v;
