@@ -746,7 +746,8 @@ struct Variant {
 
 const Variant kWarp2D_F[] = {{8, 8, true}, {8, 4, true}, {16, 4, true}, {16, 2, true},
                              {16, 1, true}, {8, 1, true},  {6, 8, true},  {4, 8, true},
-                             {4, 4, true},  {8, 2, true}};
+                             {4, 4, true},  {8, 2, true},  {8, 3, true},  {8, 5, true},
+                             {8, 6, true}};
 const Variant kWarp2D_D[] = {{4, 8, true}, {8, 4, true}, {8, 2, true}, {8, 1, true}, {2, 8, true}};
 const Variant kVariants2D_F[] = {{16, 4, false}, {8, 4, false}, {8, 8, false}, {16, 2, false},
                                  {8, 2, false}, {4, 4, false}, {16, 1, false}};
@@ -1748,7 +1749,7 @@ extern "C" int obte_solve_batch(obte_ctx* const* ctxs, int n, const obte_solve_o
     if (!r_eff[i]) use_warp = false;
   }
   // Fixed-rows classes (mixed precision without s(x)): every geometry runs the
-  // compiled fixed-R instance with the most lanes in use (R in 1, 2, 4, 8
+  // compiled fixed-R instance with the most lanes in use (R in 1 .. 6 or 8
   // dividing N with N / R <= 32 lanes); the geometries of one class share a
   // launch, the classes run side by side on forked streams, and a class whose
   // rows fill the 32 lanes adds the four warps' moments in shared memory
@@ -1757,7 +1758,7 @@ extern "C" int obte_solve_batch(obte_ctx* const* ctxs, int n, const obte_solve_o
     std::vector<int> r_cls(n, 0);
     for (int i = 0; use_cls && i < n; ++i) {
       const int ny = ctxs[i]->n[1];
-      for (int R : {1, 2, 4, 8})
+      for (int R : {1, 2, 3, 4, 5, 6, 8})
         if (ny % R == 0 && ny / R <= 32 && sweep2d_warp_exists(prec, wG, R, false, true)) {
           r_cls[i] = R;
           break;

@@ -135,10 +135,14 @@ struct WarpCfg {
 // bits, so that the eight lanes of a quarter-warp reading the same r hit
 // eight different 16-byte bank groups (the unpermuted layout puts them all
 // on the same banks).
+// Rows per lane that are not a power of two keep the plain order: for odd
+// RMAX the eight lanes already fall on eight bank groups (RMAX l mod 8 is a
+// permutation), and 6 leaves two-way conflicts.
 template <int RMAX>
 __device__ __forceinline__ int rec_slot(int lane, int r) {
+  constexpr bool POW2 = (RMAX & (RMAX - 1)) == 0;
   constexpr int SH = RMAX >= 8 ? 0 : (RMAX == 4 ? 1 : (RMAX == 2 ? 2 : 0));
-  constexpr int MSK = RMAX >= 8 ? 7 : RMAX - 1;
+  constexpr int MSK = !POW2 ? 0 : (RMAX >= 8 ? 7 : RMAX - 1);
   return lane * RMAX + (r ^ ((lane >> SH) & MSK));
 }
 

@@ -11,6 +11,9 @@
   X(float, 4, 4, false, true) \
   X(float, 8, 4, false, true) \
   X(float, 8, 2, false, true) \
+  X(float, 8, 3, false, true) \
+  X(float, 8, 5, false, true) \
+  X(float, 8, 6, false, true) \
   X(float, 16, 4, false, true) \
   X(float, 16, 2, false, true) \
   X(float, 16, 1, false, true) \

@@ -74,8 +74,8 @@ def test_batch_anderson():
 def _class_geoms():
     """Sizes that make the mixed batch run several fixed-rows classes at once:
     32 (1 row per lane, 32 lanes: moments combined per block of four warps),
-    64 (2 rows, 32 lanes: combined), 48 (2 rows, 24 lanes), 96 (4 rows,
-    24 lanes), 24 (1 row, 24 lanes)."""
+    64 (2 rows, 32 lanes: combined), 48 (2 rows, 24 lanes), 96 (3 rows,
+    32 lanes: combined), 80 (4 rows, 20 lanes)."""
     L = 100e-9
     q = I.circle_quadrature(16)
     return [
@@ -83,7 +83,7 @@ def _class_geoms():
         I.make_2d("c64", 64, L, [I.square_pore(L, L, 0.12, x=0.3 * L, y=0.6 * L)], 3, q),
         I.make_2d("c48", 48, L, [I.circle_pore(L, L, 0.15, x=0.4 * L, y=0.45 * L)], 3, q),
         I.make_2d("c96", 96, L, [I.circle_pore(L, L, 0.1)], 3, q),
-        I.make_2d("c24", 24, L, [], 3, q),
+        I.make_2d("c80", 80, L, [], 3, q),
     ]
 
 
@@ -96,7 +96,7 @@ def test_mixed_batch_fixed_row_classes():
     solvers = [Solver.from_workload(w) for w in geoms]
     opts = dict(tol=0.0, tol_TL=0.0, max_iter=3000, check_every=50)
     stats = solve_batch(solvers, precision="mixed", allow_not_converged=True, **opts)
-    assert sorted({st["rows_per_thread"] for st in stats}) == [1, 2, 4]
+    assert sorted({st["rows_per_thread"] for st in stats}) == [1, 2, 3, 4]
     for w, s in zip(geoms, solvers):
         pr, ref = oracle(w)
         assert abs(s.kappa_eff - ref.kappa) <= KAPPA_RTOL["mixed"] * ref.kappa

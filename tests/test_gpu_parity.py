@@ -221,15 +221,20 @@ def test_fma_rate_measurement():
     assert 0.0 < f64 < f32
 
 
-@pytest.mark.parametrize("n,G,R", [(32, 8, 1), (32, 16, 1), (64, 8, 2), (64, 16, 2)])
-def test_full_lane_variants_block_combine(n, G, R):
-    """Fixed-rows variants whose rows fill the 32 lanes (N = 32 R) add the four
+@pytest.mark.parametrize("ny,G,R", [(32, 8, 1), (32, 16, 1), (64, 8, 2), (64, 16, 2), (96, 8, 3),
+                                    (160, 8, 5), (192, 8, 6)])
+def test_full_lane_variants_block_combine(ny, G, R):
+    """Fixed-rows variants whose rows fill the 32 lanes (N_y = 32 R) add the four
     warps' moments of a block in shared memory before the atomics; every row
-    range must be added once, also with fewer than four rows per lane."""
+    range must be added once, also with fewer than four or a number of rows per
+    lane that is not a power of two (plain record-slot order)."""
     from paper_2106_02764_gb300 import inputs as I
-    L = 100e-9
-    wl = I.make_2d(f"full{n}", n, L, [I.square_pore(L, L, 0.1, x=0.35 * L, y=0.6 * L)], 2,
-                   I.circle_quadrature(16))
+    L, nx = 100e-9, 16
+    Ly = L * ny / nx
+    wl = I.make_2d(f"full{ny}", nx, L, [], 2, I.circle_quadrature(16))
+    wl.mask = I.pores_mask(nx, ny, L, Ly, [I.square_pore(L, Ly, 0.1, x=0.35 * L, y=0.6 * Ly)])
+    wl.shape = (nx, ny, 1)
+    wl.lengths = (L, Ly, 0.0)
     pr, ref = oracle(wl)
     s, st = gpu(wl, "mixed", group_size=G, rows_per_thread=R)
     assert st["group_size"] == G and st["rows_per_thread"] == R and st["kernel"] == 2
