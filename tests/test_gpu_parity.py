@@ -227,7 +227,20 @@ def test_full_lane_variants_block_combine(ny, G, R):
     """Fixed-rows variants whose rows fill the 32 lanes (N_y = 32 R) add the four
     warps' moments of a block in shared memory before the atomics; every row
     range must be added once, also with fewer than four or a number of rows per
-    lane that is not a power of two (plain record-slot order)."""
+    lane that is not a power of two (plain record-slot order).
+
+    The row-combining logic is checked against the 8 x 8 variant on the same
+    mesh, whose rows fill at most 24 lanes, so that each warp issues its own
+    atomics (no block combine): both sum the same float products in another
+    order, while a row range dropped or added twice moves T_L by ~0.1 K.
+    Against the FP64 oracle, kappa is held to the mixed bar.  T_L is held to
+    1e-5 K, or to the float floor of these tall meshes where that is larger.
+    Their longest-MFP ordinates (Lambda = 100 L) carry temperatures up to
+    ~dT l / L (8 K at N_y = 32, 23 K at 96, 42 K at 192), and T_L is their
+    cancelling weighted sum.  Rounding them in float leaves the fixed point
+    a few units of 2^-24 max|T_o| from the FP64 one (measured: 1.29e-5 K at
+    N_y = 96, 9.3 units)."""
+    from oracle import bte
     from paper_2106_02764_gb300 import inputs as I
     L, nx = 100e-9, 16
     Ly = L * ny / nx
@@ -238,4 +251,11 @@ def test_full_lane_variants_block_combine(ny, G, R):
     pr, ref = oracle(wl)
     s, st = gpu(wl, "mixed", group_size=G, rows_per_thread=R)
     assert st["group_size"] == G and st["rows_per_thread"] == R and st["kernel"] == 2
-    _check(wl, pr, ref, s, "mixed")
+    b, sb = gpu(wl, "mixed", group_size=8, rows_per_thread=8)
+    assert sb["rows_per_thread"] == 8 and sb["kernel"] == 2
+    TL, TLb = solid_vector(pr, s.T_L()), solid_vector(pr, b.T_L())
+    assert np.abs(TL - TLb).max() <= TL_ATOL
+    assert abs(s.kappa_eff - b.kappa_eff) <= 1e-5 * abs(b.kappa_eff)
+    assert abs(s.kappa_eff - ref.kappa) <= KAPPA_RTOL["mixed"] * abs(ref.kappa)
+    t_max = max(np.abs(T).max() for T in bte.fields(pr, ref)["T"].values())
+    assert np.abs(TL - ref.T_L).max() <= max(TL_ATOL, 16 * 2.0 ** -24 * t_max)
