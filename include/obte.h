@@ -83,8 +83,11 @@ typedef struct {
   int check_every;      /* iterations per CUDA-graph launch between host checks */
   int fourier_max_iter; /* CG iterations for the Fourier first guess (0: auto) */
   double fourier_tol;   /* relative CG residual (0: 1e-3)                      */
-  int group_size;       /* ordinates per thread block (0: autotuned)           */
-  int rows_per_thread;  /* mesh rows per thread (0: autotuned)                 */
+  int group_size;       /* ordinates per group (0: chosen by rule, or by an
+                           earlier timed choice for the same mesh shape;
+                           -1: timed choice among the compiled variants,
+                           for a batch among its launch forms)           */
+  int rows_per_thread;  /* mesh rows per thread or lane (0: chosen by rule) */
   int use_graph;        /* 1: capture check_every iterations in a CUDA graph   */
   int profile;          /* 1: time every sweep / finalize launch with CUDA
                            events recorded on the solve stream (stats below)   */
@@ -189,8 +192,13 @@ int obte_solve(obte_ctx* ctx, const obte_solve_opts* opts, obte_solve_stats* sta
 
 /* Several independent geometries (each its own context on the same device and
  * stream) iterated together: one persistent launch per iteration over a work
- * list of (geometry, ordinate group) items, the iteration captured in a CUDA
- * graph, per-geometry convergence.  stats: array of n or NULL. */
+ * list of (geometry, ordinate group) items, or in mixed precision one launch
+ * per class of geometries with the same rows per lane, the iteration captured
+ * in a CUDA graph, per-geometry convergence.  opts->group_size = -1 times the
+ * launch forms the batch accepts (class launches, persistent warp queue,
+ * persistent block kernel) over a few iterations each, keeps the fastest for
+ * this batch shape and solves with it; the timing runs overwrite the
+ * contexts' state before the solve.  stats: array of n or NULL. */
 int obte_solve_batch(obte_ctx* const* ctxs, int n, const obte_solve_opts* opts,
                      obte_solve_stats* stats);
 

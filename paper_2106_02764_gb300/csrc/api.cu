@@ -1707,6 +1707,76 @@ extern "C" int obte_kappa_grad_s(obte_ctx* ctx, double* out, size_t max_field_by
 // ---------------------------------------------------------------------------
 // batched solve: many geometries, one persistent sweep launch per iteration
 // ---------------------------------------------------------------------------
+// Timed choice of the batch form (opts.group_size = -1).  The compiled
+// variants allow up to three forms for a batch: fixed-rows class launches
+// (mixed precision without s(x), rows per lane chosen per geometry), one
+// persistent launch of the warp kernel over a cost-sorted work queue (general
+// rows per lane), and one persistent launch of the block kernel.  Each form
+// the batch accepts runs the same fixed number of iterations twice from the
+// Fourier guess (the first run pays for module loading and graph
+// instantiation); the fastest second run is kept per batch shape
+// (precision, dimension, and every geometry's cells per axis, ordinates and
+// s(x) flag) and returned in *best as explicit options.
+static std::map<std::vector<int>, std::tuple<int, int, int>>& batch_tune_cache() {
+  static std::map<std::vector<int>, std::tuple<int, int, int>> c;
+  return c;
+}
+
+static int batch_autotune(obte_ctx* const* ctxs, int n, const obte_solve_opts& op,
+                          obte_solve_opts* best) {
+  std::vector<int> key{op.precision, ctxs[0]->dim, n, op.accel};
+  for (int i = 0; i < n; ++i) {
+    const obte_ctx* c = ctxs[i];
+    key.insert(key.end(), {c->n[0], c->n[1], c->n[2], c->O, c->has_s ? 1 : 0});
+  }
+  // (group_size, rows_per_thread, kernel) of each form; 0 leaves the choice
+  // inside the form to the batch solver's rules
+  const std::tuple<int, int, int> forms[3] = {
+      std::make_tuple(0, 0, 0),  // fixed-rows classes where they apply
+      std::make_tuple(0, 8, 0),  // persistent warp queue, general rows per lane
+      std::make_tuple(0, 0, 1)}; // persistent block kernel
+  auto with = [&](const std::tuple<int, int, int>& f) {
+    obte_solve_opts o = op;
+    o.group_size = std::get<0>(f);
+    o.rows_per_thread = std::get<1>(f);
+    o.kernel = std::get<2>(f);
+    return o;
+  };
+  auto hit = batch_tune_cache().find(key);
+  if (hit != batch_tune_cache().end()) {
+    *best = with(hit->second);
+    return OBTE_OK;
+  }
+  std::vector<obte_solve_stats> st(n);
+  double best_ms = 1e300;
+  int bi = -1;
+  for (int f = 0; f < 3; ++f) {
+    obte_solve_opts t = with(forms[f]);
+    t.tol = 0.0;
+    t.tol_TL = 0.0;
+    t.min_iter = 0;
+    t.profile = 0;
+    t.check_every = std::max(1, op.check_every);
+    t.max_iter = 4 * t.check_every;
+    double ms = 0.0;
+    int rc = OBTE_OK;
+    for (int rep = 0; rep < 2 && (rc == OBTE_OK || rc == OBTE_NOT_CONVERGED); ++rep) {
+      rc = obte_solve_batch(ctxs, n, &t, st.data());
+      ms = st[0].time_iter_ms;
+    }
+    if (rc == OBTE_EINVAL) continue;  // this batch does not fit the form
+    if (rc != OBTE_OK && rc != OBTE_NOT_CONVERGED) return rc;
+    if (ms < best_ms) {
+      best_ms = ms;
+      bi = f;
+    }
+  }
+  if (bi < 0) return ctxs[0]->fail(OBTE_EINVAL, "no batch form fits every geometry");
+  batch_tune_cache()[key] = forms[bi];
+  *best = with(forms[bi]);
+  return OBTE_OK;
+}
+
 extern "C" int obte_solve_batch(obte_ctx* const* ctxs, int n, const obte_solve_opts* opts,
                                 obte_solve_stats* stats) {
   if (!ctxs || n < 1 || !ctxs[0]) return OBTE_EINVAL;
@@ -1725,6 +1795,12 @@ extern "C" int obte_solve_batch(obte_ctx* const* ctxs, int n, const obte_solve_o
   if (op.max_iter < 1) return ctx->fail(OBTE_EINVAL, "max_iter must be >= 1");
   const int prec = op.precision == OBTE_FP64 ? 0 : 1;
   cudaSetDevice(ctx->device);
+  if (op.group_size < 0) {
+    obte_solve_opts tuned;
+    const int rc = batch_autotune(ctxs, n, op, &tuned);
+    if (rc) return rc;
+    return obte_solve_batch(ctxs, n, &tuned, stats);
+  }
   // 2D: the warp kernel with per-geometry rows per lane (R <= 8 dividing ny,
   // ny / R <= 32 lanes); otherwise a block-kernel variant every geometry accepts
   bool any_s = false;

@@ -104,3 +104,33 @@ def test_mixed_batch_fixed_row_classes():
         one = Solver.from_workload(w)
         one.solve(precision="mixed", allow_not_converged=True, **opts)
         assert abs(one.kappa_eff - s.kappa_eff) <= 1e-5 * one.kappa_eff
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_batch_autotune(precision):
+    """group_size = -1 times the batch forms the compiled variants allow
+    (fixed-rows class launches, persistent warp queue, persistent block
+    kernel) for a few iterations and solves with the fastest: every geometry
+    reaches the kappa_eff of the default form, geometries 1 and 2 the oracle's
+    stored value, and a second call takes the cached choice."""
+    from paper_2106_02764_gb300.binding import Solver, solve_batch
+    from gpu_common import golden
+    geoms = I.config4(n_geom=4)  # N = 96, 64, 48, 96
+    solvers = [Solver.from_workload(w) for w in geoms]
+    opts = dict(precision=precision, tol=1e-9 if precision == "fp64" else 1e-8, max_iter=3000, check_every=16)
+    solve_batch(solvers, **opts)
+    k_default = [s.kappa_eff for s in solvers]
+    st = solve_batch(solvers, group_size=-1, **opts)
+    assert all(x["converged"] == 1 for x in st)
+    assert st[0]["kernel"] in (1, 2)
+    for s, k in zip(solvers, k_default):
+        assert abs(s.kappa_eff - k) <= 1e-5 * k, (s.kappa_eff, k)
+    for gi in (1, 2):
+        g = golden(f"4_{gi}")
+        if g is not None:
+            assert abs(solvers[gi].kappa_eff - g["kappa_eff"]) <= KAPPA_RTOL[precision] * g["kappa_eff"]
+    st2 = solve_batch(solvers, group_size=-1, **opts)
+    assert [(x["kernel"], x["group_size"], x["rows_per_thread"]) for x in st2] == \
+        [(x["kernel"], x["group_size"], x["rows_per_thread"]) for x in st]
+    print(f"batch autotune ({precision}): kernel {st[0]['kernel']}, G {st[0]['group_size']}, "
+          f"rows per lane {[x['rows_per_thread'] for x in st]}")
