@@ -259,6 +259,61 @@ def test_roll_and_mirror_symmetry():
     assert np.abs(g3[:, :, ::-1][ok] + g[ok]).max() < 1e-11
 
 
+# ---------------------------------------------------------------- p11 reciprocity
+def _cross_flux(wl, plane=0):
+    """kappa of the in-plane axis normal to the gradient: the upwinded heat
+    rate through the solid faces of the plane y' = plane (y' the other axis;
+    no jump along it), divided by dT.  With the gradient along x this is
+    kappa_yx (Q_y = kappa_yx dT / L_x over the length L_x of the plane)."""
+    pr = bte.Problem.from_workload(wl)
+    sol = bte.solve_mode_B(pr, rtol=1e-13)
+    me, od = pr.mesh, pr.ords
+    g = me.grad_axis
+    a = 1 - g
+    cells = np.nonzero((me.coords[:, a] == plane) & (me.nbr[:, a, 0] >= 0))[0]
+    img = me.nbr[cells, a, 0]
+    q = 0.0
+    for o, T in bte.fields(pr, sol)["T"].items():
+        K = od.K[o, a]
+        q += K * (T[img].sum() if K > 0 else T[cells].sum())
+    return me.h[g] * q / me.delta_T
+
+
+def _random_mask_wl(quad, with_s):
+    """8 x 8 cell with seven seeded single-cell pores: no mirror or transposition
+    symmetry, so the off-diagonal conductivities are not zero by symmetry."""
+    L = 100e-9
+    wl = I.make_2d("rand", 8, L, [], 2, quad)
+    rng = np.random.default_rng(7)
+    m = np.ones((1, 8, 8), np.uint8)
+    for _ in range(7):
+        x, y = rng.integers(1, 7, size=2)
+        m[0, y, x] = 0
+    wl.mask = m
+    if with_s:
+        wl.s = I.scattering_field(m.shape, seed=11)
+    return wl
+
+
+@pytest.mark.parametrize("with_s", [False, True])
+@pytest.mark.parametrize("quad", [I.circle_quadrature(8), I.projected_quadrature(8, 4)])
+def test_onsager_reciprocity(quad, with_s):
+    """kappa_xy = kappa_yx for an asymmetric mask and a quadrature symmetric
+    under s -> -s: the upwind transport of p is the transpose of that of -p and
+    the diffuse-wall and T_L couplings are symmetric (Sec. 2 with App. A's
+    discretisation), so the discrete conductivity tensor is symmetric.  The
+    cross flux is also the same through every section (conservation)."""
+    import copy
+    wl = _random_mask_wl(quad, with_s)
+    k_yx = _cross_flux(wl)
+    assert abs(k_yx) > 1e-3          # a real off-diagonal term (~1 % of kappa_xx)
+    assert abs(_cross_flux(wl, plane=5) - k_yx) < 1e-10 * abs(k_yx)
+    wt = copy.deepcopy(wl)
+    wt.grad_axis = 1
+    k_xy = _cross_flux(wt)
+    assert abs(k_xy - k_yx) < 1e-10 * abs(k_yx), (k_xy, k_yx)
+
+
 # ---------------------------------------------------------------- p8 folding
 def test_projected_folding():
     L = 100e-9
