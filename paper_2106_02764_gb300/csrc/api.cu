@@ -811,6 +811,22 @@ std::map<std::tuple<int, int, int, int, int, int>, Variant>& tune_cache() {
   return c;
 }
 
+// guards tune_cache and the batch-form cache: contexts may be driven from
+// different host threads
+std::mutex& tune_mutex() {
+  static std::mutex m;
+  return m;
+}
+
+// events destroyed on every return path
+struct EventPair {
+  cudaEvent_t a = nullptr, b = nullptr;
+  ~EventPair() {
+    if (a) cudaEventDestroy(a);
+    if (b) cudaEventDestroy(b);
+  }
+};
+
 }  // namespace
 
 // Work items: runs of at most G ordinates of one octant.  Items of one octant
@@ -1157,10 +1173,13 @@ static int pick_variant(obte_ctx* ctx, int precision, const obte_solve_opts& op,
                                   "rows_per_thread for this mesh");
   auto key = std::make_tuple(precision * 2 + (ctx->has_s ? 1 : 0), ctx->dim, ctx->n[0], ctx->n[1],
                              ctx->n[2], ctx->O);
-  auto it = tune_cache().find(key);
-  if (op.group_size == 0 && op.rows_per_thread == 0 && op.kernel == 0 && it != tune_cache().end()) {
-    *out = it->second;
-    return OBTE_OK;
+  if (op.group_size == 0 && op.rows_per_thread == 0 && op.kernel == 0) {
+    std::lock_guard<std::mutex> lock(tune_mutex());
+    auto it = tune_cache().find(key);
+    if (it != tune_cache().end()) {
+      *out = it->second;
+      return OBTE_OK;
+    }
   }
   // default: the first listed candidate that gives every SM at least one warp
   // of work; the lists are ordered by measured preference
@@ -1184,9 +1203,10 @@ static int autotune(obte_ctx* ctx, int precision, const obte_solve_opts& op, Var
   auto key = std::make_tuple(precision * 2 + (ctx->has_s ? 1 : 0), ctx->dim, ctx->n[0], ctx->n[1], ctx->n[2], ctx->O);
   auto cands = filtered_candidates(ctx, precision, op);
   if (cands.empty()) return ctx->fail(OBTE_EINVAL, "no compiled sweep variant fits this mesh");
-  cudaEvent_t a, b;
-  CK(cudaEventCreate(&a));
-  CK(cudaEventCreate(&b));
+  EventPair ev;
+  CK(cudaEventCreate(&ev.a));
+  CK(cudaEventCreate(&ev.b));
+  cudaEvent_t a = ev.a, b = ev.b;
   float best = 1e30f;
   Variant bv = cands[0];
   for (auto& c : cands) {
@@ -1208,9 +1228,10 @@ static int autotune(obte_ctx* ctx, int precision, const obte_solve_opts& op, Var
       bv = c;
     }
   }
-  cudaEventDestroy(a);
-  cudaEventDestroy(b);
-  tune_cache()[key] = bv;
+  {
+    std::lock_guard<std::mutex> lock(tune_mutex());
+    tune_cache()[key] = bv;
+  }
   *out = bv;
   return OBTE_OK;
 }
@@ -1227,7 +1248,6 @@ static int run_iterations(obte_ctx* ctx, const obte_solve_opts& op, int* iters, 
                           IterTiming* tm) {
   const int k = std::max(1, op.check_every);
   int* host_ctrl = nullptr;
-  CK(cudaMallocHost(&host_ctrl, 4 * sizeof(int)));
   int rc = OBTE_OK;
   // optional per-launch events: ev[3 i] before sweep i, ev[3 i + 1] after it,
   // ev[3 i + 2] after finalize i
@@ -1242,6 +1262,8 @@ static int run_iterations(obte_ctx* ctx, const obte_solve_opts& op, int* iters, 
       for (auto& e : ctx->it_events) CK(cudaEventCreate(&e));
     }
   }
+  // pinned after the event setup, whose failures return early
+  CK(cudaMallocHost(&host_ctrl, 4 * sizeof(int)));
   std::vector<cudaEvent_t>& ev = ctx->it_events;
   auto body = [&]() -> cudaError_t {
     for (int i = 0; i < k; ++i) {
@@ -1742,10 +1764,13 @@ static int batch_autotune(obte_ctx* const* ctxs, int n, const obte_solve_opts& o
     o.kernel = std::get<2>(f);
     return o;
   };
-  auto hit = batch_tune_cache().find(key);
-  if (hit != batch_tune_cache().end()) {
-    *best = with(hit->second);
-    return OBTE_OK;
+  {
+    std::lock_guard<std::mutex> lock(tune_mutex());
+    auto hit = batch_tune_cache().find(key);
+    if (hit != batch_tune_cache().end()) {
+      *best = with(hit->second);
+      return OBTE_OK;
+    }
   }
   std::vector<obte_solve_stats> st(n);
   double best_ms = 1e300;
@@ -1772,7 +1797,10 @@ static int batch_autotune(obte_ctx* const* ctxs, int n, const obte_solve_opts& o
     }
   }
   if (bi < 0) return ctxs[0]->fail(OBTE_EINVAL, "no batch form fits every geometry");
-  batch_tune_cache()[key] = forms[bi];
+  {
+    std::lock_guard<std::mutex> lock(tune_mutex());
+    batch_tune_cache()[key] = forms[bi];
+  }
   *best = with(forms[bi]);
   return OBTE_OK;
 }

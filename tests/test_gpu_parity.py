@@ -259,3 +259,18 @@ def test_full_lane_variants_block_combine(ny, G, R):
     assert abs(s.kappa_eff - ref.kappa) <= KAPPA_RTOL["mixed"] * abs(ref.kappa)
     t_max = max(np.abs(T).max() for T in bte.fields(pr, ref)["T"].values())
     assert np.abs(TL - ref.T_L).max() <= max(TL_ATOL, 16 * 2.0 ** -24 * t_max)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_single_solve_autotune(precision):
+    """group_size = -1 times every compiled variant that fits the mesh for a few
+    sweeps, solves with the fastest and caches it for the mesh shape; a later
+    solve with the default options takes the cached variant."""
+    wl, pr, ref = _ref("2d_square_16", SMALL["2d_square_16"])
+    s, st = gpu(wl, precision, group_size=-1)
+    _check(wl, pr, ref, s, precision)
+    assert st["group_size"] > 0 and st["rows_per_thread"] > 0 and st["kernel"] in (1, 2)
+    s2, st2 = gpu(wl, precision)
+    assert (st2["kernel"], st2["group_size"], st2["rows_per_thread"]) == \
+        (st["kernel"], st["group_size"], st["rows_per_thread"])
+    _check(wl, pr, ref, s2, precision)
