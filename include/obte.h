@@ -182,7 +182,9 @@ int obte_set_material_ordinates(obte_ctx* ctx, int n_ord, const double* lambda, 
 
 /* Per-cell scattering scale s_i > 0 multiplying the collision term of every
  * ordinate in cell i (not in the paper; used for sensitivities).
- * s: host double[nz][ny][nx] or NULL (all ones). */
+ * s: host double[nz][ny][nx] or NULL (all ones); pore entries are ignored.
+ * Needs create_mesh (OBTE_ESTATE otherwise); a solid entry that is not finite
+ * gives OBTE_ENONFINITE, one <= 0 OBTE_EINVAL.  Invalidates earlier results. */
 int obte_set_scattering_scale(obte_ctx* ctx, const double* s);
 
 /* Fourier first guess then source iteration to the fixed point (Algorithm 1).
@@ -201,6 +203,10 @@ int obte_solve(obte_ctx* ctx, const obte_solve_opts* opts, obte_solve_stats* sta
  * contexts' state before the solve.  stats: array of n or NULL. */
 int obte_solve_batch(obte_ctx* const* ctxs, int n, const obte_solve_opts* opts,
                      obte_solve_stats* stats);
+
+/* Getters below: ctx or out NULL gives OBTE_EINVAL; before a solve (or after
+ * an input change that invalidates it) OBTE_ESTATE.  Arrays are written in
+ * the caller's axis order (x fastest), whatever axis the gradient was on. */
 
 /* Lattice temperature of the last solve, gauged to zero mean over the solid
  * cells: host double[nz][ny][nx], NaN in pores. */
@@ -278,7 +284,14 @@ int obte_solve_fourier(obte_ctx* ctx, double tol, int max_iter, double* kappa_ou
  * utility). */
 int obte_measure_fma_rate(int precision, int device, double* flops_per_s);
 
+/* Message of the last failing call on ctx ("" if none has failed; "null
+ * context" for NULL).  The pointer stays valid until the next failing call on
+ * ctx or obte_destroy. */
 const char* obte_last_error(const obte_ctx* ctx);
+
+/* Wait for the context's stream, then release every device buffer (through
+ * the allocator's free callback where one was given), the cached iteration
+ * graph and a stream the library created.  NULL is a no-op. */
 void obte_destroy(obte_ctx* ctx);
 
 #ifdef __cplusplus
