@@ -1,0 +1,204 @@
+"""Planted mistakes in the FP64 oracle must fail its pins (CPU).
+
+Each test plants one plausible mistake in ``oracle.bte`` for the duration of
+the test (monkeypatch): a flipped jump sign, a term dropped from the E1
+diagonal, wrong E2 or E3 weights, upwinding from the downwind side, a lost
+scattering scale on the right-hand side, a wrong angular dimension in the
+flux weights.  It then checks that at least the pin that guards that part of
+the method fails.  A control test runs the same pins on the unmodified
+oracle.  The pins here recompute what they need (flux weights from the
+workload, the dense brute-force system from ``oracle.dense``) instead of
+reading it back from the oracle under test.
+"""
+import numpy as np
+import pytest
+
+from paper_2106_02764_gb300 import inputs as I
+from oracle import bte, dense
+
+L = 100e-9
+
+
+def _solve(wl):
+    pr = bte.Problem.from_workload(wl)
+    return pr, bte.solve_mode_B(pr, rtol=1e-12, maxiter=20)
+
+
+def _flux_weights(wl):
+    """K_o = d_ang kappa_m w_s p_s / Lambda_m (Sec. 2), from the workload."""
+    q = wl.quad
+    K = []
+    for k, lam in zip(wl.kappa_m, wl.lambda_m):
+        for p, w in zip(q.dirs, q.weights):
+            K.append(q.angular_dim * k * w * np.asarray(p[:3], float) / lam)
+    K = np.array(K)
+    if wl.dim == 2:
+        K[:, 2] = 0.0
+    return K
+
+
+def pin_porefree(quad):
+    """Pore-free closed form: kappa = kappa_bulk + (h/2) sum_o |K_ox| and T_L
+    linear with slope -dT/L."""
+    wl = I.make_2d("pf", 8, L, [], 3, quad)
+    pr, sol = _solve(wl)
+    K = _flux_weights(wl)
+    h = L / 8
+    expect = float(np.sum(wl.kappa_m)) + 0.5 * h * np.abs(K[:, 0]).sum()
+    x = (pr.mesh.coords[:, 0] + 0.5) * h
+    lin = -(x - x.mean()) / L
+    return abs(sol.kappa - expect) < 1e-10 * expect and np.abs(sol.T_L - lin).max() < 1e-10
+
+
+def _porous_4x4(s_seed=None):
+    wl = I.small_2d(n=4, porosity=0, n_bins=2, n_phi=8, s_seed=s_seed)
+    wl.mask = np.ones((1, 4, 4), np.uint8)
+    wl.mask[0, 1:3, 1:3] = 0
+    return wl
+
+
+def pin_dense(s_seed=None):
+    """The oracle's kappa and T_L equal the dense brute-force solve."""
+    wl = _porous_4x4(s_seed)
+    pr, sol = _solve(wl)
+    d = dense.dense_from_workload(wl)
+    return abs(sol.kappa - d["kappa"]) < 1e-9 * abs(d["kappa"]) and np.abs(sol.T_L - d["T_L"]).max() < 1e-9
+
+
+def pin_conservation():
+    """Every cell's upwinded face fluxes balance and every wall face carries
+    zero net flux (E2, E3), with K recomputed from the workload."""
+    wl = I.small_2d(n=8, porosity=0.2, n_bins=2, n_phi=8)
+    pr, sol = _solve(wl)
+    me = pr.mesh
+    K = _flux_weights(wl)
+    Ts = bte.fields(pr, sol)["T"]
+    div = np.zeros(me.nc)
+    wall_net = np.zeros(me.nw)
+    for o, T in Ts.items():
+        for a in me.axes:
+            k = K[o, a] / me.h[a]
+            for side, sgn in ((0, -1), (1, 1)):
+                kn = k * sgn
+                j = me.nbr[:, a, side]
+                f = me.wall[:, a, side]
+                if kn > 0:
+                    up = T
+                else:
+                    up = np.where(j >= 0, T[np.maximum(j, 0)] + me.jump[:, a, side],
+                                  sol.T_w[np.maximum(f, 0)])
+                div += kn * up
+                wf = f >= 0
+                np.add.at(wall_net, f[wf], (kn * up)[wf])
+    scale = np.abs(K).sum() / me.h[0]
+    return np.abs(div).max() < 1e-9 * scale and np.abs(wall_net).max() < 1e-9 * scale
+
+
+def all_pins():
+    return {
+        "porefree_circle": pin_porefree(I.circle_quadrature(8)),
+        "porefree_projected": pin_porefree(I.projected_quadrature(8, 4)),
+        "dense": pin_dense(),
+        "dense_s": pin_dense(s_seed=3),
+        "conservation": pin_conservation(),
+    }
+
+
+def test_control_all_pins_pass():
+    r = all_pins()
+    assert all(r.values()), r
+
+
+# ----------------------------------------------------------------- mutations
+def _jump_flipped(monkeypatch):
+    orig = bte.Mesh.__init__
+
+    def init(self, *a, **k):
+        orig(self, *a, **k)
+        self.jump = -self.jump
+    monkeypatch.setattr(bte.Mesh, "__init__", init)
+
+
+def _upwind_from_downwind_side(monkeypatch):
+    orig = bte.Mesh.__init__
+
+    def init(self, *a, **k):
+        orig(self, *a, **k)
+        self.nbr = self.nbr[:, :, ::-1].copy()
+        self.jump = self.jump[:, :, ::-1].copy()
+        self.wall = self.wall[:, :, ::-1].copy()
+    monkeypatch.setattr(bte.Mesh, "__init__", init)
+
+
+def _wall_outflow_off_diagonal(monkeypatch):
+    """Outgoing flux into a wall face left off the E1 diagonal."""
+    orig = bte.Transport.matrix
+
+    def matrix(self, o):
+        A = orig(self, o).tolil()
+        me, od = self.prob.mesh, self.prob.ords
+        b = self.beta(o)
+        for a in me.axes:
+            if od.p[o, a] == 0.0:
+                continue
+            out = 1 if od.p[o, a] > 0 else 0
+            for c in np.nonzero(me.wall[:, a, out] >= 0)[0]:
+                A[c, c] -= b[a]
+        return A.tocsc()
+    monkeypatch.setattr(bte.Transport, "matrix", matrix)
+
+
+def _TL_weights_without_inverse_lambda_squared(monkeypatch):
+    orig = bte.Ordinates.__init__
+
+    def init(self, kappa_m, lambda_m, dirs, weights, angular_dim, dim):
+        orig(self, kappa_m, lambda_m, dirs, weights, angular_dim, dim)
+        km = np.asarray(kappa_m, float)
+        self.a = np.repeat(km / km.sum(), self.S) * self.w
+    monkeypatch.setattr(bte.Ordinates, "__init__", init)
+
+
+def _wall_temperature_from_every_ordinate(monkeypatch):
+    orig = bte.Transport.__init__
+
+    def init(self, prob, cache=True):
+        orig(self, prob, cache)
+        me, od = prob.mesh, prob.ords
+        kn = od.K[:, me.walls[:, 1]] * me.walls[:, 2][None, :]
+        self.w_out = np.abs(kn)
+        den = self.w_out.sum(axis=0)
+        self.w_den = np.where(den > 0, den, 1.0)
+    monkeypatch.setattr(bte.Transport, "__init__", init)
+
+
+def _scattering_scale_dropped_from_rhs(monkeypatch):
+    orig = bte.Transport.rhs
+
+    def rhs(self, o, T_L, T_w, with_jump=True):
+        return orig(self, o, T_L, T_w, with_jump) - (self.prob.s - 1.0) * T_L
+    monkeypatch.setattr(bte.Transport, "rhs", rhs)
+
+
+def _flux_weights_with_planar_angular_dim(monkeypatch):
+    orig = bte.Ordinates.__init__
+
+    def init(self, kappa_m, lambda_m, dirs, weights, angular_dim, dim):
+        orig(self, kappa_m, lambda_m, dirs, weights, angular_dim, dim)
+        if angular_dim == 3:
+            self.K = self.K * (2.0 / 3.0)
+    monkeypatch.setattr(bte.Ordinates, "__init__", init)
+
+
+@pytest.mark.parametrize("plant,caught_by", [
+    (_jump_flipped, "porefree_circle"),
+    (_upwind_from_downwind_side, "porefree_circle"),
+    (_wall_outflow_off_diagonal, "conservation"),
+    (_TL_weights_without_inverse_lambda_squared, "conservation"),
+    (_wall_temperature_from_every_ordinate, "conservation"),
+    (_scattering_scale_dropped_from_rhs, "dense_s"),
+    (_flux_weights_with_planar_angular_dim, "porefree_projected"),
+])
+def test_planted_mistake_fails_a_pin(monkeypatch, plant, caught_by):
+    plant(monkeypatch)
+    r = all_pins()
+    assert not r[caught_by], r
