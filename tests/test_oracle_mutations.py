@@ -1,11 +1,14 @@
 """Planted mistakes in the FP64 oracle must fail its pins (CPU).
 
-Each test plants one plausible mistake in ``oracle.bte`` for the duration of
-the test (monkeypatch): a flipped jump sign, a term dropped from the E1
+Each test plants one plausible mistake for the duration of the test
+(monkeypatch): in ``oracle.bte`` (a flipped jump sign, a term dropped from the E1
 diagonal, wrong E2 or E3 weights, upwinding from the downwind side, a lost
 scattering scale on the right-hand side, a wrong angular dimension in the
-flux weights.  It then checks that at least the pin that guards that part of
-the method fails.  A control test runs the same pins on the unmodified
+flux weights), in ``oracle.fourier`` (jump sign, conducting pore walls, the
+hot-face flux read from the wrong side) or in ``oracle.adjoint`` (an
+untransposed solve, a lost s_i in the T_L column, wall couplings taken from
+the leaving side).  It then checks that the pin that guards that part of the
+method fails.  A control test runs the same pins on the unmodified
 oracle.  The pins here recompute what they need (flux weights from the
 workload, the dense brute-force system from ``oracle.dense``) instead of
 reading it back from the oracle under test.
@@ -202,3 +205,143 @@ def test_planted_mistake_fails_a_pin(monkeypatch, plant, caught_by):
     plant(monkeypatch)
     r = all_pins()
     assert not r[caught_by], r
+
+
+# ----------------------------------------------------------------- Fourier model (App. B)
+from oracle import adjoint, fourier  # noqa: E402
+
+
+def fourier_pins():
+    """Pore-free: kappa_fourier = kappa_bulk and T linear.  Circular pore
+    (phi = 0.1, 128^2): Eucken-Maxwell (1 - phi)/(1 + phi) within 1 %."""
+    wl = I.make_2d("pf", 16, L, [], 1, I.circle_quadrature(4))
+    me = bte.Mesh(wl.mask, wl.lengths, wl.periodic, 1.0, 2)
+    r = fourier.solve_fourier(me, 150.0)
+    x = (me.coords[:, 0] + 0.5) / 16
+    porefree = abs(r["kappa"] - 150.0) < 1e-10 and np.abs(r["T"] + (x - x.mean())).max() < 1e-12
+    wl = I.make_2d("em", 128, L, [I.circle_pore(L, L, 0.1)], 1, I.circle_quadrature(4))
+    me = bte.Mesh(wl.mask, wl.lengths, wl.periodic, 1.0, 2)
+    k = fourier.solve_fourier(me, 150.0)["kappa"] / 150.0
+    ph = wl.porosity
+    em = abs(k / ((1 - ph) / (1 + ph)) - 1) < 0.01
+    return {"fourier_porefree": porefree, "eucken_maxwell": em}
+
+
+def test_control_fourier_pins_pass():
+    r = fourier_pins()
+    assert all(r.values()), r
+
+
+def _fourier_jump_sign(monkeypatch):
+    orig = fourier.assemble
+
+    def assemble(mesh, kappa_bulk):
+        A, rhs = orig(mesh, kappa_bulk)
+        return A, -rhs
+    monkeypatch.setattr(fourier, "assemble", assemble)
+
+
+def _fourier_walls_conducting(monkeypatch):
+    """Pore faces held at T = 0 instead of adiabatic."""
+    orig = fourier.assemble
+
+    def assemble(mesh, kappa_bulk):
+        A, rhs = orig(mesh, kappa_bulk)
+        A = A.tolil()
+        for a in mesh.axes:
+            G = 150.0 / mesh.h[a] ** 2
+            for side in (0, 1):
+                for c in np.nonzero(mesh.wall[:, a, side] >= 0)[0]:
+                    A[c, c] -= G
+        return A.tocsr(), rhs
+    monkeypatch.setattr(fourier, "assemble", assemble)
+
+
+def _fourier_flux_wrong_side(monkeypatch):
+    """Hot-face flux with the jump on the cell's side instead of the image's."""
+    def kappa_fourier(mesh, kappa_bulk, T):
+        g = mesh.grad_axis
+        cells, img = mesh.hot_faces()
+        jump = mesh.jump[cells, g, 0]
+        flux = fourier._axes(kappa_bulk)[g] * (T[img] - jump - T[cells]) / mesh.h[g]
+        return mesh.lengths[g] / (mesh.delta_T * mesh.n_sec) * flux.sum()
+    monkeypatch.setattr(fourier, "kappa_fourier", kappa_fourier)
+
+
+@pytest.mark.parametrize("plant,caught_by", [
+    (_fourier_jump_sign, "fourier_porefree"),
+    (_fourier_walls_conducting, "eucken_maxwell"),
+    (_fourier_flux_wrong_side, "fourier_porefree"),
+])
+def test_planted_fourier_mistake_fails_a_pin(monkeypatch, plant, caught_by):
+    plant(monkeypatch)
+    r = fourier_pins()
+    assert not r[caught_by], r
+
+
+# ----------------------------------------------------------------- adjoint gradient
+def adjoint_pin():
+    """d kappa / d s_i against central differences of the converged kappa on
+    three seeded cells (6 x 6 cell, circular pore, s ~ U[0.5, 2])."""
+    wl = I.small_2d(n=6, porosity=0.15, n_bins=2, n_phi=8, s_seed=7)
+    pr = bte.Problem.from_workload(wl)
+    g, _ = adjoint.kappa_grad_s(pr, rtol=1e-13)
+    h = 1e-5
+    ok = True
+    for i in np.random.default_rng(5).choice(pr.mesh.nc, size=3, replace=False):
+        sp_, sm_ = pr.s.copy(), pr.s.copy()
+        sp_[i] += h
+        sm_[i] -= h
+        kp = bte.solve_mode_B(bte.Problem(pr.mesh, pr.ords, sp_), rtol=1e-14).kappa
+        km = bte.solve_mode_B(bte.Problem(pr.mesh, pr.ords, sm_), rtol=1e-14).kappa
+        ok = ok and abs((kp - km) / (2 * h) - g[i]) < 1e-5 * np.abs(g).max()
+    return ok
+
+
+def test_control_adjoint_pin_passes():
+    assert adjoint_pin()
+
+
+def _adjoint_not_transposed(monkeypatch):
+    def lam_o(self, o, mu, nu, with_q=True):
+        tr, od = self.tr, self.prob.ords
+        r = od.a[o] * mu
+        if with_q:
+            r = r + self.q[o]
+        np.add.at(r, self.wc, tr.w_out[o] / tr.w_den * nu)
+        return tr.lu(o).solve(r)
+    monkeypatch.setattr(adjoint.Adjoint, "lam_o", lam_o)
+
+
+def _adjoint_TL_column_without_s(monkeypatch):
+    orig = adjoint.Adjoint.reduced
+
+    def reduced(self, mu, nu, with_q=True, keep=False):
+        m, n, lams = orig(self, mu, nu, with_q, keep)
+        return m / self.prob.s, n, lams
+    monkeypatch.setattr(adjoint.Adjoint, "reduced", reduced)
+
+
+def _adjoint_wall_column_from_leaving_side(monkeypatch):
+    def reduced(self, mu, nu, with_q=True, keep=False):
+        me, od = self.prob.mesh, self.prob.ords
+        mu_new, nu_new = np.zeros(me.nc), np.zeros(me.nw)
+        lams = {} if keep else None
+        for o in range(od.n):
+            lam = self.lam_o(o, mu, nu, with_q)
+            mu_new += lam
+            pa = od.p[o, self.wa]
+            leave = self.ws * pa > 0
+            beta = od.lam[o] * np.abs(pa) / np.array(me.h)[self.wa]
+            nu_new += np.where(leave, beta * lam[self.wc], 0.0)
+            if keep:
+                lams[o] = lam
+        return mu_new * self.prob.s, nu_new, lams
+    monkeypatch.setattr(adjoint.Adjoint, "reduced", reduced)
+
+
+@pytest.mark.parametrize("plant", [_adjoint_not_transposed, _adjoint_TL_column_without_s,
+                                   _adjoint_wall_column_from_leaving_side])
+def test_planted_adjoint_mistake_fails_the_pin(monkeypatch, plant):
+    plant(monkeypatch)
+    assert not adjoint_pin()
