@@ -204,6 +204,17 @@ def traffic_from_profile(name):
     return e.get("dram_bytes_per_launch")
 
 
+def launches_per_solve(iterations, check_every):
+    """Kernels one mixed Anderson solve launches: the first guess (cluster CG)
+    and four start-of-solve kernels (state, wall temperatures, records,
+    Anderson history), then per launched iteration the sweep, finalize, its
+    tail and the three Anderson kernels.  Iterations go in graph chunks of
+    check_every and a solve stops inside a chunk, whose remaining iterations
+    launch and return at once."""
+    launched = -(-int(iterations) // int(check_every)) * int(check_every)
+    return 5 + 6 * launched
+
+
 def main():
     a = _args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -256,8 +267,7 @@ def main():
     clk = clocks.stop()
     total_ms = sum(step_ms)
     updates = sum(n_solid * n_ord * s["iterations"] for s in stats)
-    # CG + init + records + anderson init; per iteration sweep, finalize, 3 Anderson kernels, records
-    launches = sum(4 + 6 * s["iterations"] for s in stats)
+    launches = sum(launches_per_solve(s["iterations"], opts["check_every"]) for s in stats)
     if dist:
         t = torch.tensor([total_ms], device="cuda")
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
