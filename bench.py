@@ -204,6 +204,16 @@ def traffic_from_profile(name):
     return e.get("dram_bytes_per_launch")
 
 
+def sweep_blocks(st):
+    """Thread blocks of one sweep launch: the 2D warp kernel (kernel 2) runs
+    one ordinate group per warp, the block kernels one group per block."""
+    groups = int(st["n_groups"])
+    if st["kernel"] == 2:
+        warps = max(1, int(st["threads_per_block"]) // 32)
+        return -(-groups // warps)
+    return groups
+
+
 def launches_per_solve(iterations, check_every):
     """Kernels one mixed Anderson solve launches: the first guess (cluster CG)
     and four start-of-solve kernels (state, wall temperatures, records,
@@ -353,7 +363,8 @@ def main():
                              "iteration fits L2 and is reused within a step",
                        "group_size": stats[-1]["group_size"], "rows_per_thread": stats[-1]["rows_per_thread"],
                        "threads_per_block": stats[-1]["threads_per_block"],
-                       "blocks_per_sweep": stats[-1]["n_groups"],
+                       "groups_per_sweep": stats[-1]["n_groups"],
+                       "blocks_per_sweep": sweep_blocks(stats[-1]),
                        "parallelism": "replicas" if world > 1 else "single"},
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                          "frac": achieved / peak, "traffic": traffic_from_profile("cfg2_mixed"),

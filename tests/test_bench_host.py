@@ -15,3 +15,13 @@ def test_launch_count_matches_the_launch_list():
     assert 5 * bench.launches_per_solve(34, 8) == 1225
     assert bench.launches_per_solve(32, 8) == 5 + 6 * 32
     assert bench.launches_per_solve(1, 8) == 5 + 6 * 8
+
+
+def test_sweep_blocks_of_the_warp_kernel():
+    """Config 2: 1088 warp work items (groups padded to blocks of four of one
+    quadrant) in blocks of 128 threads give the 272-block grid of the launch
+    list; block kernels run one group per block."""
+    import bench
+    assert bench.sweep_blocks({"n_groups": 1088, "kernel": 2, "threads_per_block": 128}) == 272
+    assert bench.sweep_blocks({"n_groups": 1081, "kernel": 2, "threads_per_block": 128}) == 271
+    assert bench.sweep_blocks({"n_groups": 300, "kernel": 1, "threads_per_block": 256}) == 300
