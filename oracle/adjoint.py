@@ -30,7 +30,8 @@ from . import bte
 
 
 def kappa_functional(prob: bte.Problem):
-    """q_o: coefficients of kappa on T_o (one vector per ordinate, dict)."""
+    """q_o: coefficients of kappa on T_o (one vector per ordinate, dict): the
+    hot-contact flux of Eq. keff (App. A) as a linear functional."""
     me, od = prob.mesh, prob.ords
     g = me.grad_axis
     scale = me.lengths[g] / (me.delta_T * me.n_sec)
@@ -48,6 +49,8 @@ def kappa_functional(prob: bte.Problem):
 
 
 class Adjoint:
+    """Adjoint of the discrete system E1-E3 (module docstring): transposed
+    per-ordinate solves and GMRES on the reduced unknowns (mu, nu)."""
     def __init__(self, prob: bte.Problem, tr: bte.Transport = None):
         self.prob = prob
         self.tr = tr or bte.Transport(prob)
@@ -87,6 +90,8 @@ class Adjoint:
         return mu_new, nu_new, lams
 
     def solve(self, rtol=1e-12, restart=60, maxiter=400):
+        """GMRES on (mu, nu), the adjoint counterpart of the forward mode B
+        (Algorithm 1's fixed point solved by a Krylov method)."""
         me = self.prob.mesh
         n1, n2 = me.nc, me.nw
         b_mu, b_nu, _ = self.reduced(np.zeros(n1), np.zeros(n2), with_q=True)

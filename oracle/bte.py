@@ -125,7 +125,8 @@ class Mesh:
         self.n_sec = int(np.prod([self.n[a] for a in self.axes if a != grad_axis]))
 
     def hot_faces(self):
-        """Solid-solid faces on the periodic plane x_g = 0: (cell at x_g = 0,
+        """Solid-solid faces on the periodic plane x_g = 0 of Eq. keff (App. A):
+        (cell at x_g = 0,
         its periodic image neighbour)."""
         g = self.grad_axis
         at0 = self.coords[:, g] == 0
@@ -202,12 +203,17 @@ class Ordinates:
 
 @dataclasses.dataclass
 class Problem:
+    """Inputs of E1-E4: the voxel mesh (Sec. 6, faces of App. A), the
+    ordinates (Sec. 2 and App. A, F_ml = Lambda_m s_l) and the per-cell
+    scattering scale s_i of E1 (1 unless a sensitivity is asked for)."""
     mesh: Mesh
     ords: Ordinates
     s: np.ndarray            # scattering scale per solid cell (E1), default 1
 
     @classmethod
     def from_workload(cls, wl, s=None):
+        """Build E1-E4's inputs from a synthetic workload (mask, lengths,
+        bins and quadrature, or a general per-ordinate material of Sec. 5)."""
         mesh = Mesh(wl.mask, wl.lengths, wl.periodic, wl.delta_T, wl.dim, wl.grad_axis)
         if getattr(wl, "ords", None) is not None:
             o = wl.ords
@@ -232,6 +238,9 @@ class Transport:
     """Per-ordinate sparse matrices of E1 with their LU factors (Sec. 3)."""
 
     def __init__(self, prob: Problem, cache: bool = True):
+        """E3 weights of the thermalising walls (Sec. 2): a wall face takes the
+        flux-weighted mean sum_{K.n>0} (K_o.n) T_o / sum_{K.n>0} K_o.n of the
+        ordinates leaving its cell into it."""
         self.prob = prob
         self.cache = cache
         self._lu = {}
@@ -245,6 +254,8 @@ class Transport:
         self.w_den = np.where(den > 0, den, 1.0)
 
     def beta(self, o):
+        """Upwind face coefficients Lambda_m |p_a| A_f / V_i = Lambda_m |p_a| / h_a
+        of E1 (App. A, Eq. iter2 on a Cartesian cell)."""
         me, od = self.prob.mesh, self.prob.ords
         return np.array([od.lam[o] * abs(od.p[o, a]) / me.h[a] for a in range(3)])
 
@@ -268,6 +279,8 @@ class Transport:
         return A
 
     def lu(self, o):
+        """Sparse LU of ordinate o's E1 matrix, kept across iterations when
+        memory allows (Sec. 3: the factorisations are reused)."""
         f = self._lu.get(o)
         if f is None:
             f = spla.splu(self.matrix(o))
@@ -293,10 +306,13 @@ class Transport:
         return r
 
     def solve_ordinate(self, o, T_L, T_w, with_jump=True):
+        """One ordinate's transport solve of E1 (App. A, Eq. iter2) with T_L
+        and the wall temperatures lagged (Algorithm 1)."""
         return self.lu(o).solve(self.rhs(o, T_L, T_w, with_jump))
 
     def flux_section(self, o, T, i=0, with_jump=True):
-        """Upwinded x-flux of ordinate o through the solid faces of plane i."""
+        """Upwinded x-flux of ordinate o through the solid faces of plane i
+        (the flux of App. A's Eq. keff; equal on every plane by E2)."""
         me, od = self.prob.mesh, self.prob.ords
         g = me.grad_axis
         cells, img, jmp = me.section_faces(i)
@@ -308,7 +324,8 @@ class Transport:
         return Kx * up.sum()
 
     def sweep(self, T_L, T_w, ords=None, with_jump=True, keep_T=False, sections=False):
-        """One pass over ordinates: returns partial moments
+        """One pass of Algorithm 1's loop over ordinates (Sec. 3): solves E1 for
+        each and returns partial moments
         (sum a_o T_o, wall numerators, x=0 face flux[, per-section fluxes][, T])."""
         me, od = self.prob.mesh, self.prob.ords
         if ords is None:
@@ -337,6 +354,9 @@ class Transport:
         return out
 
     def kappa_from_phi(self, phi, with_jump=True):
+        """kappa_eff = L_x / (dT A_sec) times the upwinded flux through the plane
+        x = 0 (App. A, Eq. keff in its hot-contact form); A_sec counts the
+        cells of a full cross-section, pores included."""
         me = self.prob.mesh
         return me.lengths[me.grad_axis] / (me.delta_T * me.n_sec) * phi
 
@@ -373,6 +393,8 @@ def gauge(T_L, T_w):
 
 @dataclasses.dataclass
 class Solution:
+    """Fixed point of Algorithm 1 (Sec. 3): gauged T_L and T_w (E4), kappa_eff,
+    the iterations or GMRES matrix products taken, the kappa history."""
     T_L: np.ndarray
     T_w: np.ndarray
     kappa: float
@@ -436,7 +458,8 @@ def solve_mode_B(prob: Problem, rtol=1e-12, restart=60, maxiter=400, tr=None, x0
 
 
 def fields(prob: Problem, sol: Solution, tr=None):
-    """Ordinate fields T_o at the solution (one pass from its T_L, T_w)."""
+    """Ordinate fields T_o at the solution: one more pass of E1 (App. A)
+    from its T_L and T_w, with the E2 / E3 numerators and section fluxes."""
     tr = tr or Transport(prob)
     return tr.sweep(sol.T_L, sol.T_w, keep_T=True, sections=True)
 
@@ -461,7 +484,8 @@ def kappa_bulk_discrete(prob: Problem):
 
 
 def to_grid(prob: Problem, v, fill=np.nan):
-    """Scatter a per-solid-cell vector onto the (nz, ny, nx) grid."""
+    """Scatter a per-solid-cell vector onto the (nz, ny, nx) grid (layout only;
+    no arithmetic of the method)."""
     me = prob.mesh
     out = np.full(me.mask.shape, fill, dtype=float)
     c = me.coords

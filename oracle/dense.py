@@ -56,7 +56,9 @@ def dense_solve(mask, lengths, periodic, delta_T, dim, kappa_m, lambda_m, dirs,
     O = len(lam)
 
     def neighbour(c, a, sgn):
-        """(solid neighbour or None, jump, is_wall)."""
+        """(solid neighbour or None, jump, is_wall): the face kinds of App. A
+        (R_ij between cells, R^P_ij across the period with the jump, g_si at a
+        wall), found by walking the grid."""
         q = list(c)
         q[a] += sgn
         jump = 0.0
@@ -163,6 +165,7 @@ def dense_solve(mask, lengths, periodic, delta_T, dim, kappa_m, lambda_m, dirs,
 
 
 def dense_from_workload(wl, s=None, **kw):
+    """dense_solve on a synthetic workload's inputs (input marshalling only)."""
     q = wl.quad
     return dense_solve(wl.mask, wl.lengths, wl.periodic, wl.delta_T, wl.dim,
                        list(wl.kappa_m), list(wl.lambda_m), [list(d) for d in q.dirs],

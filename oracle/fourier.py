@@ -27,12 +27,15 @@ import scipy.sparse.linalg as spla
 
 
 def _axes(kappa_bulk):
-    """kappa along each axis: a scalar (isotropic) or three diagonal entries."""
+    """kappa along each axis: a scalar (isotropic) or three diagonal entries
+    (input handling only)."""
     return np.broadcast_to(np.asarray(kappa_bulk, float), (3,))
 
 
 def assemble(mesh, kappa_bulk):
-    """Primary-flux stiffness (negative semidefinite) and jump right-hand side.
+    """Primary-flux stiffness of App. B's finite-volume heat equation
+    (negative semidefinite; the secondary flux vanishes on Cartesian cells)
+    and the right-hand side of the periodic jump.
     kappa_bulk: scalar or the diagonal of an axis-aligned bulk tensor."""
     kap = _axes(kappa_bulk)
     rows, cols, vals = [], [], []
@@ -59,7 +62,8 @@ def assemble(mesh, kappa_bulk):
 
 
 def solve_fourier(mesh, kappa_bulk):
-    """Solve the Fourier system with the solid-cell mean of T fixed at 0."""
+    """Solve App. B's Fourier system with the solid-cell mean of T fixed at 0
+    (the gauge of E4); the first guess of Algorithm 1."""
     A, rhs = assemble(mesh, kappa_bulk)
     n = mesh.nc
     one = sp.csr_matrix(np.ones((1, n)))
@@ -70,7 +74,8 @@ def solve_fourier(mesh, kappa_bulk):
 
 
 def kappa_fourier(mesh, kappa_bulk, T):
-    """Conductive flux through the solid faces of the plane x_g = 0."""
+    """kappa_fourier: the conductive flux through the solid faces of the plane
+    x_g = 0 times L / (dT A_sec) (App. B, last equation)."""
     g = mesh.grad_axis
     cells, img = mesh.hot_faces()
     jump = mesh.jump[cells, g, 0]

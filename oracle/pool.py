@@ -21,18 +21,21 @@ _STATE = {}
 
 
 def _init(workload, s, cache):
+    """Worker set-up: the problem and its per-ordinate LU cache (Sec. 3)."""
     from . import bte
     prob = bte.Problem.from_workload(workload, s=s)
     _STATE["tr"] = bte.Transport(prob, cache=cache)
 
 
 def _work(args):
+    """One worker's share of Algorithm 1's loop over ordinates (Sec. 3)."""
     ords, T_L, T_w, with_jump = args
     tr = _STATE["tr"]
     return tr.sweep(T_L, T_w, ords=ords, with_jump=with_jump)
 
 
 def usable_cores():
+    """Cores this process may run on (the core count the baseline reports)."""
     try:
         return len(os.sched_getaffinity(0))
     except AttributeError:
