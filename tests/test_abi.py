@@ -62,3 +62,17 @@ def test_solver_refuses_without_gpu():
         pytest.skip("GPU present")
     with pytest.raises(RuntimeError):
         binding.Solver()
+
+
+def test_package_level_names():
+    """The package exposes the binding's main names and the autograd Function
+    without importing them at package import."""
+    import importlib
+    import sys
+    pkg = importlib.import_module("paper_2106_02764_gb300")
+    from paper_2106_02764_gb300 import binding
+    assert pkg.Solver is binding.Solver and pkg.solve_batch is binding.solve_batch
+    assert pkg.ObteError is binding.ObteError
+    from paper_2106_02764_gb300.autograd import KappaEff
+    assert pkg.KappaEff is KappaEff
+    assert "paper_2106_02764_gb300" in sys.modules
