@@ -473,6 +473,20 @@ def heat_flux(prob: Problem, Ts: dict):
     return J[:, :prob.mesh.dim]
 
 
+def kappa_bins(prob: Problem, sol: Solution, tr=None):
+    """Per-MFP-bin contributions to kappa_eff (the aMFP counterpart of the
+    mode-resolved conductivity, Sec. 2 and App. A): the upwinded flux of Eq.
+    keff through the plane x = 0 summed over the ordinates of each bin, times
+    L_x / (dT A_sec).  They add up to kappa_eff."""
+    tr = tr or Transport(prob)
+    od = prob.ords
+    Ts = tr.sweep(sol.T_L, sol.T_w, keep_T=True)["T"]
+    out = np.zeros(int(od.m_of.max()) + 1)
+    for o, T in Ts.items():
+        out[od.m_of[o]] += tr.flux_section(o, T, 0)
+    return tr.kappa_from_phi(out)
+
+
 def kappa_bulk_discrete(prob: Problem):
     """Pore-free closed form of the upwind scheme: the exact discrete solution
     is T_o = T_L - Lambda_m p_x a (linear T_L of slope a = -dT/L_x), whose
