@@ -49,8 +49,6 @@ the fly).  Walls and T_L are lagged as in Eq. iter2.
 from __future__ import annotations
 
 import dataclasses
-import math
-from typing import Optional
 
 import numpy as np
 import scipy.sparse as sp

@@ -1,5 +1,4 @@
 """Seeded input generators: quadrature moments, folding, masks (CPU)."""
-import math
 
 import numpy as np
 import pytest

@@ -1,6 +1,5 @@
 """Pins of the oracle's adjoint and d kappa_eff / d s(x) (CPU)."""
 import numpy as np
-import pytest
 
 from paper_2106_02764_gb300 import inputs as I
 from oracle import adjoint, bte, dense
