@@ -291,9 +291,9 @@ def test_full_lane_variants_block_combine(ny, G, R):
     that is larger (N_y = 96).  The floor is the distance between the exact
     fixed point and the FP64 fixed point of the same E1-E4 system with the
     transport coefficients rounded to float as the mixed sweep rounds them.
-    These tall cells with a Lambda = 100 L bin are sensitive to those
-    coefficients: the floor is 5.6e-6 K at N_y = 64 and 1.08e-5 K at 96,
-    against 9.5e-6 and 1.29e-5 K measured."""
+    These tall cells are sensitive to those coefficients through the 1 nm
+    bin, which carries almost all of the T_L weight: the floor is 5.6e-6 K at
+    N_y = 64 and 1.08e-5 K at 96, against 9.5e-6 and 1.29e-5 K measured."""
     from paper_2106_02764_gb300 import inputs as I
     L, nx = 100e-9, 16
     Ly = L * ny / nx
