@@ -148,7 +148,6 @@ def reference_arm(a, rank, world):
         if i >= a.warmup:
             vals.append(r)
     v = float(np.mean([r["value"] for r in vals]))
-    n_upd = sum(float(r["sample"].split(" over ")[1].split(" of ")[0]) for r in vals)
     ms = 1e3 * float(np.mean([r["seconds"] for r in vals]))
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": a.gpus,
             "steps": a.steps, "warmup": a.warmup, "ms_per_step": ms, "higher_is_better": True,
