@@ -1,0 +1,110 @@
+"""A model of the mixed-precision mode's rounding, built on the FP64 oracle
+(test helper, CPU).
+
+The mixed sweep stores App. A's upwind coefficients of E1, divided by its
+diagonal, in float: T_i = A0 s_i T_L,i + sum_a A_a u_a with A0 = fl(1 / (1 + D))
+and A_a = fl(fl(beta_a) A0).  ``RoundedCoefficients`` is the oracle's
+transport with those rounded coefficients and everything else exact, so its
+FP64 fixed point shows what the rounding of the coefficients alone does.
+``FloatTransport`` instead solves each ordinate in float32 (sparse LU) with
+the moments in FP64.
+"""
+import numpy as np
+import scipy.sparse as sp
+import scipy.sparse.linalg as spla
+
+from oracle import bte
+
+f32 = np.float32
+
+
+class RoundedCoefficients(bte.Transport):
+    """E1 with float-rounded coefficients.  ``which`` picks what is rounded:
+    "A0", "Aa" (A_x, A_y, A_z) or both; ``bins`` limits the rounding to
+    those MFP bins (None: all)."""
+
+    def __init__(self, prob, which=("A0", "Aa"), bins=None):
+        super().__init__(prob)
+        self.which = which
+        self.bins = bins
+
+    def _coef(self, o):
+        b = self.beta(o)
+        me = self.prob.mesh
+        a0 = 1.0 / (1.0 + sum(b[a] for a in me.axes))
+        rounded = self.bins is None or self.prob.ords.m_of[o] in self.bins
+        if rounded and "Aa" in self.which:
+            A = [float(f32(float(f32(b[a])) * float(f32(a0)))) for a in range(3)]
+        else:
+            A = [b[a] * a0 for a in range(3)]
+        if rounded and "A0" in self.which:
+            a0 = float(f32(a0))
+        return a0, A
+
+    def matrix(self, o):
+        me, od = self.prob.mesh, self.prob.ords
+        _, A = self._coef(o)
+        rows, cols, vals = [np.arange(me.nc)], [np.arange(me.nc)], [np.ones(me.nc)]
+        for a in me.axes:
+            if od.p[o, a] == 0.0:
+                continue
+            j = me.nbr[:, a, 0 if od.p[o, a] > 0 else 1]
+            ok = j >= 0
+            rows.append(np.nonzero(ok)[0])
+            cols.append(j[ok])
+            vals.append(np.full(ok.sum(), -A[a]))
+        return sp.csc_matrix((np.concatenate(vals), (np.concatenate(rows), np.concatenate(cols))),
+                             shape=(me.nc, me.nc))
+
+    def rhs(self, o, T_L, T_w, with_jump=True):
+        me, od = self.prob.mesh, self.prob.ords
+        a0, A = self._coef(o)
+        r = a0 * self.prob.s * T_L
+        for a in me.axes:
+            if od.p[o, a] == 0.0:
+                continue
+            side = 0 if od.p[o, a] > 0 else 1
+            if with_jump:
+                r = r + A[a] * me.jump[:, a, side]
+            wid = me.wall[:, a, side]
+            ok = wid >= 0
+            if ok.any():
+                r[ok] += A[a] * T_w[wid[ok]]
+        return r
+
+
+class FloatTransport(bte.Transport):
+    """Each ordinate's E1 solved in float32 (sparse LU of the float matrix,
+    float right-hand side); the moments stay FP64."""
+
+    def lu(self, o):
+        f = self._lu.get(o)
+        if f is None:
+            f = spla.splu(self.matrix(o).astype(np.float32))
+            self._lu[o] = f
+        return f
+
+    def solve_ordinate(self, o, T_L, T_w, with_jump=True):
+        r = self.rhs(o, T_L, T_w, with_jump).astype(np.float32)
+        return self.lu(o).solve(r).astype(np.float64)
+
+
+def float_coefficient_floor(pr, ref, which=("A0", "Aa"), bins=None):
+    """max |T_L - T_L*| between the exact fixed point ``ref`` and the FP64
+    fixed point of E1-E4 with the float-rounded coefficients."""
+    sol = bte.solve_mode_B(pr, rtol=1e-13, tr=RoundedCoefficients(pr, which, bins))
+    return float(np.abs(sol.T_L - ref.T_L).max())
+
+
+def tall_cell(ny, nx=16, length=100e-9):
+    """The tall test cell of the fixed-rows warp variants: nx x ny cells,
+    L x (L ny / nx), one square pore of porosity 0.1, two MFP bins (1 nm and
+    10 um), 16 in-plane directions."""
+    from paper_2106_02764_gb300 import inputs as I
+    Ly = length * ny / nx
+    wl = I.make_2d(f"tall{ny}", nx, length, [], 2, I.circle_quadrature(16))
+    wl.mask = I.pores_mask(nx, ny, length, Ly, [I.square_pore(length, Ly, 0.1, x=0.35 * length,
+                                                              y=0.6 * Ly)])
+    wl.shape = (nx, ny, 1)
+    wl.lengths = (length, Ly, 0.0)
+    return wl

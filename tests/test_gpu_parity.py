@@ -10,6 +10,7 @@ import numpy as np
 import pytest
 
 from gpu_common import KAPPA_RTOL, SMALL, TL_ATOL, gpu, oracle, rect_2d, solid_vector, transposed
+from mixed_model import float_coefficient_floor
 
 pytestmark = pytest.mark.gpu
 
@@ -221,59 +222,6 @@ def test_fma_rate_measurement():
     assert 0.0 < f64 < f32
 
 
-def _float_coefficient_floor(pr, ref):
-    """max |T_L - T_L*| between the exact fixed point and the FP64 fixed point
-    of E1-E4 with the mixed sweep's float transport coefficients: E1 divided by
-    its diagonal, T_i = A0 s_i T_L,i + sum_a A_a u_a with A0 = fl(1 / (1 + D))
-    and A_a = fl(fl(beta_a) A0) (App. A's upwind coefficients, rounded as the
-    mixed mode stores them), everything else exact."""
-    import scipy.sparse as sp
-    from oracle import bte
-
-    f32 = np.float32
-
-    class RoundedCoefficients(bte.Transport):
-        def _coef(self, o):
-            b = self.beta(o)
-            me = self.prob.mesh
-            a0 = float(f32(1.0 / (1.0 + sum(b[a] for a in me.axes))))
-            return a0, [float(f32(float(f32(b[a])) * a0)) for a in range(3)]
-
-        def matrix(self, o):
-            me, od = self.prob.mesh, self.prob.ords
-            _, A = self._coef(o)
-            rows, cols, vals = [np.arange(me.nc)], [np.arange(me.nc)], [np.ones(me.nc)]
-            for a in me.axes:
-                if od.p[o, a] == 0.0:
-                    continue
-                j = me.nbr[:, a, 0 if od.p[o, a] > 0 else 1]
-                ok = j >= 0
-                rows.append(np.nonzero(ok)[0])
-                cols.append(j[ok])
-                vals.append(np.full(ok.sum(), -A[a]))
-            return sp.csc_matrix((np.concatenate(vals), (np.concatenate(rows), np.concatenate(cols))),
-                                 shape=(me.nc, me.nc))
-
-        def rhs(self, o, T_L, T_w, with_jump=True):
-            me, od = self.prob.mesh, self.prob.ords
-            a0, A = self._coef(o)
-            r = a0 * self.prob.s * T_L
-            for a in me.axes:
-                if od.p[o, a] == 0.0:
-                    continue
-                side = 0 if od.p[o, a] > 0 else 1
-                if with_jump:
-                    r = r + A[a] * me.jump[:, a, side]
-                wid = me.wall[:, a, side]
-                ok = wid >= 0
-                if ok.any():
-                    r[ok] += A[a] * T_w[wid[ok]]
-            return r
-
-    sol = bte.solve_mode_B(pr, rtol=1e-13, tr=RoundedCoefficients(pr))
-    return float(np.abs(sol.T_L - ref.T_L).max())
-
-
 @pytest.mark.parametrize("ny,G,R", [(32, 8, 1), (32, 16, 1), (64, 8, 2), (64, 16, 2), (96, 8, 3),
                                     (160, 8, 5), (192, 8, 6)])
 def test_full_lane_variants_block_combine(ny, G, R):
@@ -310,7 +258,7 @@ def test_full_lane_variants_block_combine(ny, G, R):
     assert np.abs(TL - TLb).max() <= TL_ATOL
     assert abs(s.kappa_eff - b.kappa_eff) <= 1e-5 * abs(b.kappa_eff)
     assert abs(s.kappa_eff - ref.kappa) <= KAPPA_RTOL["mixed"] * abs(ref.kappa)
-    floor = _float_coefficient_floor(pr, ref)
+    floor = float_coefficient_floor(pr, ref)
     assert np.abs(TL - ref.T_L).max() <= max(TL_ATOL, 4 * floor)
 
 

@@ -1,0 +1,41 @@
+"""Where the mixed mode's T_L error comes from, on the oracle (CPU).
+
+On the tall 16 x 96 test cell (a 1 nm and a 10 um bin) the GPU's mixed
+fixed point lies 1.29e-5 K from the FP64 one.  These tests reproduce the
+separation of that error on the oracle: the float rounding of the transport
+coefficients alone gives about that much (mostly A0, and through the 1 nm
+bin), while float32 transport solves with FP64 moments stay near 1e-7 K.
+"""
+import numpy as np
+
+from mixed_model import FloatTransport, float_coefficient_floor, tall_cell
+from oracle import bte
+
+
+def _ref(ny):
+    pr = bte.Problem.from_workload(tall_cell(ny))
+    return pr, bte.solve_mode_B(pr, rtol=1e-13)
+
+
+def test_coefficient_rounding_sets_the_floor():
+    pr, ref = _ref(96)
+    both = float_coefficient_floor(pr, ref)
+    assert 5e-6 < both < 2e-5                       # GPU: 1.29e-5 K
+    assert float_coefficient_floor(pr, ref, which=("A0",)) > 0.5 * both
+    assert float_coefficient_floor(pr, ref, which=("Aa",)) < 0.3 * both
+    lam_bin = [pr.ords.lam[pr.ords.m_of == m][0] for m in range(pr.ords.M)]
+    short, long_ = int(np.argmin(lam_bin)), int(np.argmax(lam_bin))
+    assert float_coefficient_floor(pr, ref, bins=(short,)) > 0.8 * both
+    assert float_coefficient_floor(pr, ref, bins=(long_,)) < 0.05 * both
+
+
+def test_float_transport_with_fp64_moments_stays_small():
+    """Float32 solves of every ordinate, started at the exact fixed point and
+    iterated with FP64 moments, stay two orders below the coefficient floor."""
+    pr, ref = _ref(96)
+    tr = FloatTransport(pr)
+    T_L, T_w = ref.T_L.copy(), ref.T_w.copy()
+    for _ in range(60):
+        T_L, T_w, _k = bte.apply_M(tr, T_L, T_w)
+    T_L = bte.gauge(T_L, T_w)[0]
+    assert np.abs(T_L - ref.T_L).max() < 5e-7
