@@ -235,12 +235,14 @@ class Problem:
 class Transport:
     """Per-ordinate sparse matrices of E1 with their LU factors (Sec. 3)."""
 
-    def __init__(self, prob: Problem, cache: bool = True):
+    def __init__(self, prob: Problem, cache: bool = True, cache_max: int = None):
         """E3 weights of the thermalising walls (Sec. 2): a wall face takes the
         flux-weighted mean sum_{K.n>0} (K_o.n) T_o / sum_{K.n>0} K_o.n of the
-        ordinates leaving its cell into it."""
+        ordinates leaving its cell into it.  ``cache_max`` bounds the number
+        of LU factors kept (the rest are refactorised on every pass)."""
         self.prob = prob
         self.cache = cache
+        self.cache_max = cache_max
         self._lu = {}
         me, od = prob.mesh, prob.ords
         # wall-face weights of E3: numerator weights per (wall, ordinate)
@@ -282,7 +284,7 @@ class Transport:
         f = self._lu.get(o)
         if f is None:
             f = spla.splu(self.matrix(o))
-            if self.cache:
+            if self.cache and (self.cache_max is None or len(self._lu) < self.cache_max):
                 self._lu[o] = f
         return f
 
@@ -321,32 +323,42 @@ class Transport:
             up = T[cells]
         return Kx * up.sum()
 
-    def sweep(self, T_L, T_w, ords=None, with_jump=True, keep_T=False, sections=False):
+    def sweep(self, T_L, T_w, ords=None, with_jump=True, keep_T=False, sections=False,
+              flux=False):
         """One pass of Algorithm 1's loop over ordinates (Sec. 3): solves E1 for
         each and returns partial moments
-        (sum a_o T_o, wall numerators, x=0 face flux[, per-section fluxes][, T])."""
+        (sum a_o T_o, wall numerators, x=0 face flux and its split by MFP bin
+        [, per-section fluxes][, cell heat flux J = sum_o K_o T_o][, T])."""
         me, od = self.prob.mesh, self.prob.ords
         if ords is None:
             ords = range(od.n)
         TL_new = np.zeros(me.nc)
         wall_num = np.zeros(me.nw)
         phi = 0.0
+        phi_bins = np.zeros(int(od.m_of.max()) + 1)
         phis = np.zeros(me.n[me.grad_axis]) if sections else None
+        J = np.zeros((me.nc, 3)) if flux else None
         Ts = {} if keep_T else None
         wc = me.walls[:, 0]
         for o in ords:
             T = self.solve_ordinate(o, T_L, T_w, with_jump)
             TL_new += od.a[o] * T
             wall_num += self.w_out[o] * T[wc]
-            phi += self.flux_section(o, T, 0, with_jump)
+            f0 = self.flux_section(o, T, 0, with_jump)
+            phi += f0
+            phi_bins[od.m_of[o]] += f0
             if sections:
                 for i in range(len(phis)):
                     phis[i] += self.flux_section(o, T, i, with_jump)
+            if flux:
+                J += T[:, None] * od.K[o][None, :]
             if keep_T:
                 Ts[o] = T
-        out = {"TL": TL_new, "wall_num": wall_num, "phi": phi}
+        out = {"TL": TL_new, "wall_num": wall_num, "phi": phi, "phi_bins": phi_bins}
         if sections:
             out["phis"] = phis
+        if flux:
+            out["J"] = J[:, :me.dim]
         if keep_T:
             out["T"] = Ts
         return out

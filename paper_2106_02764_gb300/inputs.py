@@ -218,6 +218,20 @@ def config3() -> Workload:
                     sphere_quadrature(24, 12))
 
 
+def config3_reduced(n_bins: int = 3, n_phi: int = 8, n_mu: int = 4) -> Workload:
+    """The 64x64x32 film mesh of ``config3`` (same cylinder, walls and
+    lengths) with fewer MFP bins and directions: 3 bins x (8 azimuthal x 4
+    polar) sphere directions, 96 ordinates.  Same mesh, faces and walls as
+    the full film; the smaller ordinate set is one whose per-ordinate sparse
+    factorisations fit a host's memory, so a converged FP64 reference exists
+    for the 3D kernels at the film's own mesh size."""
+    wl = config3()
+    kappa_m, lambda_m = mfp_bins(n_bins)
+    return dataclasses.replace(
+        wl, name=f"3d-film-64x64x32-cyl-phi0.15-{n_bins}bins-{n_phi}x{n_mu}",
+        kappa_m=kappa_m, lambda_m=lambda_m, quad=sphere_quadrature(n_phi, n_mu))
+
+
 def _random_pores(rng, n, length, n_pores, porosity, min_gap_cells=2.0,
                   max_tries=2000):
     h = length / n
