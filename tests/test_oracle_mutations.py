@@ -345,3 +345,66 @@ def _adjoint_wall_column_from_leaving_side(monkeypatch):
 def test_planted_adjoint_mistake_fails_the_pin(monkeypatch, plant):
     plant(monkeypatch)
     assert not adjoint_pin()
+
+
+# ----------------------------------------------------------------- cell heat flux J (Sec. 2)
+def flux_pins():
+    """Pore-free: J = (kappa_bulk dT / L_x, 0) in every cell.  With a pore:
+    the section identity of sum_i J_x,i (test_oracle_pins) and the y mirror
+    symmetry of a centred pore."""
+    from test_oracle_pins import _flux_section_identity
+    wl = I.make_2d("pf", 8, L, [], 3, I.circle_quadrature(8))
+    pr, sol = _solve(wl)
+    J = bte.heat_flux(pr, bte.fields(pr, sol)["T"])
+    expect = float(np.sum(wl.kappa_m)) / L
+    porefree = np.abs(J[:, 0] - expect).max() < 1e-9 * expect and np.abs(J[:, 1]).max() < 1e-9 * expect
+    lhs, rhs, pr, J = _flux_section_identity(I.small_2d(n=12, porosity=0.2, n_bins=3, n_phi=8))
+    grid = np.full((12, 12), np.nan)
+    c = pr.mesh.coords
+    grid[c[:, 1], c[:, 0]] = J[:, 1]
+    mirror = np.nanmax(np.abs(grid + grid[::-1])) < 1e-9 * np.abs(J[:, 0]).max()
+    return {"flux_porefree": porefree, "flux_sections": abs(lhs - rhs) < 1e-10 * abs(lhs),
+            "flux_mirror": bool(mirror)}
+
+
+def test_control_flux_pins_pass():
+    r = flux_pins()
+    assert all(r.values()), r
+
+
+def _flux_with_unsigned_weights(monkeypatch):
+    def heat_flux(prob, Ts):
+        J = np.zeros((prob.mesh.nc, 3))
+        for o, T in Ts.items():
+            J += T[:, None] * np.abs(prob.ords.K[o])[None, :]
+        return J[:, :prob.mesh.dim]
+    monkeypatch.setattr(bte, "heat_flux", heat_flux)
+
+
+def _flux_components_swapped(monkeypatch):
+    orig = bte.heat_flux
+
+    def heat_flux(prob, Ts):
+        return orig(prob, Ts)[:, ::-1].copy()
+    monkeypatch.setattr(bte, "heat_flux", heat_flux)
+
+
+def _flux_from_reversed_ordinate(monkeypatch):
+    """Each field weighted by the flux weight of the opposite direction."""
+    def heat_flux(prob, Ts):
+        J = np.zeros((prob.mesh.nc, 3))
+        for o, T in Ts.items():
+            J -= T[:, None] * prob.ords.K[o][None, :]
+        return J[:, :prob.mesh.dim]
+    monkeypatch.setattr(bte, "heat_flux", heat_flux)
+
+
+@pytest.mark.parametrize("plant,caught_by", [
+    (_flux_with_unsigned_weights, "flux_porefree"),
+    (_flux_components_swapped, "flux_porefree"),
+    (_flux_from_reversed_ordinate, "flux_sections"),
+])
+def test_planted_flux_mistake_fails_a_pin(monkeypatch, plant, caught_by):
+    plant(monkeypatch)
+    r = flux_pins()
+    assert not r[caught_by], r

@@ -370,3 +370,74 @@ def test_kappa_bins_porefree_closed_form_and_sum():
             phi += Kx * ((T[img] + jmp).sum() if Kx > 0 else T[cells].sum())
         km = L / (1.0 * me.n_sec) * phi
         assert abs(kb[m] - km) < 1e-9 * abs(sol.kappa)
+
+
+# ---------------------------------------------------------------- heat flux J (Sec. 2)
+def _flux_weights(wl):
+    """K_o = d_ang kappa_m w_s p_s / Lambda_m (Sec. 2), from the workload."""
+    q = wl.quad
+    K = np.array([q.angular_dim * k * w * np.asarray(p[:3], float) / lam
+                  for k, lam in zip(wl.kappa_m, wl.lambda_m) for p, w in zip(q.dirs, q.weights)])
+    if wl.dim == 2:
+        K[:, 2] = 0.0
+    return K
+
+
+@pytest.mark.parametrize("quad", [I.circle_quadrature(8), I.projected_quadrature(8, 4)])
+@pytest.mark.parametrize("axis", [0, 1])
+def test_heat_flux_porefree_closed_form(quad, axis):
+    """Pore-free periodic cell: T_o = T_L - Lambda_m p_g a exactly (a the slope
+    -dT/L_g of T_L along the gradient axis g), so the cell flux
+    J_i = sum_o K_o T_o,i = -a sum_o K_o Lambda_m p_og is kappa_bulk dT / L_g
+    along g and 0 across it, in every cell: the cell-centred flux carries no
+    upwind term.  Pins heat_flux's weights, sign and component order."""
+    L = 100e-9
+    wl = I.make_2d("pf", 8, L, [], 3, quad)
+    wl.grad_axis = axis
+    pr, sol = _solve(wl, rtol=1e-13)
+    J = bte.heat_flux(pr, bte.fields(pr, sol)["T"])
+    expect = float(np.sum(wl.kappa_m)) * wl.delta_T / L
+    assert np.abs(J[:, axis] - expect).max() < 1e-11 * expect
+    assert np.abs(J[:, 1 - axis]).max() < 1e-11 * expect
+
+
+def _flux_section_identity(wl):
+    """Sum over cells of J_x against the face fluxes: every cell's x flux
+    K_ox T_o,i leaves through its downwind x face, a solid face of one of the
+    nx sections or a wall face, so
+      sum_i J_x,i = nx Phi - dT N_hot sum_{p_x>0} K_ox
+                    + sum_{+x walls} num_f - sum_{-x walls} num_f,
+    Phi the section flux (kappa_eff dT N_sec / L_x, the same through every
+    section), N_hot the solid faces of the plane x = 0 (their upwind values
+    carry +dT) and num_f the E3 numerator of wall face f, den_f T_w,f at the
+    fixed point (den_f from K recomputed here).  Returns (lhs, rhs)."""
+    pr, sol = _solve(wl, rtol=1e-13)
+    me = pr.mesh
+    J = bte.heat_flux(pr, bte.fields(pr, sol)["T"])
+    K = _flux_weights(wl)
+    nx = me.n[0]
+    phi = sol.kappa * wl.delta_T * me.n_sec / me.lengths[0]
+    n_hot = len(me.hot_faces()[0])
+    kpos = K[K[:, 0] > 0, 0].sum()
+    den = np.array([np.maximum(K[:, a] * sg, 0.0).sum() for (_c, a, sg) in me.walls])
+    num = den * sol.T_w
+    xw = me.walls[:, 1] == 0
+    plus, minus = xw & (me.walls[:, 2] > 0), xw & (me.walls[:, 2] < 0)
+    rhs = nx * phi - wl.delta_T * n_hot * kpos + num[plus].sum() - num[minus].sum()
+    return J[:, 0].sum(), rhs, pr, J
+
+
+def test_heat_flux_sections_and_mirror():
+    """Cell flux with pores: the section identity above ties sum J_x to the
+    pinned kappa and wall temperatures, and for a pore centred in the cell J
+    is mirror-symmetric in y (J_x even, J_y odd).  Pins J's x weights and
+    the sign of its y component."""
+    wl = I.small_2d(n=12, porosity=0.2, n_bins=3, n_phi=8)
+    lhs, rhs, pr, J = _flux_section_identity(wl)
+    assert abs(lhs - rhs) < 1e-10 * abs(lhs)
+    grid = np.full((2, 12, 12), np.nan)
+    c = pr.mesh.coords
+    grid[:, c[:, 1], c[:, 0]] = J.T
+    assert np.nanmax(np.abs(grid[0] - grid[0][::-1])) < 1e-9 * np.nanmax(np.abs(grid[0]))
+    assert np.nanmax(np.abs(grid[1] + grid[1][::-1])) < 1e-9 * np.nanmax(np.abs(grid[0]))
+    assert np.nanmax(np.abs(grid[1])) > 1e-3 * np.nanmax(np.abs(grid[0]))  # J_y is not trivially 0
