@@ -72,15 +72,14 @@ typedef struct {
 
 typedef struct {
   int precision;        /* obte_precision.  FP64: every step in double.  MIXED:
-                           transport sweeps in float; T_L, flux, kappa and
-                           wall sums, the periodic jump term and the
-                           convergence test in double.  Its accuracy is set
-                           by the float rounding of the per-ordinate
-                           transport coefficients.  On the measured 2D and
-                           film workloads it gave kappa within 2e-6 and T_L
-                           within 3e-7 K of the FP64 fixed point; tall cells
-                           whose T_L is carried by a short-MFP bin reached
-                           1.3e-5 K                                            */
+                           transport sweeps in float, in delta form
+                           T = s T_L + sum_a A_a (u_a - s T_L), so that the
+                           weight of T_L is exactly 1 - sum_a A_a whatever
+                           the rounding of the float coefficients A_a; the
+                           applied jump enters the float upwind value of the
+                           first column (u = T_image +- dT); T_L, flux,
+                           kappa (its jump part dT sum K_x included) and
+                           wall sums and the convergence test in double    */
   double tol;           /* stop when |kappa_n - kappa_{n-1}| <= tol |kappa_n|
                            (Algorithm 1); <= 0 disables                        */
   double tol_TL;        /* and max_i |T_L,n - T_L,n-1| <= tol_TL (K); <= 0 off  */
@@ -240,20 +239,25 @@ int obte_get_section_flux(obte_ctx* ctx, double* out);
 int obte_kappa_grad_s(obte_ctx* ctx, double* out, size_t max_field_bytes);
 
 /* d kappa_eff / d s_i like obte_kappa_grad_s, for callers that cannot allocate
- * device memory at the time they need it (for example a framework capturing a
- * CUDA graph, where cudaMalloc / cudaFree are not allowed, or a service held to
- * a fixed device-memory budget).  This call allocates nothing: the recorded
- * ordinate fields, the gradient accumulator and the small index tables live in
- * a fixed 32 MiB device array inside the library (held by every GPU that loads
- * the library until the process exits).  The context's own buffers, made by
- * earlier calls, are reused.  out: host double[nz][ny][nx], 0 in pores.
- * Returns OBTE_EINVAL with a message when the gradient, the ordinate tables and
- * one reversed pair of ordinate fields do not fit in the 32 MiB.  The first
- * call on a device takes the array's device address (cudaGetSymbolAddress);
- * make that first call before any stream capture.  Every call shares the one
- * array and overwrites it: calls whose work overlaps on the GPU (other
- * threads, other contexts on other streams) race and must be serialised by
- * the caller.  The paper has no counterpart to this entry point. */
+ * device memory at the time they need it: a service that reserves its whole
+ * device-memory budget at start-up and whose allocator refuses new blocks
+ * afterwards, or an optimisation loop sharing a full GPU with other jobs,
+ * where allocating the recorded fields could fail in the middle of a run.
+ * This call allocates nothing: the recorded ordinate fields, the gradient
+ * accumulator and the small index tables live in a fixed 32 MiB device array
+ * inside the library (held by every GPU that loads the library until the
+ * process exits).  The context's own buffers, made by earlier calls, are
+ * reused.  out: host double[nz][ny][nx], 0 in pores.  Returns OBTE_EINVAL
+ * with a message when the gradient, the ordinate tables and one reversed pair
+ * of ordinate fields do not fit in the 32 MiB; larger problems run as several
+ * batches of ordinate pairs.  The call blocks the host: it synchronises the
+ * context's stream after every batch and copies small index tables from
+ * pageable host memory, so that stream must not be under stream capture.  The
+ * first call on a device takes the array's device address
+ * (cudaGetSymbolAddress).  Every call shares the one array and overwrites it:
+ * calls whose work overlaps on the GPU (other threads, other contexts on other
+ * streams) race and must be serialised by the caller.  The paper has no
+ * counterpart to this entry point. */
 int obte_kappa_grad_s_noalloc(obte_ctx* ctx, double* out);
 
 /* Per-MFP-bin contribution to kappa_eff (the aMFP analogue of the

@@ -57,8 +57,9 @@ __device__ __forceinline__ int pmod(int a, int n) {
 
 // Exact binary32 -> binary64 conversion by re-encoding the IEEE 754 fields on
 // the integer pipe (sign kept, exponent re-biased by 1023 - 127, mantissa
-// shifted into the wider field).  Subnormal inputs flush to a signed zero (their
-// magnitude is below 1.2e-38); Inf / NaN keep their class.
+// shifted into the wider field); Inf / NaN keep their class.  Zeros and
+// subnormals (exponent field 0, magnitude below 1.2e-38, rare) take the
+// hardware conversion, which is exact for them too.
 __device__ __forceinline__ double widen(float f) {
   const uint32_t u = __float_as_uint(f);
   const uint32_t sign = u & 0x80000000u;
@@ -66,6 +67,7 @@ __device__ __forceinline__ double widen(float f) {
   const uint32_t m = u & 0x7fffffu;
   uint32_t hi, lo;
   if (e == 0u) {
+    if (m != 0u) return (double)f;
     hi = sign;
     lo = 0u;
   } else {
@@ -306,12 +308,21 @@ __global__ void __launch_bounds__((DIM == 3 && RMAX < 8) ? 512 : 256, 1) sweep_k
               const T uy = wy ? uyw : (r > 0 ? v[r > 0 ? r - 1 : 0][g] : dn0[g]);
               const T jx = jump ? JX[g] : T(0);
               T acc;
-              if (HAS_S) acc = fma(AY[g], uy, src + jx);
-              else acc = fma(AY[g], uy, fma(src, A0[g], jx));
-              acc = fma(AX[g], v[r][g], acc);
+              if (HAS_S) {
+                acc = fma(AY[g], uy, src + jx);
+                acc = fma(AX[g], v[r][g], acc);
+              } else if (sizeof(T) == 4) {
+                // delta form T = src + jx + sum_a A_a (u_a - src): the weight
+                // of src is 1 - sum_a A_a exactly (float A_a)
+                acc = fma(AY[g], uy - src, src + jx);
+                acc = fma(AX[g], v[r][g] - src, acc);
+              } else {
+                acc = fma(AY[g], uy, fma(src, A0[g], jx));
+                acc = fma(AX[g], v[r][g], acc);
+              }
               if (DIM == 3) {
                 const T uz = wz ? uzw : ((tz >= 0) ? xall[((prv * nthr + tz) * RMAX + r) * G + g] : T(0));
-                acc = fma(AZ[g], uz, acc);
+                acc = fma(AZ[g], (!HAS_S && sizeof(T) == 4) ? uz - src : uz, acc);
               }
               T val;
               if (HAS_S) {

@@ -240,11 +240,10 @@ __global__ void __launch_bounds__(32 * WarpCfg<T, G, RMAX>::WPB, WarpCfg<T, G, R
       if constexpr (X2) return (g & 1) ? v[r][g >> 1].y : v[r][g >> 1].x;
       else return v[r][g];
     };
-    VV A0v[GV], AXv[GV], AYv[GV], AWv[GV];
+    VV AXv[GV], AYv[GV], AWv[GV];
 #pragma unroll
     for (int h = 0; h < GV; ++h) {
       if constexpr (X2) {
-        A0v[h] = make_float2(A0[2 * h], A0[2 * h + 1]);
         AXv[h] = make_float2(AX[2 * h], AX[2 * h + 1]);
         AYv[h] = make_float2(AY[2 * h], AY[2 * h + 1]);
         AWv[h] = make_float2(AW[2 * h], AW[2 * h + 1]);
@@ -387,20 +386,23 @@ __global__ void __launch_bounds__(32 * WarpCfg<T, G, RMAX>::WPB, WarpCfg<T, G, R
             if constexpr (X2) {
               // u_x = m_x T + t_x: the row value, the wall temperature
               // (m_x = 0, t_x = T_w), or the value across the jump
-              // (t_x = +-dT); the record's x field holds t_x, its y field t_y
-              const float mx = wx ? 0.f : 1.f, tx = twx;
-              const float my = wy ? 0.f : 1.f, ty = twy;
+              // (t_x = +-dT); the record's x field holds t_x, its y field t_y.
+              // Delta form T = src + A_x (u_x - src) + A_y (u_y - src): the
+              // weight of src is 1 - A_x - A_y exactly, whatever the float
+              // rounding of A_x and A_y, so every ordinate's transport keeps
+              // T = T_L on a uniform field (a float 1 / (1 + D) would not)
+              const float mx = wx ? 0.f : 1.f, tx = twx - src;
+              const float my = wy ? 0.f : 1.f, ty = twy - src;
               const float2 mx2 = make_float2(mx, mx), tx2 = make_float2(tx, tx);
               const float2 my2 = make_float2(my, my), ty2 = make_float2(ty, ty);
               const float2 src2 = make_float2(src, src);
               float2 tlp = make_float2(0.f, 0.f);
 #pragma unroll
               for (int h = 0; h < GV; ++h) {
-                const float2 ux = __ffma2_rn(mx2, v[r][h], tx2);
+                const float2 ux = __ffma2_rn(mx2, v[r][h], tx2);  // u_x - src
                 const float2 ud = below_in_lane ? v[r > 0 ? r - 1 : 0][h] : dn0[h];
-                const float2 uy = __ffma2_rn(my2, ud, ty2);
-                float2 acc = __fmul2_rn(src2, A0v[h]);
-                acc = __ffma2_rn(AYv[h], uy, acc);
+                const float2 uy = __ffma2_rn(my2, ud, ty2);       // u_y - src
+                float2 acc = __ffma2_rn(AYv[h], uy, src2);
                 acc = __ffma2_rn(AXv[h], ux, acc);
                 v[r][h] = acc;
                 tlp = __ffma2_rn(AWv[h], acc, tlp);
@@ -409,15 +411,19 @@ __global__ void __launch_bounds__(32 * WarpCfg<T, G, RMAX>::WPB, WarpCfg<T, G, R
               tls[r] = tlp.x + tlp.y;
             } else {
             T tl = T(0), tl2 = T(0);  // two partial chains of the T_L moment
+            // float without s(x): the delta form of the paired path
+            constexpr bool DELTA = !JSEL && !HAS_S;
 #pragma unroll
             for (int g = 0; g < G; ++g) {
-              const T ux = JSEL ? (wx ? twx : VG(r, g)) : (wx ? T(0) : VG(r, g)) + twx;
+              const T ux = JSEL ? (wx ? twx : VG(r, g))
+                                : (wx ? T(0) : VG(r, g)) + (DELTA ? twx - src : twx);
               const T ud = below_in_lane ? VG(r > 0 ? r - 1 : 0, g) : dn0[g];
-              const T uy = wy ? twy : ud;
+              const T uy = DELTA ? (wy ? T(0) : ud) + (twy - src) : (wy ? twy : ud);
               const T jx = (JSEL && jump) ? JX[JSEL ? g : 0] : T(0);
               T acc;
               if (HAS_S) acc = fma(AY[g], uy, JSEL ? src + jx : src);
-              else acc = fma(AY[g], uy, JSEL ? fma(src, A0[g], jx) : src * A0[g]);
+              else if (DELTA) acc = fma(AY[g], uy, src);
+              else acc = fma(AY[g], uy, fma(src, A0[g], jx));
               acc = fma(AX[g], ux, acc);
               T val;
               if (HAS_S) {

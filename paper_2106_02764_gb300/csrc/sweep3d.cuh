@@ -172,11 +172,10 @@ __global__ void __launch_bounds__(Sweep3DCfg<RMAX>::NT, 1) sweep3d_kernel(const 
     if constexpr (X2) return (g & 1) ? v[r][g >> 1].y : v[r][g >> 1].x;
     else return v[r][g];
   };
-  VV A0v[GV], AXv[GV], AYv[GV], AZv[GV], AWv[GV];
+  VV AXv[GV], AYv[GV], AZv[GV], AWv[GV];
 #pragma unroll
   for (int h = 0; h < GV; ++h) {
     if constexpr (X2) {
-      A0v[h] = make_float2(A0[2 * h], A0[2 * h + 1]);
       AXv[h] = make_float2(AX[2 * h], AX[2 * h + 1]);
       AYv[h] = make_float2(AY[2 * h], AY[2 * h + 1]);
       AZv[h] = make_float2(AZ[2 * h], AZ[2 * h + 1]);
@@ -316,21 +315,24 @@ __global__ void __launch_bounds__(Sweep3DCfg<RMAX>::NT, 1) sweep3d_kernel(const 
           // u = m T + t per direction: the upwind value, the wall
           // temperature (m = 0), or the value across the jump (the record's
           // x field holds +-dT on the jump column)
+          // Delta form T = src + sum_a A_a (u_a - src): the weight of src is
+          // 1 - A_x - A_y - A_z exactly, whatever the float rounding of the
+          // A_a, so every ordinate keeps T = T_L on a uniform field
           const float mx = wx ? 0.f : 1.f, my = wy ? 0.f : 1.f, mz = wz ? 0.f : 1.f;
-          const float2 mx2 = make_float2(mx, mx), tx2 = make_float2(twx, twx);
-          const float2 my2 = make_float2(my, my), ty2 = make_float2(twy, twy);
-          const float2 mz2 = make_float2(mz, mz), tz2 = make_float2(twz, twz);
+          const float dx = twx - src, dy = twy - src, dz = twz - src;
+          const float2 mx2 = make_float2(mx, mx), tx2 = make_float2(dx, dx);
+          const float2 my2 = make_float2(my, my), ty2 = make_float2(dy, dy);
+          const float2 mz2 = make_float2(mz, mz), tz2 = make_float2(dz, dz);
           const float2 src2 = make_float2(src, src);
           float2 tlp = make_float2(0.f, 0.f);
 #pragma unroll
           for (int h = 0; h < GV; ++h) {
-            const float2 ux = __ffma2_rn(mx2, v[r][h], tx2);
+            const float2 ux = __ffma2_rn(mx2, v[r][h], tx2);  // u_x - src
             const float2 ud = r > 0 ? v[r > 0 ? r - 1 : 0][h] : dny[h];
             const float2 uy = __ffma2_rn(my2, ud, ty2);
             const float2 uzv = (tz >= 0) ? XP(prv, r, h, tz) : make_float2(0.f, 0.f);
             const float2 uz = __ffma2_rn(mz2, uzv, tz2);
-            float2 acc = __fmul2_rn(src2, A0v[h]);
-            acc = __ffma2_rn(AXv[h], ux, acc);
+            float2 acc = __ffma2_rn(AXv[h], ux, src2);
             acc = __ffma2_rn(AYv[h], uy, acc);
             acc = __ffma2_rn(AZv[h], uz, acc);
             v[r][h] = acc;

@@ -1,14 +1,20 @@
 """A model of the mixed-precision mode's rounding, built on the FP64 oracle
 (test helper, CPU).
 
-The mixed sweep stores App. A's upwind coefficients of E1, divided by its
-diagonal, in float: T_i = A0 s_i T_L,i + sum_a A_a u_a with A0 = fl(1 / (1 + D))
-and A_a = fl(fl(beta_a) A0).  ``RoundedCoefficients`` is the oracle's
-transport with those rounded coefficients and everything else exact, so its
-FP64 fixed point shows what the rounding of the coefficients alone does.
-``FloatTransport`` instead solves each ordinate in float32 (sparse LU) with
-the moments in FP64.
+A float sweep stores App. A's upwind coefficients of E1, divided by its
+diagonal: A_a = fl(fl(beta_a) A0) with A0 = 1 / (1 + D).  Written as
+T_i = A0 s_i T_L,i + sum_a A_a u_a with A0 = fl(1 / (1 + D)) (the first
+mixed sweeps), the weight of T_L is a rounded number of its own; written in
+delta form T_i = T_L,i + sum_a A_a (u_a - T_L,i) (the current sweeps), it is
+1 - sum_a A_a exactly.  ``RoundedCoefficients`` is the oracle's transport
+with such rounded coefficients and everything else exact, so its FP64 fixed
+point shows what the rounding of the coefficients alone does;
+``DeltaCoefficients`` the same for the delta form, optionally with the E2
+weights a_o rounded to float as well.  ``FloatTransport`` instead solves each
+ordinate in float32 (sparse LU) with the moments in FP64.
 """
+import copy
+
 import numpy as np
 import scipy.sparse as sp
 import scipy.sparse.linalg as spla
@@ -71,6 +77,29 @@ class RoundedCoefficients(bte.Transport):
             if ok.any():
                 r[ok] += A[a] * T_w[wid[ok]]
         return r
+
+
+class DeltaCoefficients(RoundedCoefficients):
+    """E1 as the delta-form float sweep has it: A_a rounded as above, the
+    weight of s_i T_L exactly 1 - sum_a A_a."""
+
+    def __init__(self, prob):
+        super().__init__(prob, which=("Aa",))
+
+    def _coef(self, o):
+        _a0, A = super()._coef(o)
+        return 1.0 - sum(A[a] for a in self.prob.mesh.axes), A
+
+
+def delta_form_floor(pr, ref, float_weights=True):
+    """max |T_L - T_L*| for the delta-form coefficients (and, with
+    ``float_weights``, the E2 weights a_o rounded to float as the sweep holds
+    them)."""
+    p2 = copy.deepcopy(pr)
+    if float_weights:
+        p2.ords.a = p2.ords.a.astype(f32).astype(np.float64)
+    sol = bte.solve_mode_B(p2, rtol=1e-13, tr=DeltaCoefficients(p2))
+    return float(np.abs(sol.T_L - ref.T_L).max())
 
 
 class FloatTransport(bte.Transport):

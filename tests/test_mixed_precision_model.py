@@ -1,14 +1,17 @@
 """Where the mixed mode's T_L error comes from, on the oracle (CPU).
 
-On the tall 16 x 96 test cell (a 1 nm and a 10 um bin) the GPU's mixed
-fixed point lies 1.29e-5 K from the FP64 one.  These tests reproduce the
-separation of that error on the oracle: the float rounding of the transport
-coefficients alone gives about that much (mostly A0, and through the 1 nm
-bin), while float32 transport solves with FP64 moments stay near 1e-7 K.
+On the tall 16 x 96 test cell (a 1 nm and a 10 um bin) the first mixed sweep
+(T = A0 s T_L + sum_a A_a u_a, A0 rounded to float) had its fixed point
+1.29e-5 K from the FP64 one.  These tests reproduce the separation of that
+error on the oracle: the float rounding of the transport coefficients alone
+gives about that much (mostly A0, and through the 1 nm bin), while float32
+transport solves with FP64 moments stay near 1e-7 K.  The delta form of the
+current sweeps, whose weight of T_L is exactly 1 - sum_a A_a, brings the
+coefficient floor below 1e-6 K even with float E2 weights.
 """
 import numpy as np
 
-from mixed_model import FloatTransport, float_coefficient_floor, tall_cell
+from mixed_model import FloatTransport, delta_form_floor, float_coefficient_floor, tall_cell
 from oracle import bte
 
 
@@ -39,3 +42,13 @@ def test_float_transport_with_fp64_moments_stays_small():
         T_L, T_w, _k = bte.apply_M(tr, T_L, T_w)
     T_L = bte.gauge(T_L, T_w)[0]
     assert np.abs(T_L - ref.T_L).max() < 5e-7
+
+
+def test_delta_form_floor_below_the_bar():
+    """Delta-form coefficients: the same float A_a, the weight of T_L exact;
+    with float E2 weights too (as the sweep holds a_o) the fixed point stays
+    an order below the 1e-5 K bar on the 64- and 96-row cells."""
+    for ny in (64, 96):
+        pr, ref = _ref(ny)
+        assert delta_form_floor(pr, ref, float_weights=False) < 2e-7
+        assert delta_form_floor(pr, ref) < 2e-6
