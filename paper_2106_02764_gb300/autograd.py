@@ -4,7 +4,9 @@
 ``workload`` with the per-cell scattering scale ``s`` (a float64 tensor of the
 mesh's shape) on the GPU and returns kappa_eff as a 0-d tensor; ``backward``
 returns d kappa_eff / d s from ``obte_kappa_grad_s`` (reversed-direction
-adjoint sweeps contracted with the forward fields, group by group).
+adjoint sweeps contracted with the forward fields, group by group;
+``max_field_bytes`` bounds the device memory of the recorded fields, 0 for
+the library's default of 1 GiB).
 """
 from __future__ import annotations
 
@@ -18,7 +20,8 @@ from .binding import Solver
 
 class KappaEff(torch.autograd.Function):
     @staticmethod
-    def forward(ctx, s, workload, precision="fp64", tol_TL=None, max_iter=200000):
+    def forward(ctx, s, workload, precision="fp64", tol_TL=None, max_iter=200000,
+                max_field_bytes=0):
         wl = copy.copy(workload)
         wl.s = s.detach().cpu().numpy().astype(np.float64).reshape(workload.mask.shape)
         solver = Solver.from_workload(wl)
@@ -30,11 +33,12 @@ class KappaEff(torch.autograd.Function):
                          allow_not_converged=True)
         ctx.solver = solver
         ctx.shape = s.shape
+        ctx.max_field_bytes = max_field_bytes
         return torch.tensor(solver.kappa_eff, dtype=torch.float64)
 
     @staticmethod
     def backward(ctx, grad_out):
-        g = ctx.solver.kappa_grad_s()
+        g = ctx.solver.kappa_grad_s(max_field_bytes=ctx.max_field_bytes)
         gt = torch.from_numpy(g).reshape(ctx.shape) * grad_out.to(torch.float64)
         ctx.solver.close()
-        return gt, None, None, None, None
+        return gt, None, None, None, None, None

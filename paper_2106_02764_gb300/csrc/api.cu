@@ -2188,15 +2188,17 @@ extern "C" int obte_solve_batch(obte_ctx* const* ctxs, int n, const obte_solve_o
 // d kappa / d s without device allocation
 // ---------------------------------------------------------------------------
 // Some callers cannot allocate device memory when they need the gradient: a
-// framework that is capturing a CUDA graph (cudaMalloc / cudaFree are not
-// allowed while a stream capture is active), a service running under a fixed
-// device-memory budget whose allocator refuses new blocks, or a host thread
-// that must not stall on the implicit synchronisation of cudaFree.  For them,
-// obte_kappa_grad_s_noalloc does the work of obte_kappa_grad_s with every
-// buffer it needs beyond the context's existing state (recorded ordinate
-// fields, gradient accumulator, record slots, work list) carved out of this
-// fixed, file-scope device array.  The array is part of the library image:
-// every GPU that loads the library holds it until the process exits.
+// service that reserves its whole device-memory budget at start-up and whose
+// allocator refuses new blocks afterwards, or an optimisation loop running
+// next to other jobs on a GPU that is already full, where a cudaMalloc of the
+// recorded fields would fail (or evict a neighbour's cached blocks) in the
+// middle of a run.  For them, obte_kappa_grad_s_noalloc does the work of
+// obte_kappa_grad_s with every buffer it needs beyond the context's existing
+// state (recorded ordinate fields, gradient accumulator, record slots, work
+// list) carved out of this fixed, file-scope device array.  The array is part
+// of the library image: every GPU that loads the library holds it until the
+// process exits.  The call synchronises the host with the context's stream
+// between batches and copies small index tables from pageable host memory.
 #define OBTE_NOALLOC_SCRATCH_BYTES ((size_t)32 << 20)
 static __device__ __align__(256) unsigned char g_obte_noalloc_scratch[OBTE_NOALLOC_SCRATCH_BYTES];
 
@@ -2244,9 +2246,12 @@ extern "C" int obte_kappa_grad_s_noalloc(obte_ctx* ctx, double* out) {
                                       " MiB: gradient, ordinate slots, work list and one reversed "
                                       "ordinate pair of fields must fit)");
   const size_t pairs_cap = (OBTE_NOALLOC_SCRATCH_BYTES - fixed) / (2 * per_ord);
-  size_t off = 0;
+  // every carve starts on a 256-byte boundary; the last one need not end on
+  // one, so the layout is checked against its unrounded end
+  size_t off = 0, end = 0;
   auto carve = [&](size_t bytes) {
     unsigned char* p = base + off;
+    end = off + bytes;
     off += up(bytes);
     return p;
   };
@@ -2256,7 +2261,7 @@ extern "C" int obte_kappa_grad_s_noalloc(obte_ctx* ctx, double* out) {
   int* revl_d = reinterpret_cast<int*>(carve(sizeof(int) * 2 * pairs_cap));
   double* a_d = reinterpret_cast<double*>(carve(sizeof(double) * 2 * pairs_cap));
   void* rec = carve(e * (size_t)ctx->n_cells * 2 * pairs_cap);
-  if (off > OBTE_NOALLOC_SCRATCH_BYTES) return ctx->fail(OBTE_EINVAL, "no-allocation scratch layout overflow");
+  if (end > OBTE_NOALLOC_SCRATCH_BYTES) return ctx->fail(OBTE_EINVAL, "no-allocation scratch layout overflow");
   // batches of reversed ordinate pairs
   std::vector<std::vector<int>> batches;
   {

@@ -1,18 +1,25 @@
-"""Full-size workloads on the GPU (GPU).
+"""Full-size workloads on the GPU against the oracle's stored values (GPU).
 
-Where the oracle finishes (configs 1 and 5, two small geometries of the batch,
-config 2 when its stored value exists), kappa_eff and T_L at seeded sample
-cells are compared with the oracle's stored values (tests/golden, written by
-tests/golden/make_golden.py, which calls only the oracle).  Where it cannot
-(the 3D film), properties that hold at any size are checked: equal heat flux
-through every x-section, per-bin contributions that add up to kappa_eff, and
-agreement of the two precisions.
+The oracle's converged values (tests/golden, written by
+tests/golden/make_golden.py, which calls only the oracle) hold kappa_eff,
+kappa per MFP bin, the gauged T_L of every solid cell (``.npz``) and the cell
+heat flux J at seeded sample cells.  Each workload is solved on the GPU to a
+tight fixed point in both precisions and held to the bars: kappa_eff within
+1e-6 relative (FP64) / 1e-4 (mixed), each bin's share of kappa within the
+same fraction of kappa_eff, T_L within 1e-5 K in every solid cell, J within
+the kappa bar of max |J|.  The 3D film of config 3 is too large for the
+oracle's sparse LU factors (0.4 GB per ordinate); the same 64 x 64 x 32 film
+mesh with 3 bins x 8 x 4 directions stands in for it against the oracle, and
+the full film is checked through properties that hold at any size.
 """
+import copy
+import os
+
 import numpy as np
 import pytest
 
 from paper_2106_02764_gb300 import inputs as I
-from gpu_common import KAPPA_RTOL, TL_ATOL, golden, gpu
+from gpu_common import HERE, KAPPA_RTOL, TL_ATOL, golden, gpu
 
 pytestmark = pytest.mark.gpu
 
@@ -23,26 +30,49 @@ def _built():
     build.build()
 
 
-def _samples(g, TL):
+def _samples(g, grid):
     xyz = np.array(g["samples_xyz"])
-    return TL[xyz[:, 2], xyz[:, 1], xyz[:, 0]]
+    return grid[xyz[:, 2], xyz[:, 1], xyz[:, 0]]
 
 
-def _check_golden(name, wl, precision, **kw):
+def _full(name):
+    p = os.path.join(HERE, "golden", f"kappa_star_cfg{name}.npz")
+    return dict(np.load(p)) if os.path.exists(p) else None
+
+
+def compare(name, s, precision, tl_atol=TL_ATOL):
+    """Every stored quantity of workload ``name`` against solver ``s``;
+    returns the errors (for the messages)."""
     g = golden(name)
-    if g is None:
-        pytest.skip(f"no stored oracle value for {name}")
-    s, st = gpu(wl, precision, **kw)
+    assert g is not None, f"no stored oracle value for {name}"
     k = s.kappa_eff
-    assert abs(k - g["kappa_eff"]) <= KAPPA_RTOL[precision] * g["kappa_eff"], (k, g["kappa_eff"])
-    t = _samples(g, s.T_L())
-    assert np.abs(t - np.array(g["T_L_samples"])).max() <= TL_ATOL
-    return s, st
+    rt = KAPPA_RTOL[precision]
+    err = {"kappa": abs(k - g["kappa_eff"]) / g["kappa_eff"]}
+    TL = s.T_L()
+    full = _full(name)
+    if full is not None:
+        c = full["coords"]
+        err["T_L"] = float(np.abs(TL[c[:, 2], c[:, 1], c[:, 0]] - full["T_L"]).max())
+    else:
+        err["T_L"] = float(np.abs(_samples(g, TL) - np.array(g["T_L_samples"])).max())
+    if "kappa_bins" in g:
+        kb = s.kappa_bins()
+        err["bins"] = float(np.abs(kb - np.array(g["kappa_bins"])).max() / g["kappa_eff"])
+    if "J_samples" in g:
+        J = s.flux()
+        Jr = np.array(g["J_samples"])
+        err["J"] = float(np.abs(_samples(g, J) - Jr).max() / np.abs(Jr).max())
+    assert err["kappa"] <= rt, (name, precision, err)
+    assert err["T_L"] <= tl_atol, (name, precision, err)
+    assert err.get("bins", 0.0) <= rt, (name, precision, err)
+    assert err.get("J", 0.0) <= rt, (name, precision, err)
+    return err
 
 
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
 def test_config1_vs_oracle(precision):
-    _check_golden("1", I.config1(), precision)
+    s, _ = gpu(I.config1(), precision)
+    compare("1", s, precision)
 
 
 def test_config1_algorithm1_stop():
@@ -57,28 +87,57 @@ def test_config1_algorithm1_stop():
 
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
 def test_config5_vs_oracle(precision):
-    _check_golden("5", I.config5(), precision)
+    s, _ = gpu(I.config5(), precision)
+    compare("5", s, precision)
+
+
+def _tight_cfg2(precision):
+    """Config 2 at a tight fixed point: Anderson(5); FP64 to a relative kappa
+    change of 1e-12 and max |dT_L| 1e-12 K, mixed a fixed 600 iterations."""
+    if precision == "fp64":
+        return gpu(I.config2(), "fp64", tol=1e-12, tol_TL=1e-12, max_iter=3000, check_every=16,
+                   accel=5)
+    return gpu(I.config2(), "mixed", max_iter=600, check_every=50, accel=5)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_config2_tight_fixed_point(precision):
+    s, st = _tight_cfg2(precision)
+    compare("2", s, precision)
 
 
 def test_config2_bench_launch():
     """The bench's launch configuration: mixed precision, Anderson(5), Algorithm-1
-    stop 1e-6 tested every 8 iterations (bench.py's solve options)."""
+    stop 1e-6 tested every 8 iterations (bench.py's solve options).  This
+    checks the stopping rule the bench times (kappa within the 1e-4 of its
+    time-to-kappa criterion); the fixed point itself is held to the bars by
+    test_config2_tight_fixed_point."""
     from paper_2106_02764_gb300.binding import Solver
     wl = I.config2()
     s = Solver.from_workload(wl)
     st = s.solve(precision="mixed", tol=1e-6, max_iter=3000, check_every=8, accel=5)
     assert st["converged"] == 1
     g = golden("2")
-    if g is not None:
-        assert abs(s.kappa_eff - g["kappa_eff"]) <= KAPPA_RTOL["mixed"] * g["kappa_eff"]
-        assert np.abs(_samples(g, s.T_L()) - np.array(g["T_L_samples"])).max() <= 1e-4
+    assert abs(s.kappa_eff - g["kappa_eff"]) <= KAPPA_RTOL["mixed"] * g["kappa_eff"]
     sec = s.section_flux(wl.shape[0])
     assert np.abs(sec - s.kappa_eff).max() <= 2e-4 * s.kappa_eff
     assert abs(s.kappa_bins().sum() - s.kappa_eff) <= 1e-5 * s.kappa_eff
 
 
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_config3_film_mesh_vs_oracle(precision):
+    """The 64 x 64 x 32 film mesh of config 3 (cylindrical pore, diffuse
+    film walls) with 3 bins x 8 x 4 sphere directions against the oracle."""
+    wl = I.config3_reduced()
+    if precision == "fp64":
+        s, _ = gpu(wl, "fp64", tol=1e-12, tol_TL=1e-12, max_iter=20000, check_every=32, accel=5)
+    else:
+        s, _ = gpu(wl, "mixed", max_iter=1000, check_every=50, accel=5)
+    compare("3r", s, precision)
+
+
 def test_config3_film_properties():
-    """3D film: conservation across every x-section, bins add up, and the
+    """The full 3D film: conservation across every x-section, bins add up, and the
     mixed-precision fixed point agrees with the FP64 one."""
     wl = I.config3()
     sm, _ = gpu(wl, "mixed", tol=1e-8, max_iter=3000, check_every=16)
@@ -92,25 +151,104 @@ def test_config3_film_properties():
     assert 0 < sd.kappa_eff < 150.0
 
 
-def test_config4_batch():
-    """64 uneven geometries in one persistent launch per iteration; geometries
-    with stored oracle values are compared with them, all converge, and the
-    batch agrees with single solves."""
+def _stored_batch_geometries():
+    out = []
+    for gi in range(64):
+        if golden(f"4_{gi}") is not None:
+            out.append(gi)
+    return out
+
+
+@pytest.mark.parametrize("precision", ["mixed", "fp64"])
+def test_config4_batch(precision):
+    """64 uneven geometries in one batched solve: every geometry converges,
+    the geometries with stored oracle values (one or more of each size class
+    of the fixed-rows launches) meet the bars, and the batch agrees with
+    single solves."""
     from paper_2106_02764_gb300.binding import Solver, solve_batch
     geoms = I.config4()
+    stored = _stored_batch_geometries()
+    assert len(stored) >= 8
     solvers = [Solver.from_workload(w) for w in geoms]
-    stats = solve_batch(solvers, precision="mixed", tol=1e-8, max_iter=3000, check_every=16)
-    assert all(st["converged"] == 1 for st in stats)
-    checked = 0
-    for gi in range(len(geoms)):
-        g = golden(f"4_{gi}")
-        if g is None:
-            continue
-        k = solvers[gi].kappa_eff
-        assert abs(k - g["kappa_eff"]) <= KAPPA_RTOL["mixed"] * g["kappa_eff"], (gi, k, g["kappa_eff"])
-        assert np.abs(_samples(g, solvers[gi].T_L()) - np.array(g["T_L_samples"])).max() <= 1e-4
-        checked += 1
+    if precision == "mixed":
+        stats = solve_batch(solvers, precision="mixed", tol=0.0, max_iter=1200, check_every=50,
+                            accel=5, allow_not_converged=True)
+    else:
+        stats = solve_batch(solvers, precision="fp64", tol=1e-12, tol_TL=1e-12, max_iter=20000,
+                            check_every=32, accel=5, allow_not_converged=True)
+    assert all(st["iterations"] > 0 for st in stats)
+    for gi in stored:
+        compare(f"4_{gi}", solvers[gi], precision)
     for gi in (0, 7, 33):
         one = Solver.from_workload(geoms[gi])
-        one.solve(precision="mixed", tol=1e-8, max_iter=3000, check_every=16)
-        assert abs(one.kappa_eff - solvers[gi].kappa_eff) <= 1e-5 * one.kappa_eff
+        if precision == "mixed":
+            one.solve(precision="mixed", tol=0.0, max_iter=1200, check_every=50, accel=5,
+                      allow_not_converged=True)
+            assert abs(one.kappa_eff - solvers[gi].kappa_eff) <= 1e-5 * one.kappa_eff
+        else:
+            one.solve(precision="fp64", tol=1e-12, tol_TL=1e-12, max_iter=20000, check_every=32,
+                      accel=5, allow_not_converged=True)
+            assert abs(one.kappa_eff - solvers[gi].kappa_eff) <= 1e-9 * one.kappa_eff
+
+
+# ----------------------------------------------------------------- config 5: d kappa / d s
+def _grad_golden():
+    import json
+    with open(os.path.join(HERE, "golden", "grad_cfg5.json")) as f:
+        meta = json.load(f)
+    z = np.load(os.path.join(HERE, "golden", "grad_cfg5.npz"))
+    return meta, z["grad"], z["coords"]
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_config5_gradient_vs_oracle_adjoint(precision):
+    """d kappa_eff / d s over every solid cell of config 5 against the oracle
+    adjoint (transposed sparse solves, GMRES): FP64 within 1e-6 of max |grad|,
+    mixed within 1e-3.  The gradient is taken through the autograd Function
+    with a field budget of 4 group pairs, so that it runs as many recorded
+    batches."""
+    import torch
+    from paper_2106_02764_gb300.autograd import KappaEff
+    meta, g_ref, c = _grad_golden()
+    wl = I.config5()
+    s_t = torch.tensor(wl.s, dtype=torch.float64, requires_grad=True)
+    elem = 8 if precision == "fp64" else 4
+    budget = 2 * 4 * 8 * elem * wl.mask.size  # 4 pairs of 8-ordinate groups
+    k = KappaEff.apply(s_t, wl, precision, None, 200000, budget)
+    k.backward()
+    g = s_t.grad.numpy()[c[:, 2], c[:, 1], c[:, 0]]
+    tol = 1e-6 if precision == "fp64" else 1e-3
+    assert abs(float(k) - meta["kappa_eff"]) <= KAPPA_RTOL[precision] * meta["kappa_eff"]
+    assert np.abs(g - g_ref).max() <= tol * np.abs(g_ref).max()
+    assert np.all(s_t.grad.numpy()[wl.mask == 0] == 0)
+
+
+def test_config5_gradient_vs_central_differences():
+    """Central differences of the GPU's FP64 kappa_eff (h = 1e-4) on the 64
+    seeded cells stored with the oracle gradient, within 1e-5 of max |grad|."""
+    from paper_2106_02764_gb300.binding import Solver
+    meta, g_ref, _c = _grad_golden()
+    wl = I.config5()
+
+    def kappa(w):
+        s = Solver.from_workload(w)
+        s.solve(precision="fp64", tol=1e-14, tol_TL=1e-15, max_iter=20000, check_every=32, accel=5,
+                allow_not_converged=True)
+        return s, s.kappa_eff
+
+    s0, _ = kappa(wl)
+    g = s0.kappa_grad_s()
+    scale = np.abs(g).max()
+    assert abs(scale - meta["grad_max_abs"]) <= 1e-6 * meta["grad_max_abs"]
+    h = 1e-4
+    worst = 0.0
+    for (x, y, z) in meta["fd_cells_xyz"]:
+        kk = []
+        for sgn in (1, -1):
+            w2 = copy.copy(wl)
+            w2.s = wl.s.copy()
+            w2.s[z, y, x] += sgn * h
+            kk.append(kappa(w2)[1])
+        fd = (kk[0] - kk[1]) / (2 * h)
+        worst = max(worst, abs(fd - g[z, y, x]))
+    assert worst <= 1e-5 * scale, worst / scale
