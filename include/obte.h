@@ -260,6 +260,46 @@ int obte_kappa_grad_s(obte_ctx* ctx, double* out, size_t max_field_bytes);
  * counterpart to this entry point. */
 int obte_kappa_grad_s_noalloc(obte_ctx* ctx, double* out);
 
+/* Ordinate sharding of one solve across processes or devices (Sec. 3: the
+ * paper spreads the phonon directions over MPI processes; within an iteration
+ * the ordinates are independent, and the only exchange is a sum of the FP64
+ * moment partials).  Each rank holds the whole mesh and material and sweeps
+ * the runs of ordinate groups r with r mod n_ranks == rank.  Per iteration:
+ *
+ *   obte_shard_sweep(ctx, buf)      enqueue this rank's sweep on ctx's stream
+ *                                   and write its partials to buf
+ *   (caller) sum buf over the ranks (an all-reduce; between contexts on one
+ *            device, a device add)
+ *   obte_shard_finalize(ctx, sum, &done)
+ *                                   T_L, T_w, kappa and the stopping test from
+ *                                   the summed partials; blocks until done
+ *
+ * Every rank computes the same finalisation from the same sums, so all ranks
+ * hold the same T_L, T_w and kappa and stop at the same iteration.  buf and
+ * sum are device arrays of obte_shard_partials_count(ctx) doubles on ctx's
+ * device, owned by the caller:
+ *   [0, n_cells)                    T_L numerator sum_o a_o T_o per cell (E2;
+ *                                   0 in pores), cell order x fastest
+ *   [n_cells, n_cells + n_walls)    E3 numerator of each wall face
+ *   [n_cells + n_walls]             hot-face flux through x = 0 (Eq. keff)
+ * obte_set_shard (rank in [0, n_ranks)) comes after set_material and before
+ * obte_shard_begin; n_ranks = 1 makes the context whole again.  obte_shard_begin
+ * takes the solve options like obte_solve, with group_size >= 0 (every rank
+ * must pick the same variant) and accel = 0 (the plain source iteration of
+ * Algorithm 1), and runs the Fourier first guess.  *done after
+ * obte_shard_finalize: 0 running, 1 converged, 2 max_iter reached, 3
+ * non-finite (the call then returns OBTE_ENONFINITE).  After any finalize,
+ * obte_get_T_L and obte_get_kappa_eff give the (full) current iterate;
+ * obte_get_flux, obte_get_section_flux and obte_get_kappa_bins give this
+ * rank's ordinates' share, whose sum over the ranks is the full output.  On a
+ * sharded context obte_solve, obte_solve_batch and the gradient return
+ * OBTE_ESTATE. */
+int obte_set_shard(obte_ctx* ctx, int rank, int n_ranks);
+size_t obte_shard_partials_count(const obte_ctx* ctx);
+int obte_shard_begin(obte_ctx* ctx, const obte_solve_opts* opts);
+int obte_shard_sweep(obte_ctx* ctx, double* partials);
+int obte_shard_finalize(obte_ctx* ctx, const double* partials, int* done);
+
 /* Per-MFP-bin contribution to kappa_eff (the aMFP analogue of the
  * mode-resolved conductivity, App. A): host double[n_mfp]; sums to kappa_eff.
  * Runs with obte_get_flux's extra sweep. */

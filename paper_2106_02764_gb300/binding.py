@@ -84,6 +84,11 @@ SIGNATURES = [
     ("obte_solve_fourier", C.c_int, [C.c_void_p, C.c_double, C.c_int, C.POINTER(C.c_double),
                                      C.c_void_p, C.POINTER(C.c_int)]),
     ("obte_measure_fma_rate", C.c_int, [C.c_int, C.c_int, C.POINTER(C.c_double)]),
+    ("obte_set_shard", C.c_int, [C.c_void_p, C.c_int, C.c_int]),
+    ("obte_shard_partials_count", C.c_size_t, [C.c_void_p]),
+    ("obte_shard_begin", C.c_int, [C.c_void_p, C.POINTER(SolveOpts)]),
+    ("obte_shard_sweep", C.c_int, [C.c_void_p, C.c_void_p]),
+    ("obte_shard_finalize", C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(C.c_int)]),
     ("obte_last_error", C.c_char_p, [C.c_void_p]),
     ("obte_destroy", None, [C.c_void_p]),
 ]
@@ -312,6 +317,47 @@ class Solver:
         if not (rc == OBTE_NOT_CONVERGED and allow_not_converged):
             self._check(rc)
         return {"kappa": k.value, "T": T, "iterations": it.value, "converged": rc == OBTE_OK}
+
+
+def _set_shard(self, rank, n_ranks):
+    """Sweep only this rank's share of the ordinate groups (obte_set_shard)."""
+    self._check(self.lib.obte_set_shard(self.ctx, int(rank), int(n_ranks)))
+    return self
+
+
+def _shard_partials_count(self):
+    return int(self.lib.obte_shard_partials_count(self.ctx))
+
+
+def _shard_begin(self, **kw):
+    """State and Fourier first guess of a sharded solve (obte_shard_begin)."""
+    kw.setdefault("group_size", 0)
+    kw.setdefault("accel", 0)
+    o = self.options(**kw)
+    self._check(self.lib.obte_shard_begin(self.ctx, C.byref(o)))
+    return self
+
+
+def _shard_sweep(self, partials):
+    """One sweep of this rank's ordinates; its FP64 moment partials go to
+    ``partials``, a CUDA float64 tensor of shard_partials_count() elements on
+    the solver's device (enqueued on the solver's stream)."""
+    self._check(self.lib.obte_shard_sweep(self.ctx, C.c_void_p(partials.data_ptr())))
+
+
+def _shard_finalize(self, partials):
+    """Finalise the iteration from the partials summed over the ranks;
+    returns the done code (0 running, 1 converged, 2 iteration cap)."""
+    done = C.c_int(0)
+    self._check(self.lib.obte_shard_finalize(self.ctx, C.c_void_p(partials.data_ptr()), C.byref(done)))
+    return done.value
+
+
+Solver.set_shard = _set_shard
+Solver.shard_partials_count = _shard_partials_count
+Solver.shard_begin = _shard_begin
+Solver.shard_sweep = _shard_sweep
+Solver.shard_finalize = _shard_finalize
 
 
 def _grad_noalloc(self):

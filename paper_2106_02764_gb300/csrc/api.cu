@@ -119,6 +119,11 @@ struct obte_ctx {
     it_events.clear();
   }
   obte_solve_opts last_opts{};
+  // ordinate sharding: this context sweeps the runs of work items r with
+  // r mod shard_n == shard_rank (obte_set_shard); shard_active after
+  // obte_shard_begin
+  int shard_rank = 0, shard_n = 1;
+  bool shard_active = false;
 
   void* dalloc(size_t bytes) {
     if (bytes == 0) bytes = 16;
@@ -1060,6 +1065,16 @@ static int prepare_state(obte_ctx* ctx, int precision, int G, int R, bool warp, 
                        ? 4
                        : 1;
   build_items(ctx, 0, G, items, &ord_d0, ctx->items_pad);
+  if (ctx->shard_n > 1) {
+    // runs of items_pad items (one start column, one octant) go round-robin
+    // to the ranks; every rank keeps the full ordinate tables
+    std::vector<WorkItem> mine;
+    for (size_t k = 0; k < items.size(); ++k)
+      if ((int)((k / ctx->items_pad) % ctx->shard_n) == ctx->shard_rank) mine.push_back(items[k]);
+    if (mine.empty())  // one run of empty items: the rank sweeps nothing
+      for (int k = 0; k < ctx->items_pad; ++k) mine.push_back({0, items[0].octant, items[0].o0, 0, items[0].d0});
+    items.swap(mine);
+  }
   const bool same = ctx->items_d && items.size() == ctx->items_h.size() &&
                     std::memcmp(items.data(), ctx->items_h.data(), sizeof(WorkItem) * items.size()) == 0;
   if (!same) {
@@ -1347,6 +1362,8 @@ static int run_iterations(obte_ctx* ctx, const obte_solve_opts& op, int* iters, 
 extern "C" int obte_solve(obte_ctx* ctx, const obte_solve_opts* opts, obte_solve_stats* stats) {
   if (!ctx) return OBTE_EINVAL;
   if (!ctx->has_mesh || !ctx->has_material) return ctx->fail(OBTE_ESTATE, "create_mesh and set_material first");
+  if (ctx->shard_n > 1)
+    return ctx->fail(OBTE_ESTATE, "context holds one shard of the ordinates: iterate with obte_shard_*");
   obte_solve_opts op;
   if (opts) op = *opts;
   else obte_default_opts(&op);
@@ -1422,6 +1439,86 @@ extern "C" int obte_solve(obte_ctx* ctx, const obte_solve_opts* opts, obte_solve
   }
   if (done == 3) return ctx->fail(OBTE_ENONFINITE, "non-finite value in the iterate");
   if (done != 1) return ctx->fail(OBTE_NOT_CONVERGED, "stopping test not met within max_iter");
+  return OBTE_OK;
+}
+
+// ---------------------------------------------------------------------------
+// ordinate sharding of one solve (Sec. 3: directions spread over processors)
+// ---------------------------------------------------------------------------
+extern "C" int obte_set_shard(obte_ctx* ctx, int rank, int n_ranks) {
+  if (!ctx) return OBTE_EINVAL;
+  if (n_ranks < 1 || rank < 0 || rank >= n_ranks) return ctx->fail(OBTE_EINVAL, "need 0 <= rank < n_ranks");
+  ctx->drop_graph();
+  ctx->shard_rank = rank;
+  ctx->shard_n = n_ranks;
+  ctx->shard_active = false;
+  ctx->solved = false;
+  ctx->precision = -1;  // work items are rebuilt by the next begin
+  return OBTE_OK;
+}
+
+extern "C" size_t obte_shard_partials_count(const obte_ctx* ctx) {
+  if (!ctx || !ctx->has_mesh) return 0;
+  return (size_t)ctx->n_cells + (size_t)ctx->n_walls + 1;
+}
+
+extern "C" int obte_shard_begin(obte_ctx* ctx, const obte_solve_opts* opts) {
+  if (!ctx) return OBTE_EINVAL;
+  if (!ctx->has_mesh || !ctx->has_material) return ctx->fail(OBTE_ESTATE, "create_mesh and set_material first");
+  obte_solve_opts op;
+  if (opts) op = *opts;
+  else obte_default_opts(&op);
+  if (op.precision != OBTE_FP64 && op.precision != OBTE_MIXED) return ctx->fail(OBTE_EINVAL, "bad precision");
+  if (op.max_iter < 1) return ctx->fail(OBTE_EINVAL, "max_iter must be >= 1");
+  if (op.group_size < 0) return ctx->fail(OBTE_EINVAL, "a sharded solve needs a fixed variant (group_size >= 0)");
+  if (op.accel != 0) return ctx->fail(OBTE_EINVAL, "a sharded solve runs the plain source iteration (accel = 0)");
+  CK(cudaSetDevice(ctx->device));
+  const int prec = op.precision == OBTE_FP64 ? 0 : 1;
+  Variant v;
+  int rc = pick_variant(ctx, prec, op, &v);
+  if (rc) return rc;
+  rc = prepare_state(ctx, prec, v.G, v.R, v.warp, op.max_iter, op, v.k3d);
+  if (rc) return rc;
+  ctx->flux_done = false;
+  rc = init_from_fourier(ctx, op, nullptr);
+  if (rc) return rc;
+  CK(cudaStreamSynchronize(ctx->stream));
+  ctx->last_opts = op;
+  ctx->last_iters = 0;
+  ctx->kappa = NAN;
+  ctx->solved = false;
+  ctx->shard_active = true;
+  return OBTE_OK;
+}
+
+extern "C" int obte_shard_sweep(obte_ctx* ctx, double* partials) {
+  if (!ctx || !partials) return OBTE_EINVAL;
+  if (!ctx->shard_active) return ctx->fail(OBTE_ESTATE, "obte_shard_begin first");
+  CK(cudaSetDevice(ctx->device));
+  CK(sweep_once(ctx, 0));
+  CK(launch_shard_export(ctx->gd, partials, finalize_blocks(ctx->n_cells), ctx->stream));
+  return OBTE_OK;
+}
+
+extern "C" int obte_shard_finalize(obte_ctx* ctx, const double* partials, int* done) {
+  if (!ctx || !partials) return OBTE_EINVAL;
+  if (!ctx->shard_active) return ctx->fail(OBTE_ESTATE, "obte_shard_begin first");
+  CK(cudaSetDevice(ctx->device));
+  CK(launch_shard_import(ctx->gd, partials, finalize_blocks(ctx->n_cells), ctx->stream));
+  CK(launch_finalize(ctx->gd, 1, ctx->precision, finalize_blocks(ctx->n_cells), ctx->stream));
+  int ctrl[4];
+  CK(cudaMemcpyAsync(ctrl, ctx->ctrl, sizeof(ctrl), cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  const int iters = ctrl[1];
+  if (iters >= 1 && iters <= kMaxHist) {
+    double k = NAN;
+    CK(cudaMemcpy(&k, ctx->hist + (iters - 1), sizeof(double), cudaMemcpyDeviceToHost));
+    ctx->kappa = k;
+  }
+  ctx->last_iters = iters;
+  ctx->solved = true;
+  if (done) *done = ctrl[0];
+  if (ctrl[0] == 3) return ctx->fail(OBTE_ENONFINITE, "non-finite value in the iterate");
   return OBTE_OK;
 }
 
@@ -1609,6 +1706,7 @@ extern "C" int obte_solve_fourier(obte_ctx* ctx, double tol, int max_iter, doubl
 extern "C" int obte_kappa_grad_s(obte_ctx* ctx, double* out, size_t max_field_bytes) {
   if (!ctx || !out) return OBTE_EINVAL;
   if (!ctx->solved) return ctx->fail(OBTE_ESTATE, "solve first");
+  if (ctx->shard_n > 1) return ctx->fail(OBTE_ESTATE, "gradient of a sharded solve is not available");
   cudaSetDevice(ctx->device);
   const int O = ctx->O;
   // reversed ordinate of every sorted ordinate (same bin, opposite direction)
@@ -1815,6 +1913,7 @@ extern "C" int obte_solve_batch(obte_ctx* const* ctxs, int n, const obte_solve_o
       return ctx->fail(OBTE_ESTATE, "every context needs create_mesh and set_material");
     if (ctxs[i]->device != ctx->device || ctxs[i]->dim != ctx->dim)
       return ctx->fail(OBTE_EINVAL, "batch contexts must share device and dimension");
+    if (ctxs[i]->shard_n > 1) return ctx->fail(OBTE_ESTATE, "sharded contexts cannot join a batch");
   }
   obte_solve_opts op;
   if (opts) op = *opts;
@@ -2225,6 +2324,7 @@ static cudaError_t noalloc_scratch(int device, unsigned char** out) {
 extern "C" int obte_kappa_grad_s_noalloc(obte_ctx* ctx, double* out) {
   if (!ctx || !out) return OBTE_EINVAL;
   if (!ctx->solved) return ctx->fail(OBTE_ESTATE, "solve first");
+  if (ctx->shard_n > 1) return ctx->fail(OBTE_ESTATE, "gradient of a sharded solve is not available");
   CK(cudaSetDevice(ctx->device));
   unsigned char* base = nullptr;
   CK(noalloc_scratch(ctx->device, &base));

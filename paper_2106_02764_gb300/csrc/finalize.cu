@@ -281,7 +281,84 @@ __global__ void build_records_kernel(const GeomDev* geoms) {
   }
 }
 
+// Ordinate sharding (Sec. 3: directions spread over processors; the only
+// exchange per iteration is a sum of the moment partials).  Export: the
+// moment partials of the sweep that just ran over this context's share of the
+// ordinates, in one compact FP64 vector
+//   out[c]                   T_L numerator sum_o a_o T_o of cell c (pores 0)
+//   out[n_cells + f]         E3 numerator of wall face f
+//   out[n_cells + n_walls]   hot-face flux
+// with the accumulators zeroed behind them.  Import: the summed vector back
+// into the accumulators (the T_L numerator into quadrant 0 of the skewed
+// partials when the 2D warp kernel keeps them there), ready for the
+// finalisation.  One geometry; grid-stride loops.
+__device__ __forceinline__ size_t skew_index(const GeomDev& g, int c, int q) {
+  const int x = c % g.nx, y = c / g.nx;
+  const int ip = (q & 1) ? g.nx - 1 - x : x;
+  const int jp = (q & 2) ? g.ny - 1 - y : y;
+  return ((size_t)q * g.nx + (ip + jp) % g.nx) * g.ny + jp;
+}
+
+__global__ void shard_export_kernel(const GeomDev* geoms, double* out) {
+  const GeomDev g = geoms[0];
+  const int stride = gridDim.x * blockDim.x;
+  const int tid = blockIdx.x * blockDim.x + threadIdx.x;
+  for (int c = tid; c < g.n_cells; c += stride) {
+    double t = 0.0;
+    if (!g.tlq) {
+      t = g.TL_acc[c];
+      g.TL_acc[c] = 0.0;
+    } else {
+      size_t k[4];
+      double p[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        k[q] = skew_index(g, c, q);
+        p[q] = g.tlq[k[q]];
+      }
+      t = (p[0] + p[1]) + (p[2] + p[3]);
+#pragma unroll
+      for (int q = 0; q < 4; ++q) g.tlq[k[q]] = 0.0;
+    }
+    out[c] = (g.code[c] & CODE_SOLID) ? t : 0.0;
+  }
+  for (int f = tid; f < g.n_walls; f += stride) {
+    const size_t k = (size_t)g.wall_cell[f] * 6 + g.wall_side[f];
+    out[g.n_cells + f] = g.wall_acc[k];
+    g.wall_acc[k] = 0.0;
+  }
+  if (tid == 0) {
+    out[g.n_cells + g.n_walls] = *g.phi_acc;
+    *g.phi_acc = 0.0;
+  }
+}
+
+__global__ void shard_import_kernel(const GeomDev* geoms, const double* in) {
+  const GeomDev g = geoms[0];
+  if (*(volatile int*)g.done) return;
+  const int stride = gridDim.x * blockDim.x;
+  const int tid = blockIdx.x * blockDim.x + threadIdx.x;
+  for (int c = tid; c < g.n_cells; c += stride) {
+    if (g.tlq) g.tlq[skew_index(g, c, 0)] = in[c];
+    else g.TL_acc[c] = in[c];
+  }
+  for (int f = tid; f < g.n_walls; f += stride)
+    g.wall_acc[(size_t)g.wall_cell[f] * 6 + g.wall_side[f]] = in[g.n_cells + f];
+  if (tid == 0) *g.phi_acc = in[g.n_cells + g.n_walls];
+}
+
 }  // namespace
+
+cudaError_t launch_shard_export(const GeomDev* geoms_dev, double* out, int blocks, cudaStream_t st) {
+  shard_export_kernel<<<blocks, 256, 0, st>>>(geoms_dev, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_shard_import(const GeomDev* geoms_dev, const double* in, int blocks,
+                                cudaStream_t st) {
+  shard_import_kernel<<<blocks, 256, 0, st>>>(geoms_dev, in);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_build_records(const GeomDev* geoms_dev, int n_geoms, int precision, int blocks,
                                  cudaStream_t st) {

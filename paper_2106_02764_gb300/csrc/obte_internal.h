@@ -179,6 +179,12 @@ constexpr int kMaxSkewCells = 1 << 22;
 // max_work = max over them of max(6 n_cells, n_ord rows), max_walls likewise
 cudaError_t launch_init_state(const GeomDev* geoms_dev, int n_geoms, long max_work, int max_walls,
                               int precision, cudaStream_t st);
+// ordinate sharding: the moment partials of a sweep out of / back into the
+// accumulators (layout: T_L numerator [n_cells], wall numerators [n_walls],
+// hot-face flux [1]); one geometry
+cudaError_t launch_shard_export(const GeomDev* geoms_dev, double* out, int blocks, cudaStream_t st);
+cudaError_t launch_shard_import(const GeomDev* geoms_dev, const double* in, int blocks,
+                                cudaStream_t st);
 cudaError_t launch_gauge(const uint8_t* code, const double* TL, int n, double* out,
                          double* mean_out, cudaStream_t st);
 cudaError_t launch_grad_contract2(const uint8_t* code, const double* TL, int n, const void* rec,
