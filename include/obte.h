@@ -72,14 +72,16 @@ typedef struct {
 
 typedef struct {
   int precision;        /* obte_precision.  FP64: every step in double.  MIXED:
-                           transport sweeps in float, in delta form
-                           T = s T_L + sum_a A_a (u_a - s T_L), so that the
-                           weight of T_L is exactly 1 - sum_a A_a whatever
-                           the rounding of the float coefficients A_a; the
-                           applied jump enters the float upwind value of the
-                           first column (u = T_image +- dT); T_L, flux,
-                           kappa (its jump part dT sum K_x included) and
-                           wall sums and the convergence test in double    */
+                           transport sweeps in float, carrying deviations
+                           psi = T - T_L: the upwind differences u - T_L of
+                           neighbour, wall and periodic-image values (the
+                           applied jump dT included) are formed in double
+                           and rounded once, psi = sum_a A_a (u_a - T_L), so
+                           the weight of T_L is exactly 1 - sum_a A_a and no
+                           float value carries T_L itself; T_L, flux, kappa
+                           (its jump part dT sum K_x and its T_L part
+                           included) and wall sums and the convergence test
+                           in double                                          */
   double tol;           /* stop when |kappa_n - kappa_{n-1}| <= tol |kappa_n|
                            (Algorithm 1); <= 0 disables                        */
   double tol_TL;        /* and max_i |T_L,n - T_L,n-1| <= tol_TL (K); <= 0 off  */

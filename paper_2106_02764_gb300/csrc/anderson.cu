@@ -323,7 +323,9 @@ __global__ void aa_mix_kernel(const GeomDev* geoms) {
   T* src = reinterpret_cast<T*>(g.src);
   T* twc = reinterpret_cast<T*>(g.twc);
   double* Xd = g.aa_xcd;
-  const bool recs = g.rec4 != nullptr;
+  // deviation form: the records' difference fields are rebuilt from the
+  // mixed T_L and T_w by psi_records_kernel after this kernel
+  const bool recs = g.rec4 != nullptr && !g.psi;
   for (long i = tid; i < g.aa_nd; i += stride) {
     double v = 0.0;
 #pragma unroll

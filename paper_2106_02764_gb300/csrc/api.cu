@@ -902,7 +902,7 @@ static int prepare_state(obte_ctx* ctx, int precision, int G, int R, bool warp, 
     ctx->Tw = ctx->dalloc_t<double>(std::max(1, ctx->n_walls));
     ctx->wall_acc = ctx->dalloc_t<double>((size_t)ctx->n_cells * 6);
     ctx->front = ctx->dalloc(e * (size_t)ctx->O * rows);
-    ctx->scal = ctx->dalloc_t<double>(4);
+    ctx->scal = ctx->dalloc_t<double>(6);
     ctx->ctrl = ctx->dalloc_t<int>(4);
     ctx->hist = ctx->dalloc_t<double>(kMaxHist);
     ctx->TF = ctx->dalloc_t<double>(ctx->n_cells);
@@ -1019,9 +1019,17 @@ static int prepare_state(obte_ctx* ctx, int precision, int G, int R, bool warp, 
   g.tlq = rec_w == 4 ? ctx->tlq : nullptr;
   g.blk_part = ctx->blk_part;
   g.rec_w = rec_w;
+  g.psi = (precision == 1 && rec_w > 0) ? 1 : 0;  // float record kernels: deviation form
   g.front = ctx->front;
   g.phi_acc = ctx->scal;
   g.delta_max = ctx->scal + 1;
+  g.hot_tl = ctx->scal + 3;
+  g.kx_pos = g.kx_neg = 0.0;
+  for (int o = 0; o < ctx->O; ++o) {  // sorted-frame signed K_ox = sign(p_x) |K_ox|
+    const double k = ctx->pk[0][o] > 0 ? ctx->kxa[o] : (ctx->pk[0][o] < 0 ? -ctx->kxa[o] : 0.0);
+    if (k > 0) g.kx_pos += k;
+    else g.kx_neg += k;
+  }
   g.J_acc = ctx->J_acc;
   g.phi_sec = ctx->phi_sec;
   g.phi_bin = ctx->phi_bin;
@@ -1157,7 +1165,10 @@ static int init_from_fourier(obte_ctx* ctx, const obte_solve_opts& op, int* fite
   }
   CK(launch_init_state(ctx->gd, 1, std::max((long)ctx->gh.n_cells * 6, (long)ctx->gh.n_ord * ctx->gh.rows),
                        ctx->gh.n_walls, prec, ctx->stream));
-  if (ctx->warp || ctx->k3d) CK(launch_build_records(ctx->gd, 1, prec, finalize_blocks(ctx->n_cells), ctx->stream));
+  if (ctx->warp || ctx->k3d) {
+    CK(launch_build_records(ctx->gd, 1, prec, finalize_blocks(ctx->n_cells), ctx->stream));
+    CK(launch_psi_records(ctx->gd, 1, prec, finalize_blocks(ctx->n_cells), ctx->stream));
+  }
   if (ctx->gh.aa_m > 0)
     CK(launch_anderson_init(ctx->gd, 1, prec, aa_blocks(ctx->n_cells, ctx->O, ctx->n[1] * ctx->n[2]), ctx->stream));
   if (fiters_out) {
@@ -1292,6 +1303,10 @@ static int run_iterations(obte_ctx* ctx, const obte_solve_opts& op, int* iters, 
       if (ctx->gh.aa_m > 0) {
         e = launch_anderson_step(ctx->gd, 1, ctx->precision,
                                  aa_blocks(ctx->n_cells, ctx->O, ctx->n[1] * ctx->n[2]), ctx->stream);
+        if (e != cudaSuccess) return e;
+      }
+      if (ctx->gh.psi) {
+        e = launch_psi_records(ctx->gd, 1, ctx->precision, finalize_blocks(ctx->n_cells), ctx->stream);
         if (e != cudaSuccess) return e;
       }
       if (op.profile && (e = cudaEventRecordWithFlags(ev[3 * i + 2], ctx->stream, cudaEventRecordExternal)) != cudaSuccess) return e;
@@ -1506,6 +1521,7 @@ extern "C" int obte_shard_finalize(obte_ctx* ctx, const double* partials, int* d
   CK(cudaSetDevice(ctx->device));
   CK(launch_shard_import(ctx->gd, partials, finalize_blocks(ctx->n_cells), ctx->stream));
   CK(launch_finalize(ctx->gd, 1, ctx->precision, finalize_blocks(ctx->n_cells), ctx->stream));
+  if (ctx->gh.psi) CK(launch_psi_records(ctx->gd, 1, ctx->precision, finalize_blocks(ctx->n_cells), ctx->stream));
   int ctrl[4];
   CK(cudaMemcpyAsync(ctrl, ctx->ctrl, sizeof(ctrl), cudaMemcpyDeviceToHost, ctx->stream));
   CK(cudaStreamSynchronize(ctx->stream));
@@ -1806,7 +1822,7 @@ extern "C" int obte_kappa_grad_s(obte_ctx* ctx, double* out, size_t max_field_by
                       L.n_items, smem, ctx->stream));
     }
     CK(launch_grad_contract2(ctx->code_d, ctx->TL, ctx->n_cells, rec, (int)b.size(), revl_d, a_d,
-                             jscale, grad_d, ctx->precision, ctx->stream));
+                             jscale, grad_d, ctx->precision, ctx->gh.psi, ctx->stream));
     CK(cudaMemsetAsync(ctx->TL_acc, 0, sizeof(double) * ctx->n_cells, ctx->stream));
     if (ctx->tlq) CK(cudaMemsetAsync(ctx->tlq, 0, sizeof(double) * 4 * (size_t)ctx->n_cells, ctx->stream));
     CK(cudaMemsetAsync(ctx->wall_acc, 0, sizeof(double) * 6 * (size_t)ctx->n_cells, ctx->stream));
@@ -2134,6 +2150,7 @@ extern "C" int obte_solve_batch(obte_ctx* const* ctxs, int n, const obte_solve_o
     }
     cudaError_t e = launch_init_state(gds, n, max_work, max_walls, prec, ctx->stream);
     if (e == cudaSuccess && v.warp) e = launch_build_records(gds, n, prec, finalize_blocks(max_cells), ctx->stream);
+    if (e == cudaSuccess && v.warp) e = launch_psi_records(gds, n, prec, finalize_blocks(max_cells), ctx->stream);
     if (e == cudaSuccess && any_aa)
       e = launch_anderson_init(gds, n, prec, aa_blocks(max_cells, max_ord, max_rows), ctx->stream);
     if (e != cudaSuccess) return ctx->cuda_fail(e, "batch init");
@@ -2176,6 +2193,10 @@ extern "C" int obte_solve_batch(obte_ctx* const* ctxs, int n, const obte_solve_o
       if (e != cudaSuccess) return e;
       if (op.accel > 0) {
         e = launch_anderson_step(gds, n, prec, aa_blocks(max_cells, max_ord, max_rows), ctx->stream);
+        if (e != cudaSuccess) return e;
+      }
+      if (v.warp) {
+        e = launch_psi_records(gds, n, prec, finalize_blocks(max_cells), ctx->stream);
         if (e != cudaSuccess) return e;
       }
     }
@@ -2432,7 +2453,7 @@ extern "C" int obte_kappa_grad_s_noalloc(obte_ctx* ctx, double* out) {
                       L.n_items, smem, ctx->stream));
     }
     CK(launch_grad_contract2(ctx->code_d, ctx->TL, ctx->n_cells, rec, (int)b.size(), revl_d, a_d,
-                             jscale, grad_d, ctx->precision, ctx->stream));
+                             jscale, grad_d, ctx->precision, ctx->gh.psi, ctx->stream));
     CK(cudaMemsetAsync(ctx->TL_acc, 0, sizeof(double) * ctx->n_cells, ctx->stream));
     if (ctx->tlq) CK(cudaMemsetAsync(ctx->tlq, 0, sizeof(double) * 4 * (size_t)ctx->n_cells, ctx->stream));
     CK(cudaMemsetAsync(ctx->wall_acc, 0, sizeof(double) * 6 * (size_t)ctx->n_cells, ctx->stream));

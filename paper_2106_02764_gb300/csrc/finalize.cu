@@ -10,6 +10,21 @@
 
 namespace {
 
+// block sum (valid in thread 0); every thread of the block calls it
+__device__ double obte_block_sum(double v, double* red) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+  __syncthreads();
+  if (lane == 0) red[w] = v;
+  __syncthreads();
+  double s = 0.0;
+  if (threadIdx.x < 32) {
+    s = (lane < nw) ? red[lane] : 0.0;
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  }
+  return s;
+}
+
 // T_L <- sum_o a_o T_o (E2), T_w <- wall numerator / denominator (E3), the
 // sweep inputs derived from them, and each block's max |dT_L| into its
 // partial slot.  Grid: x = blocks per geometry, y = geometry.
@@ -50,12 +65,32 @@ __global__ void finalize_kernel(const GeomDev* geoms) {
 #pragma unroll
       for (int q = 0; q < 4; ++q) g.tlq[k[q]] = 0.0;
     }
+    if (g.psi) {
+      // deviation form: the accumulators hold sums of psi = T_o - T_L, so
+      // T_L_new = T_L + sum_o a_o psi_o and T_w = T_L,cell + num_psi / den;
+      // the cell's walls are done here, while T_L,cell is still the old one
+      const double told = TL[c];
+      t += told;
+      const uint32_t cd = code[c];
+      T* twc = reinterpret_cast<T*>(g.twc);
+#pragma unroll
+      for (int sd = 0; sd < 6; ++sd)
+        if (cd & (1u << sd)) {
+          const int f = g.wall_id[(size_t)c * 6 + sd];
+          const size_t k = (size_t)c * 6 + sd;
+          const double w = told + g.wall_acc[k] / g.wall_den[f];
+          g.wall_acc[k] = 0.0;
+          if (!isfinite(w)) nonfin = 1;
+          g.Tw[f] = w;
+          twc[k] = (T)w;
+        }
+    }
     if (!isfinite(t)) nonfin = 1;
     dmax = fmax(dmax, fabs(t - TL[c]));
     TL[c] = t;
     const T v = (T)(sv ? sv[c] * t : t);
     src[c] = v;
-    if (recs) {
+    if (recs && !g.psi) {  // deviation form: the records are rebuilt by psi_records_kernel
       if (g.tlq) {  // the records of the 2D warp kernel share the skewed index
         T* rec = reinterpret_cast<T*>(g.rec4);
 #pragma unroll
@@ -66,7 +101,7 @@ __global__ void finalize_kernel(const GeomDev* geoms) {
     }
   }
   T* twc = reinterpret_cast<T*>(g.twc);
-  for (int f = blockIdx.x * blockDim.x + threadIdx.x; f < g.n_walls; f += stride) {
+  for (int f = blockIdx.x * blockDim.x + threadIdx.x; f < (g.psi ? 0 : g.n_walls); f += stride) {
     const int c = g.wall_cell[f], sd = g.wall_side[f];
     const size_t k = (size_t)c * 6 + sd;
     const double w = g.wall_acc[k] / g.wall_den[f];
@@ -98,7 +133,10 @@ __global__ void finalize_tail_kernel(const GeomDev* geoms, int nblocks) {
   for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
   if (threadIdx.x != 0) return;
   const double delta = m;
-  const double kappa = g.kappa_scale * (*g.phi_acc);
+  // deviation form: the sweeps summed psi = T_o - T_L; the T_L part of the
+  // hot-face flux is K+ S+ + K- S- over the T_L that sweep used
+  const double phi_tl = g.psi ? g.kx_pos * g.hot_tl[0] + g.kx_neg * g.hot_tl[1] : 0.0;
+  const double kappa = g.kappa_scale * (*g.phi_acc + phi_tl);
   *g.phi_acc = 0.0;
   const int n = *g.iter + 1;
   *g.iter = n;
@@ -155,7 +193,8 @@ __global__ void init_state_kernel(const GeomDev* geoms) {
     const int y = (oc & 2) ? g.ny - 1 - jp : jp;
     const int z = (g.dim == 3) ? ((oc & 4) ? g.nz - 1 - kp : kp) : 0;
     const int c = x + g.nx * (y + g.ny * z);
-    front[i] = (T)((g.code[c] & CODE_SOLID) ? T0[c] : 0.0);
+    // deviation form: psi = T_o - T_L = 0 on the starting guess
+    front[i] = (T)((g.code[c] & CODE_SOLID) && !g.psi ? T0[c] : 0.0);
   }
   if (tid == 0) {
     *g.phi_acc = 0.0;
@@ -206,10 +245,12 @@ __global__ void gauge_kernel(const uint8_t* code, const double* TL, int n, doubl
 // over recorded fields rec[(o - o0) * n + c]; rev_local maps o - o0 to the
 // record slot of the reversed ordinate.  The reversed field is the adjoint
 // field of o (see obte_kappa_grad_s).
+// With psi the recorded fields are deviations T_o - T_L (deviation-form
+// sweeps): then T_o - T_L is the record itself and T_rev = record + T_L.
 template <typename T>
 __global__ void grad_contract_kernel(const uint8_t* code, const double* TL, int n, const T* rec,
                                      int n_rec, const int* rev_local, const double* a_rec,
-                                     double jscale, double* grad) {
+                                     double jscale, double* grad, int psi) {
   for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < n; c += gridDim.x * blockDim.x) {
     if (!(code[c] & CODE_SOLID)) continue;
     const double tl = TL[c];
@@ -217,9 +258,72 @@ __global__ void grad_contract_kernel(const uint8_t* code, const double* TL, int 
     for (int k = 0; k < n_rec; ++k) {
       const double f = (double)rec[(size_t)k * n + c];
       const double b = (double)rec[(size_t)rev_local[k] * n + c];
-      acc += a_rec[k] * b * (f - tl);
+      acc += psi ? a_rec[k] * (b + tl) * f : a_rec[k] * b * (f - tl);
     }
     grad[c] -= jscale * acc;
+  }
+}
+
+// Deviation form: each solid cell's record fields 1 .. dim of every octant
+// hold the upwind value across that octant's upwind side minus the cell's
+// T_L, formed in FP64: T_w - T_L at a wall, otherwise the neighbour's T_L
+// (across the x period: +dT at the low side, -dT at the high side) minus the
+// cell's.  Grid: x = blocks per geometry, y = geometry.
+template <typename T>
+__global__ void psi_records_kernel(const GeomDev* geoms) {
+  const GeomDev& g = geoms[blockIdx.y];
+  if (!g.psi || !g.rec4) return;
+  if (blockIdx.x == 0) {
+    // S+, S-: T_L at the two ends of the solid-solid faces of the plane x = 0
+    // (fixed order: a block sum), for the tail's kappa of the next sweep
+    __shared__ double red[32];
+    double sp = 0.0, sm = 0.0;
+    for (int row = threadIdx.x; row < g.rows; row += blockDim.x) {
+      const int c0 = g.nx * row, c1 = c0 + g.nx - 1;
+      if ((g.code[c1] & CODE_SOLID) && !(g.code[c1] & CODE_WALL_XP)) {
+        sp += g.TL[c1];
+        sm += g.TL[c0];
+      }
+    }
+    sp = obte_block_sum(sp, red);
+    sm = obte_block_sum(sm, red);
+    if (threadIdx.x == 0) {
+      g.hot_tl[0] = sp;
+      g.hot_tl[1] = sm;
+    }
+  }
+  T* rec = reinterpret_cast<T*>(g.rec4);
+  const int nx = g.nx, ny = g.ny, nz = g.nz;
+  const int nq = g.dim == 3 ? 8 : 4;
+  const double* TL = g.TL;
+  const int stride = gridDim.x * blockDim.x;
+  for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < g.n_cells; c += stride) {
+    const uint32_t cd = g.code[c];
+    if (!(cd & CODE_SOLID)) continue;
+    const int x = c % nx, y = (c / nx) % ny, z = c / (nx * ny);
+    const double tl = TL[c];
+    auto side = [&](int sd, int nb, double jump) -> double {
+      if (cd & (1u << sd)) return g.Tw[g.wall_id[(size_t)c * 6 + sd]] - tl;
+      return TL[nb] + jump - tl;
+    };
+    const int row = nx * (y + ny * z);
+    double d[6];
+    d[0] = side(0, (x == 0 ? nx - 1 : x - 1) + row, x == 0 ? g.dT : 0.0);
+    d[1] = side(1, (x == nx - 1 ? 0 : x + 1) + row, x == nx - 1 ? -g.dT : 0.0);
+    d[2] = side(2, x + nx * ((y == 0 ? ny - 1 : y - 1) + ny * z), 0.0);
+    d[3] = side(3, x + nx * ((y == ny - 1 ? 0 : y + 1) + ny * z), 0.0);
+    d[4] = d[5] = 0.0;
+    if (g.dim == 3) {
+      d[4] = side(4, x + nx * (y + ny * (z == 0 ? nz - 1 : z - 1)), 0.0);
+      d[5] = side(5, x + nx * (y + ny * (z == nz - 1 ? 0 : z + 1)), 0.0);
+    }
+    for (int q = 0; q < nq; ++q) {
+      T* r = rec + (size_t)g.rec_w * g.rec_idx[(size_t)c * nq + q];
+      // octant bit a set: p_a < 0, the upwind side is the + side
+      r[1] = (T)d[(q & 1) ? 1 : 0];
+      r[2] = (T)d[(q & 2) ? 3 : 2];
+      if (g.rec_w == 8) r[3] = (T)d[(q & 4) ? 5 : 4];
+    }
   }
 }
 
@@ -401,6 +505,14 @@ cudaError_t launch_init_state(const GeomDev* geoms_dev, int n_geoms, long max_wo
   return cudaGetLastError();
 }
 
+cudaError_t launch_psi_records(const GeomDev* geoms_dev, int n_geoms, int precision, int blocks,
+                               cudaStream_t st) {
+  if (precision == 0) return cudaSuccess;  // FP64 sweeps carry T_o
+  dim3 grid(blocks, n_geoms);
+  psi_records_kernel<float><<<grid, 256, 0, st>>>(geoms_dev);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_gauge(const uint8_t* code, const double* TL, int n, double* out,
                          double* mean_out, cudaStream_t st) {
   gauge_kernel<<<1, 1024, 0, st>>>(code, TL, n, out, mean_out);
@@ -409,14 +521,15 @@ cudaError_t launch_gauge(const uint8_t* code, const double* TL, int n, double* o
 
 cudaError_t launch_grad_contract2(const uint8_t* code, const double* TL, int n, const void* rec,
                                   int n_rec, const int* rev_local, const double* a_rec,
-                                  double jscale, double* grad, int precision, cudaStream_t st) {
+                                  double jscale, double* grad, int precision, int psi,
+                                  cudaStream_t st) {
   int blocks = (n + 255) / 256;
   if (blocks > 2048) blocks = 2048;
   if (precision == 0)
     grad_contract_kernel<double><<<blocks, 256, 0, st>>>(code, TL, n, (const double*)rec, n_rec,
-                                                         rev_local, a_rec, jscale, grad);
+                                                         rev_local, a_rec, jscale, grad, psi);
   else
     grad_contract_kernel<float><<<blocks, 256, 0, st>>>(code, TL, n, (const float*)rec, n_rec,
-                                                        rev_local, a_rec, jscale, grad);
+                                                        rev_local, a_rec, jscale, grad, psi);
   return cudaGetLastError();
 }

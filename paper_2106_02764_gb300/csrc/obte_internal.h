@@ -87,6 +87,20 @@ struct GeomDev {
   int* rec_idx;
   double* tlq;
   int rec_w;              // values per record: 4 (2D warp kernel), 8 (3D kernel); 0: none
+  // Deviation form (float record kernels): the sweep carries psi_o = T_o - T_L
+  // per cell, the records' wall / neighbour fields hold the FP64 differences
+  // u - T_L,cell of the upwind values (neighbour T_L, wall T_w, image T_L
+  // +- dT) rounded once, and the moment accumulators receive sums of psi;
+  // the finalisation adds T_L back in FP64.  A float sweep that carried T_o
+  // itself would quantise the source s T_L to float, and the slowly
+  // converging diffusive mode of T_L stalls on that quantum.
+  int psi;
+  // deviation form: the T_L part of the hot-face flux, K+ S+ + K- S-, with
+  // K+- = sum of K_ox over the ordinates with p_x > 0 (< 0) and S+- = sum of
+  // T_L over the cells at x = nx - 1 (x = 0) of the solid-solid faces of the
+  // plane x = 0; hot_tl[0..1] = S+, S- of the T_L the next sweep uses
+  double kx_pos, kx_neg;
+  double* hot_tl;
   void* front;            // [n_ord][rows] row values carried between iterations
   double* phi_acc;        // [1] hot-face flux of the running sweep
   // flux pass outputs
@@ -185,11 +199,17 @@ cudaError_t launch_init_state(const GeomDev* geoms_dev, int n_geoms, long max_wo
 cudaError_t launch_shard_export(const GeomDev* geoms_dev, double* out, int blocks, cudaStream_t st);
 cudaError_t launch_shard_import(const GeomDev* geoms_dev, const double* in, int blocks,
                                 cudaStream_t st);
+// deviation form: rebuild the records' upwind-difference fields from T_L and
+// T_w (after the finalisation and the Anderson mix); no-op for other geometries
+cudaError_t launch_psi_records(const GeomDev* geoms_dev, int n_geoms, int precision, int blocks,
+                               cudaStream_t st);
 cudaError_t launch_gauge(const uint8_t* code, const double* TL, int n, double* out,
                          double* mean_out, cudaStream_t st);
+// psi: the recorded fields are deviations T_o - T_L (deviation-form sweeps)
 cudaError_t launch_grad_contract2(const uint8_t* code, const double* TL, int n, const void* rec,
                                   int n_rec, const int* rev_local, const double* a_rec,
-                                  double jscale, double* grad, int precision, cudaStream_t st);
+                                  double jscale, double* grad, int precision, int psi,
+                                  cudaStream_t st);
 
 // fourier.cu
 // arguments of one Fourier CG solve

@@ -26,6 +26,13 @@
 // rare epilogue (walls the ordinates leave into, the hot-contact column, flux /
 // record passes) are predicated on the cell being solid.
 //
+// Precision.  FP32 groups run in deviation form: the row values are
+// psi = T_o - T_L of the cell, the records' x / y fields hold the upwind
+// value minus the cell's T_L (formed in FP64 by the finalisation), and
+// psi = A_x (m_x psi_x + t_x) + A_y (m_y psi_y + t_y), with m = 0 and t the
+// wall difference at a wall; the T_L, wall and flux moments are sums of psi,
+// and the finalisation adds T_L back in FP64.  FP64 groups carry T_o.
+//
 // The R rows of a lane sit in the top R of RMAX register rows (slots
 // RMAX - R .. RMAX - 1), so the lane's top row is always slot RMAX - 1; with
 // RFIXED the host guarantees R == RMAX.
@@ -86,22 +93,29 @@ __device__ __noinline__ double cell_epilogue_2d(const GeomDev& gm, const T* __re
   const double dx = widen(sxk), dy = widen(syk);
   if (out_x) atomicAdd(gm.wall_acc + cell * 6 + (sx > 0 ? 1 : 0), dx);
   if (out_y) atomicAdd(gm.wall_acc + cell * 6 + (sy > 0 ? 3 : 2), dy);
+  // deviation form (FP32): T_o = psi_o + T_L, so every signed flux sum gains
+  // T_L sum_g K_g (kx_sum is sum_g sign(p_x) |K_gx|)
+  constexpr bool PSI = sizeof(T) == 4;
+  const double tl = PSI ? gm.TL[cell] : 0.0;
   const bool hot = last && !out_x;
   double phi = 0.0;
-  if (hot) phi = (sx > 0 ? dx : -dx) + (sx > 0 ? dT * kx_sum : 0.0);
+  if (hot) phi = (sx > 0 ? dx : -dx) + (sx > 0 ? dT * kx_sum : 0.0) + tl * kx_sum;
   if (flags & SWEEP_FLUX) {
     const int x = cell % nx;
-    atomicAdd(gm.J_acc + 3 * cell + 0, sx > 0 ? dx : -dx);
-    atomicAdd(gm.J_acc + 3 * cell + 1, sy > 0 ? dy : -dy);
+    double ky_sum = 0.0;
+    if (PSI)
+      for (int g = 0; g < cnt; ++g) ky_sum += (double)sy * (double)ld<T>(gm.kya, o0 + g);
+    atomicAdd(gm.J_acc + 3 * cell + 0, (sx > 0 ? dx : -dx) + tl * kx_sum);
+    atomicAdd(gm.J_acc + 3 * cell + 1, (sy > 0 ? dy : -dy) + tl * ky_sum);
     if (!out_x) {
       const int sec = sx > 0 ? (x + 1) % nx : x;
       const bool jmp = sx > 0 && x == nx - 1;
-      atomicAdd(gm.phi_sec + sec, (sx > 0 ? dx : -dx) + (jmp ? dT * kx_sum : 0.0));
+      atomicAdd(gm.phi_sec + sec, (sx > 0 ? dx : -dx) + (jmp ? dT * kx_sum : 0.0) + tl * kx_sum);
     }
     if (hot)
       for (int g = 0; g < cnt; ++g) {
         const double k = (double)sx * (double)ld<T>(gm.kxa, o0 + g);
-        atomicAdd(gm.phi_bin + gm.mbin[o0 + g], k * ((double)val[g] + (sx > 0 ? dT : 0.0)));
+        atomicAdd(gm.phi_bin + gm.mbin[o0 + g], k * ((double)val[g] + tl + (sx > 0 ? dT : 0.0)));
       }
   }
   if (flags & SWEEP_RECORD) {
@@ -198,10 +212,11 @@ __global__ void __launch_bounds__(32 * WarpCfg<T, G, RMAX>::WPB, WarpCfg<T, G, R
     const double* __restrict__ sv_ptr = gm.s;
     double* wacc = gm.wall_acc;
 
-    // the jump across the x period: FP32 adds it to the x upwind value (one
-    // FADD); FP64, whose pipe is the narrow one, selects the premultiplied
-    // term JX instead
+    // the jump across the x period: FP32 carries it in the record's x
+    // difference; FP64, whose pipe is the narrow one, selects the
+    // premultiplied term JX instead
     constexpr bool JSEL = sizeof(T) == 8;
+    constexpr bool PSI = !JSEL;  // deviation form (see the file comment)
     T A0[G], AX[G], AY[G], AW[G], JX[JSEL ? G : 1];
     double kx_sum = 0.0;
     __syncwarp();  // the previous item's rare path is done with kcoef
@@ -384,25 +399,22 @@ __global__ void __launch_bounds__(32 * WarpCfg<T, G, RMAX>::WPB, WarpCfg<T, G, R
             T sval = T(1);
             if (HAS_S) sval = (T)__ldg(sv_ptr + (packed & REC_CELL_MASK));
             if constexpr (X2) {
-              // u_x = m_x T + t_x: the row value, the wall temperature
-              // (m_x = 0, t_x = T_w), or the value across the jump
-              // (t_x = +-dT); the record's x field holds t_x, its y field t_y.
-              // Delta form T = src + A_x (u_x - src) + A_y (u_y - src): the
-              // weight of src is 1 - A_x - A_y exactly, whatever the float
-              // rounding of A_x and A_y, so every ordinate's transport keeps
-              // T = T_L on a uniform field (a float 1 / (1 + D) would not)
-              const float mx = wx ? 0.f : 1.f, tx = twx - src;
-              const float my = wy ? 0.f : 1.f, ty = twy - src;
-              const float2 mx2 = make_float2(mx, mx), tx2 = make_float2(tx, tx);
-              const float2 my2 = make_float2(my, my), ty2 = make_float2(ty, ty);
-              const float2 src2 = make_float2(src, src);
+              // deviation form: u_a - T_L,cell = m_a psi_a + t_a, with the
+              // upwind row's psi (m = 1, t = its T_L minus this cell's, the
+              // jump included on the jump column) or a wall (m = 0, t =
+              // T_w - T_L,cell); psi = A_x (u_x - T_L) + A_y (u_y - T_L).
+              // The weight of T_L is exactly 1 - A_x - A_y whatever the float
+              // rounding of A_x and A_y, and no float value carries T_L
+              const float mx = wx ? 0.f : 1.f, my = wy ? 0.f : 1.f;
+              const float2 mx2 = make_float2(mx, mx), tx2 = make_float2(twx, twx);
+              const float2 my2 = make_float2(my, my), ty2 = make_float2(twy, twy);
               float2 tlp = make_float2(0.f, 0.f);
 #pragma unroll
               for (int h = 0; h < GV; ++h) {
-                const float2 ux = __ffma2_rn(mx2, v[r][h], tx2);  // u_x - src
+                const float2 ux = __ffma2_rn(mx2, v[r][h], tx2);  // u_x - T_L,cell
                 const float2 ud = below_in_lane ? v[r > 0 ? r - 1 : 0][h] : dn0[h];
-                const float2 uy = __ffma2_rn(my2, ud, ty2);       // u_y - src
-                float2 acc = __ffma2_rn(AYv[h], uy, src2);
+                const float2 uy = __ffma2_rn(my2, ud, ty2);       // u_y - T_L,cell
+                float2 acc = __fmul2_rn(AYv[h], uy);
                 acc = __ffma2_rn(AXv[h], ux, acc);
                 v[r][h] = acc;
                 tlp = __ffma2_rn(AWv[h], acc, tlp);
@@ -411,18 +423,18 @@ __global__ void __launch_bounds__(32 * WarpCfg<T, G, RMAX>::WPB, WarpCfg<T, G, R
               tls[r] = tlp.x + tlp.y;
             } else {
             T tl = T(0), tl2 = T(0);  // two partial chains of the T_L moment
-            // float without s(x): the delta form of the paired path
-            constexpr bool DELTA = !JSEL && !HAS_S;
+            // FP32: the deviation form of the paired path (with s(x):
+            // psi = (beta_x (u_x - T_L) + beta_y (u_y - T_L)) / (s + D));
+            // FP64 carries T_o, the jump premultiplied (JX)
 #pragma unroll
             for (int g = 0; g < G; ++g) {
-              const T ux = JSEL ? (wx ? twx : VG(r, g))
-                                : (wx ? T(0) : VG(r, g)) + (DELTA ? twx - src : twx);
+              const T ux = JSEL ? (wx ? twx : VG(r, g)) : (wx ? T(0) : VG(r, g)) + twx;
               const T ud = below_in_lane ? VG(r > 0 ? r - 1 : 0, g) : dn0[g];
-              const T uy = DELTA ? (wy ? T(0) : ud) + (twy - src) : (wy ? twy : ud);
+              const T uy = JSEL ? (wy ? twy : ud) : (wy ? T(0) : ud) + twy;
               const T jx = (JSEL && jump) ? JX[JSEL ? g : 0] : T(0);
               T acc;
-              if (HAS_S) acc = fma(AY[g], uy, JSEL ? src + jx : src);
-              else if (DELTA) acc = fma(AY[g], uy, src);
+              if (!JSEL) acc = AY[g] * uy;
+              else if (HAS_S) acc = fma(AY[g], uy, src + jx);
               else acc = fma(AY[g], uy, fma(src, A0[g], jx));
               acc = fma(AX[g], ux, acc);
               T val;

@@ -20,6 +20,10 @@
 // one step ahead into registers.  The T_L moment goes to the cell's FP64
 // accumulator.
 //
+// FP32 groups run in deviation form like the 2D warp kernel (sweep2d.cuh):
+// row values psi = T_o - T_L, record fields holding the upwind value minus
+// the cell's T_L, moments of psi, T_L added back in FP64.
+//
 // Cells update branch-free (pore values never reach a solid cell, whose faces
 // towards a pore are walls); atomics and the rare epilogue (walls the
 // ordinates leave into, the hot-contact column, flux / record passes; sums in
@@ -58,23 +62,33 @@ __device__ __noinline__ double cell_epilogue_3d(const GeomDev& gm, const T* val,
   if (out_x) atomicAdd(gm.wall_acc + cell * 6 + (sx > 0 ? 1 : 0), dx);
   if (out_y) atomicAdd(gm.wall_acc + cell * 6 + (sy > 0 ? 3 : 2), dy);
   if (out_z) atomicAdd(gm.wall_acc + cell * 6 + (sz > 0 ? 5 : 4), dz);
+  // deviation form (FP32): every signed flux sum gains T_L sum_g K_g
+  constexpr bool PSI = sizeof(T) == 4;
+  const double tl = PSI ? gm.TL[cell] : 0.0;
   const bool hot = last && !out_x;
   double phi = 0.0;
-  if (hot) phi = (sx > 0 ? dx : -dx) + (sx > 0 ? dT * kx_sum : 0.0);
+  if (hot) phi = (sx > 0 ? dx : -dx) + (sx > 0 ? dT * kx_sum : 0.0) + tl * kx_sum;
   if (flags & SWEEP_FLUX) {
     const int x = cell % nx;
-    atomicAdd(gm.J_acc + 3 * cell + 0, sx > 0 ? dx : -dx);
-    atomicAdd(gm.J_acc + 3 * cell + 1, sy > 0 ? dy : -dy);
-    atomicAdd(gm.J_acc + 3 * cell + 2, sz > 0 ? dz : -dz);
+    double ky_sum = 0.0, kz_sum = 0.0;
+    if (PSI)
+      for (int g = 0; g < cnt; ++g) {
+        ky_sum += (double)sy * (double)ld<T>(gm.kya, o0 + g);
+        kz_sum += (double)sz * (double)ld<T>(gm.kza, o0 + g);
+      }
+    atomicAdd(gm.J_acc + 3 * cell + 0, (sx > 0 ? dx : -dx) + tl * kx_sum);
+    atomicAdd(gm.J_acc + 3 * cell + 1, (sy > 0 ? dy : -dy) + tl * ky_sum);
+    atomicAdd(gm.J_acc + 3 * cell + 2, (sz > 0 ? dz : -dz) + tl * kz_sum);
     if (!out_x) {
       const int sec = sx > 0 ? (x + 1) % nx : x;
       const bool jmp = sx > 0 && x == nx - 1;
-      atomicAdd(gm.phi_sec + sec, (sx > 0 ? dx : -dx) + (jmp ? dT * kx_sum : 0.0));
+      atomicAdd(gm.phi_sec + sec, (sx > 0 ? dx : -dx) + (jmp ? dT * kx_sum : 0.0) + tl * kx_sum);
     }
     if (hot)
       for (int g = 0; g < cnt; ++g) {
         const double k = (double)sx * (double)ld<T>(gm.kxa, o0 + g);
-        atomicAdd(gm.phi_bin + gm.mbin[o0 + g], k * ((double)val[g * stride] + (sx > 0 ? dT : 0.0)));
+        atomicAdd(gm.phi_bin + gm.mbin[o0 + g],
+                  k * ((double)val[g * stride] + tl + (sx > 0 ? dT : 0.0)));
       }
   }
   if (flags & SWEEP_RECORD) {
@@ -315,24 +329,23 @@ __global__ void __launch_bounds__(Sweep3DCfg<RMAX>::NT, 1) sweep3d_kernel(const 
           // u = m T + t per direction: the upwind value, the wall
           // temperature (m = 0), or the value across the jump (the record's
           // x field holds +-dT on the jump column)
-          // Delta form T = src + sum_a A_a (u_a - src): the weight of src is
-          // 1 - A_x - A_y - A_z exactly, whatever the float rounding of the
-          // A_a, so every ordinate keeps T = T_L on a uniform field
+          // deviation form: u_a - T_L,cell = m_a psi_a + t_a (record fields
+          // t_a: upwind T_L or T_w minus the cell's, the jump included);
+          // psi = sum_a A_a (u_a - T_L), whose weight of T_L is exactly
+          // 1 - sum_a A_a whatever the float rounding of the A_a
           const float mx = wx ? 0.f : 1.f, my = wy ? 0.f : 1.f, mz = wz ? 0.f : 1.f;
-          const float dx = twx - src, dy = twy - src, dz = twz - src;
-          const float2 mx2 = make_float2(mx, mx), tx2 = make_float2(dx, dx);
-          const float2 my2 = make_float2(my, my), ty2 = make_float2(dy, dy);
-          const float2 mz2 = make_float2(mz, mz), tz2 = make_float2(dz, dz);
-          const float2 src2 = make_float2(src, src);
+          const float2 mx2 = make_float2(mx, mx), tx2 = make_float2(twx, twx);
+          const float2 my2 = make_float2(my, my), ty2 = make_float2(twy, twy);
+          const float2 mz2 = make_float2(mz, mz), tz2 = make_float2(twz, twz);
           float2 tlp = make_float2(0.f, 0.f);
 #pragma unroll
           for (int h = 0; h < GV; ++h) {
-            const float2 ux = __ffma2_rn(mx2, v[r][h], tx2);  // u_x - src
+            const float2 ux = __ffma2_rn(mx2, v[r][h], tx2);  // u_x - T_L,cell
             const float2 ud = r > 0 ? v[r > 0 ? r - 1 : 0][h] : dny[h];
             const float2 uy = __ffma2_rn(my2, ud, ty2);
             const float2 uzv = (tz >= 0) ? XP(prv, r, h, tz) : make_float2(0.f, 0.f);
             const float2 uz = __ffma2_rn(mz2, uzv, tz2);
-            float2 acc = __ffma2_rn(AXv[h], ux, src2);
+            float2 acc = __fmul2_rn(AXv[h], ux);
             acc = __ffma2_rn(AYv[h], uy, acc);
             acc = __ffma2_rn(AZv[h], uz, acc);
             v[r][h] = acc;
@@ -344,12 +357,18 @@ __global__ void __launch_bounds__(Sweep3DCfg<RMAX>::NT, 1) sweep3d_kernel(const 
         T tl = T(0), tl2 = T(0);
 #pragma unroll
         for (int g = 0; g < G; ++g) {
-          const T ux = wx ? twx : VG(r, g);
-          const T uy = wy ? twy : (r > 0 ? VG(r > 0 ? r - 1 : 0, g) : dny[g]);
-          const T uz = wz ? twz : ((tz >= 0) ? XP(prv, r, g, tz) : T(0));
-          const T jx = jump ? JX[g] : T(0);
+          // FP32: deviation form (u_a - T_L = m_a psi_a + t_a); FP64: T_o,
+          // the jump premultiplied (JX)
+          constexpr bool PSI = sizeof(T) == 4;
+          const T ub = r > 0 ? VG(r > 0 ? r - 1 : 0, g) : dny[g];
+          const T uzb = (tz >= 0) ? XP(prv, r, g, tz) : T(0);
+          const T ux = PSI ? (wx ? T(0) : VG(r, g)) + twx : (wx ? twx : VG(r, g));
+          const T uy = PSI ? (wy ? T(0) : ub) + twy : (wy ? twy : ub);
+          const T uz = PSI ? (wz ? T(0) : uzb) + twz : (wz ? twz : uzb);
+          const T jx = (!PSI && jump) ? JX[g] : T(0);
           T acc;
-          if (HAS_S) acc = src + jx;
+          if (PSI) acc = T(0);
+          else if (HAS_S) acc = src + jx;
           else acc = fma(src, A0[g], jx);
           acc = fma(AZ[g], uz, fma(AY[g], uy, fma(AX[g], ux, acc)));
           T val;

@@ -218,13 +218,14 @@ def config3() -> Workload:
                     sphere_quadrature(24, 12))
 
 
-def config3_reduced(n_bins: int = 3, n_phi: int = 8, n_mu: int = 4) -> Workload:
+def config3_reduced(n_bins: int = 2, n_phi: int = 8, n_mu: int = 2) -> Workload:
     """The 64x64x32 film mesh of ``config3`` (same cylinder, walls and
-    lengths) with fewer MFP bins and directions: 3 bins x (8 azimuthal x 4
-    polar) sphere directions, 96 ordinates.  Same mesh, faces and walls as
-    the full film; the smaller ordinate set is one whose per-ordinate sparse
-    factorisations fit a host's memory, so a converged FP64 reference exists
-    for the 3D kernels at the film's own mesh size."""
+    lengths) with fewer MFP bins and directions: 2 bins (1 nm and 10 um) x
+    (8 azimuthal x 2 polar) sphere directions, 32 ordinates.  Same mesh,
+    faces and walls as the full film; the smaller ordinate set is one whose
+    per-ordinate sparse factorisations (about 1 GB each on this mesh) fit a
+    host's memory, so a converged FP64 reference exists for the 3D kernels at
+    the film's own mesh size."""
     wl = config3()
     kappa_m, lambda_m = mfp_bins(n_bins)
     return dataclasses.replace(
