@@ -5,13 +5,17 @@ A float sweep stores App. A's upwind coefficients of E1, divided by its
 diagonal: A_a = fl(fl(beta_a) A0) with A0 = 1 / (1 + D).  Written as
 T_i = A0 s_i T_L,i + sum_a A_a u_a with A0 = fl(1 / (1 + D)) (the first
 mixed sweeps), the weight of T_L is a rounded number of its own; written in
-delta form T_i = T_L,i + sum_a A_a (u_a - T_L,i) (the current sweeps), it is
-1 - sum_a A_a exactly.  ``RoundedCoefficients`` is the oracle's transport
+delta form T_i = T_L,i + sum_a A_a (u_a - T_L,i) (the current sweeps, which
+carry psi = T - T_L), it is 1 - sum_a A_a exactly.  ``RoundedCoefficients`` is the oracle's transport
 with such rounded coefficients and everything else exact, so its FP64 fixed
 point shows what the rounding of the coefficients alone does;
 ``DeltaCoefficients`` the same for the delta form, optionally with the E2
 weights a_o rounded to float as well.  ``FloatTransport`` instead solves each
-ordinate in float32 (sparse LU) with the moments in FP64.
+ordinate in float32 (sparse LU) with the moments in FP64.  ``quantised_iteration``
+runs Algorithm 1 with exact solves but float-rounded carried values, either
+T_o itself (and the source s T_L) or the deviation psi_o = T_o - T_L: the
+first stalls where the slow diffusive mode's step falls below the float
+quantum, the second does not.
 """
 import copy
 
@@ -137,3 +141,27 @@ def tall_cell(ny, nx=16, length=100e-9):
     wl.shape = (nx, ny, 1)
     wl.lengths = (length, Ly, 0.0)
     return wl
+
+
+def quantised_iteration(pr, n_iter, form):
+    """Algorithm 1 from the Fourier first guess with the per-ordinate solves
+    exact and the values a float sweep would carry rounded to float: form
+    "T" rounds the source T_L and every T_o; form "psi" rounds only
+    psi_o = T_o - T_L (T_L and the moments stay FP64).  Returns max |T_L -
+    T_L*| against the exact fixed point after n_iter iterations (gauged)."""
+    ref = bte.solve_mode_B(pr, rtol=1e-13)
+    tr = bte.Transport(pr)
+    me, od = pr.mesh, pr.ords
+    wc = me.walls[:, 0]
+    T_L, T_w = bte.initial_guess(tr)
+    for _ in range(n_iter):
+        src = T_L.astype(f32).astype(np.float64) if form == "T" else T_L
+        TL_new, wn = np.zeros(me.nc), np.zeros(me.nw)
+        for o in range(od.n):
+            T = tr.lu(o).solve(tr.rhs(o, src, T_w))
+            T = T.astype(f32).astype(np.float64) if form == "T" else \
+                T_L + (T - T_L).astype(f32).astype(np.float64)
+            TL_new += od.a[o] * T
+            wn += tr.w_out[o] * T[wc]
+        T_L, T_w = TL_new, wn / tr.w_den
+    return float(np.abs(bte.gauge(T_L, T_w)[0] - ref.T_L).max())

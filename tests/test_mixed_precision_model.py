@@ -5,13 +5,17 @@ On the tall 16 x 96 test cell (a 1 nm and a 10 um bin) the first mixed sweep
 1.29e-5 K from the FP64 one.  These tests reproduce the separation of that
 error on the oracle: the float rounding of the transport coefficients alone
 gives about that much (mostly A0, and through the 1 nm bin), while float32
-transport solves with FP64 moments stay near 1e-7 K.  The delta form of the
-current sweeps, whose weight of T_L is exactly 1 - sum_a A_a, brings the
-coefficient floor below 1e-6 K even with float E2 weights.
+transport solves with FP64 moments stay near 1e-7 K.  The delta form,
+whose weight of T_L is exactly 1 - sum_a A_a, brings the coefficient floor
+below 1e-6 K even with float E2 weights; but a float sweep that carries T
+itself also quantises the source s T_L, and from the Fourier guess its
+slowly converging diffusive mode stalls on that quantum.  The current sweeps
+carry psi = T - T_L instead (both effects are reproduced here).
 """
 import numpy as np
 
-from mixed_model import FloatTransport, delta_form_floor, float_coefficient_floor, tall_cell
+from mixed_model import (FloatTransport, delta_form_floor, float_coefficient_floor,
+                         quantised_iteration, tall_cell)
 from oracle import bte
 
 
@@ -52,3 +56,15 @@ def test_delta_form_floor_below_the_bar():
         pr, ref = _ref(ny)
         assert delta_form_floor(pr, ref, float_weights=False) < 2e-7
         assert delta_form_floor(pr, ref) < 2e-6
+
+
+def test_float_source_stalls_and_deviations_do_not():
+    """Algorithm 1 on the 96-row cell from the Fourier guess, exact solves:
+    with T_L and T_o rounded to float the iteration stops moving about
+    1.5e-6 K from the fixed point (the same after 1000 and 1400 iterations);
+    with only psi = T - T_L rounded it keeps converging, two orders lower."""
+    pr, _ = _ref(96)
+    t1000 = quantised_iteration(pr, 1000, "T")
+    t1400 = quantised_iteration(pr, 1400, "T")
+    assert t1400 > 5e-7 and abs(t1400 - t1000) < 0.01 * t1400
+    assert quantised_iteration(pr, 1400, "psi") < 1e-8
