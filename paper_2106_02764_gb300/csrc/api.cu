@@ -103,6 +103,7 @@ struct obte_ctx {
   int G = 0, R = 0, threads = 0;
   bool warp = false;
   bool k3d = false;
+  int nh = 1;  // warps per group of the 2D warp kernel
   int items_pad = 1;  // 4: items padded for the warp kernel's block-combined moments
   std::vector<WorkItem> items_h;
   WorkItem* items_d = nullptr;
@@ -747,9 +748,10 @@ struct Variant {
   int G, R;
   bool warp;         // 2D warp-per-group kernel (sweep2d.cuh)
   bool k3d = false;  // 3D block kernel with skewed records (sweep3d.cuh)
+  int nh = 1;        // warps per group of the 2D warp kernel (2: rows fill 64 lanes)
 };
 
-const Variant kWarp2D_F[] = {{8, 8, true}, {8, 4, true}, {16, 4, true}, {16, 2, true},
+const Variant kWarp2D_F[] = {{8, 8, true}, {8, 4, true, false, 2}, {8, 4, true}, {16, 4, true}, {16, 2, true},
                              {16, 1, true}, {8, 1, true},  {6, 8, true},  {4, 8, true},
                              {4, 4, true},  {8, 2, true},  {8, 3, true},  {8, 5, true},
                              {8, 6, true}};
@@ -776,7 +778,10 @@ void push_fitting(std::vector<Variant>& out, const Variant (&v)[N], int precisio
                   int nz, bool has_s) {
   for (size_t i = 0; i < N; ++i) {
     if (ny % v[i].R != 0) continue;
-    if (v[i].warp) {
+    if (v[i].warp && v[i].nh == 2) {
+      if (dim != 2 || has_s || ny != 64 * v[i].R) continue;
+      if (!sweep2d_split_exists(precision, v[i].G, v[i].R)) continue;
+    } else if (v[i].warp) {
       if (dim != 2 || ny / v[i].R > 32) continue;
       if (!sweep2d_warp_exists(precision, v[i].G, v[i].R, has_s, true)) continue;
     } else if (v[i].k3d) {
@@ -868,7 +873,7 @@ static void build_items(obte_ctx* ctx, int geom, int G, std::vector<WorkItem>& i
 
 // allocate the iteration state for a precision / variant; fill gh and gd
 static int prepare_state(obte_ctx* ctx, int precision, int G, int R, bool warp, int max_iter,
-                         const obte_solve_opts& op, bool k3d = false) {
+                         const obte_solve_opts& op, bool k3d = false, int nh = 1) {
   cudaSetDevice(ctx->device);
   const int Nx = ctx->n[0], Ny = ctx->n[1], Nz = ctx->n[2];
   const int rows = Ny * Nz;
@@ -1062,14 +1067,16 @@ static int prepare_state(obte_ctx* ctx, int precision, int G, int R, bool warp, 
   ctx->R = R;
   ctx->warp = warp;
   ctx->k3d = k3d;
-  ctx->threads = warp ? 32 * sweep2d_warps_per_block(precision, G, R, ctx->has_s, true)
+  ctx->nh = warp ? nh : 1;
+  ctx->threads = warp ? (nh == 2 ? 256 : 32 * sweep2d_warps_per_block(precision, G, R, ctx->has_s, true))
                       : threads_for(Ny, Nz, R);
   std::vector<WorkItem> items;
   std::vector<int> ord_d0;
   // block-combined moments: warp kernel with four warps per block over full
   // 32-lane rows
-  ctx->items_pad = (warp && sweep2d_warps_per_block(precision, G, R, ctx->has_s, true) == 4 &&
-                    Ny == 32 * R)
+  ctx->items_pad = (warp && ((nh == 2 && Ny == 64 * R) ||
+                              (nh == 1 && sweep2d_warps_per_block(precision, G, R, ctx->has_s, true) == 4 &&
+                               Ny == 32 * R)))
                        ? 4
                        : 1;
   build_items(ctx, 0, G, items, &ord_d0, ctx->items_pad);
@@ -1103,6 +1110,12 @@ static int prepare_state(obte_ctx* ctx, int precision, int G, int R, bool warp, 
   return OBTE_OK;
 }
 
+// the context's 2D warp-kernel variant (one- or two-warp groups)
+static cudaError_t launch_ctx_warp(obte_ctx* ctx, const SweepLaunch& L) {
+  if (ctx->nh == 2) return launch_sweep2d_split(L, ctx->precision, ctx->G, ctx->R, 0, ctx->stream);
+  return launch_sweep2d_warp(L, ctx->precision, ctx->G, ctx->R, ctx->has_s, true, 0, ctx->stream);
+}
+
 static cudaError_t sweep_once(obte_ctx* ctx, int flags) {
   SweepLaunch L;
   L.geoms = ctx->gd;
@@ -1110,8 +1123,7 @@ static cudaError_t sweep_once(obte_ctx* ctx, int flags) {
   L.n_items = (int)ctx->items_h.size();
   L.flags = flags | (ctx->warp && ctx->items_pad == 4 ? SWEEP_BLOCK_COMBINE : 0);
   L.item_counter = nullptr;
-  if (ctx->warp)
-    return launch_sweep2d_warp(L, ctx->precision, ctx->G, ctx->R, ctx->has_s, true, 0, ctx->stream);
+  if (ctx->warp) return launch_ctx_warp(ctx, L);
   if (ctx->k3d)
     return launch_sweep3d(L, ctx->precision, ctx->G, ctx->R, ctx->has_s, ctx->threads,
                           sweep3d_smem_bytes(ctx->precision, ctx->G, ctx->R, ctx->threads), ctx->stream);
@@ -1217,7 +1229,7 @@ static int pick_variant(obte_ctx* ctx, int precision, const obte_solve_opts& op,
     for (auto& c : cands) {
       const long units = (ctx->O + c.G - 1) / c.G;
       if (units < sms) continue;
-      if (pass == 0 && c.warp && ctx->n[1] / c.R != 32) continue;
+      if (pass == 0 && c.warp && ctx->n[1] / c.R != 32 * c.nh) continue;
       *out = c;
       return OBTE_OK;
     }
@@ -1236,7 +1248,7 @@ static int autotune(obte_ctx* ctx, int precision, const obte_solve_opts& op, Var
   float best = 1e30f;
   Variant bv = cands[0];
   for (auto& c : cands) {
-    int rc = prepare_state(ctx, precision, c.G, c.R, c.warp, 1 << 30, op, c.k3d);
+    int rc = prepare_state(ctx, precision, c.G, c.R, c.warp, 1 << 30, op, c.k3d, c.nh);
     if (rc) return rc;
     obte_solve_opts o2 = op;
     o2.fourier_max_iter = 1;
@@ -1390,7 +1402,7 @@ extern "C" int obte_solve(obte_ctx* ctx, const obte_solve_opts* opts, obte_solve
   Variant v;
   int rc = (op.group_size < 0) ? autotune(ctx, prec, op, &v) : pick_variant(ctx, prec, op, &v);
   if (rc) return rc;
-  rc = prepare_state(ctx, prec, v.G, v.R, v.warp, op.max_iter, op, v.k3d);
+  rc = prepare_state(ctx, prec, v.G, v.R, v.warp, op.max_iter, op, v.k3d, v.nh);
   if (rc) return rc;
   ctx->flux_done = false;
   cudaEvent_t e0, e1, e2;
@@ -1492,7 +1504,7 @@ extern "C" int obte_shard_begin(obte_ctx* ctx, const obte_solve_opts* opts) {
   Variant v;
   int rc = pick_variant(ctx, prec, op, &v);
   if (rc) return rc;
-  rc = prepare_state(ctx, prec, v.G, v.R, v.warp, op.max_iter, op, v.k3d);
+  rc = prepare_state(ctx, prec, v.G, v.R, v.warp, op.max_iter, op, v.k3d, v.nh);
   if (rc) return rc;
   ctx->flux_done = false;
   rc = init_from_fourier(ctx, op, nullptr);
@@ -1812,7 +1824,7 @@ extern "C" int obte_kappa_grad_s(obte_ctx* ctx, double* out, size_t max_field_by
     L.flags = SWEEP_RECORD;
     L.item_counter = nullptr;
     if (ctx->warp) {
-      CK(launch_sweep2d_warp(L, ctx->precision, ctx->G, ctx->R, ctx->has_s, true, 0, ctx->stream));
+      CK(launch_ctx_warp(ctx, L));
     } else if (ctx->k3d) {
       CK(launch_sweep3d(L, ctx->precision, ctx->G, ctx->R, ctx->has_s, ctx->threads,
                         sweep3d_smem_bytes(ctx->precision, ctx->G, ctx->R, ctx->threads), ctx->stream));
@@ -2443,7 +2455,7 @@ extern "C" int obte_kappa_grad_s_noalloc(obte_ctx* ctx, double* out) {
     L.flags = SWEEP_RECORD;
     L.item_counter = nullptr;
     if (ctx->warp) {
-      CK(launch_sweep2d_warp(L, ctx->precision, ctx->G, ctx->R, ctx->has_s, true, 0, ctx->stream));
+      CK(launch_ctx_warp(ctx, L));
     } else if (ctx->k3d) {
       CK(launch_sweep3d(L, ctx->precision, ctx->G, ctx->R, ctx->has_s, ctx->threads,
                         sweep3d_smem_bytes(ctx->precision, ctx->G, ctx->R, ctx->threads), ctx->stream));

@@ -168,6 +168,11 @@ cudaError_t launch_sweep3d(const SweepLaunch& L, int precision, int G, int RMAX,
 bool sweep3d_exists(int precision, int G, int RMAX, bool has_s);
 size_t sweep3d_smem_bytes(int precision, int G, int RMAX, int threads);
 int sweep2d_warps_per_block(int precision, int G, int RMAX, bool has_s, bool rfixed);
+// 2D warp kernel with two-warp groups (rows fill 64 lanes; eight warps, four
+// groups per block; FP32 without s(x))
+cudaError_t launch_sweep2d_split(const SweepLaunch& L, int precision, int G, int RMAX, int blocks,
+                                 cudaStream_t st);
+bool sweep2d_split_exists(int precision, int G, int RMAX);
 cudaError_t launch_sweep(const SweepLaunch& L, int precision, int dim, int G, int RMAX,
                          bool has_s, int threads, int blocks, size_t smem, cudaStream_t st);
 size_t sweep_smem_bytes(int precision, int dim, int G, int RMAX, int threads);

@@ -75,6 +75,25 @@ bool sweep2d_warp_exists(int precision, int G, int RMAX, bool has_s, bool rfixed
   return false;
 }
 
+#define OBTE_MATCH2DS(T, GG, RR) (precision == prec_of((T*)nullptr) && G == GG && RMAX == RR)
+
+cudaError_t launch_sweep2d_split(const SweepLaunch& L, int precision, int G, int RMAX, int blocks,
+                                 cudaStream_t st) {
+#define X(T, GG, RR) \
+  if (OBTE_MATCH2DS(T, GG, RR)) return OBTE_SWEEP2D_W2_NAME(T, GG, RR)(&L, blocks, st, nullptr);
+  OBTE_SWEEP2D_W2(X)
+#undef X
+  return cudaErrorInvalidValue;
+}
+
+bool sweep2d_split_exists(int precision, int G, int RMAX) {
+#define X(T, GG, RR) \
+  if (OBTE_MATCH2DS(T, GG, RR)) return true;
+  OBTE_SWEEP2D_W2(X)
+#undef X
+  return false;
+}
+
 #define OBTE_MATCH3D(T, GG, RR, SS) \
   (precision == prec_of((T*)nullptr) && G == GG && RMAX == RR && has_s == SS)
 

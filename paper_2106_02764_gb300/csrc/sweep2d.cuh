@@ -135,12 +135,16 @@ __device__ __noinline__ double cell_epilogue_2d(const GeomDev& gm, const T* __re
 // (G = 6) or 15 (G = 4) resident warps per SM: more warps hide the latencies
 // of a step, and single-warp blocks spread the groups evenly over the SMs.
 // NST: record buffers per warp (copies run NST - 1 steps ahead).
-template <typename T, int G, int RMAX>
+// NH = 2: a group spans two warps (rows 0 .. 32 R - 1 and 32 R .. 64 R - 1),
+// four groups of one octant and start column per block of eight warps, two
+// blocks per SM under a 128-register budget: twice the resident warps of the
+// one-warp form at the same ordinates per lane.
+template <typename T, int G, int RMAX, int NH = 1>
 struct WarpCfg {
-  static constexpr bool NARROW = sizeof(T) == 4 && G < 8 && RMAX >= 8;
+  static constexpr bool NARROW = NH == 1 && sizeof(T) == 4 && G < 8 && RMAX >= 8;
   static constexpr int NST = 2;
-  static constexpr int WPB = NARROW ? 1 : ((sizeof(T) == 8 && RMAX >= 8) ? 2 : 4);
-  static constexpr int MINB = NARROW ? (G <= 4 ? 15 : 12) : ((G * (int)sizeof(T) <= 16) ? 4 : 1);
+  static constexpr int WPB = NH == 2 ? 8 : (NARROW ? 1 : ((sizeof(T) == 8 && RMAX >= 8) ? 2 : 4));
+  static constexpr int MINB = NH == 2 ? 2 : (NARROW ? (G <= 4 ? 15 : 12) : ((G * (int)sizeof(T) <= 16) ? 4 : 1));
 };
 
 // Shared-memory slot of the record of (lane, register row r): each 16-byte
@@ -163,33 +167,48 @@ __device__ __forceinline__ int rec_slot(int lane, int r) {
 // PASS: a flux / record pass (flags SWEEP_FLUX or SWEEP_RECORD); the
 // iteration sweeps are built without the out-of-line epilogue call, so no
 // registers are saved around it in the hot loop.
-template <typename T, int G, int RMAX, bool HAS_S, bool RFIXED, bool PASS>
-__global__ void __launch_bounds__(32 * WarpCfg<T, G, RMAX>::WPB, WarpCfg<T, G, RMAX>::MINB)
+// NH = 2 (RFIXED, FP32 without s(x), ny = 64 RMAX, one item per group, no
+// work queue): warps w and w + 4 of a block hold the lower and upper half of
+// group w's rows; the row below a half's lowest row comes from the other
+// half's top row of the previous step through shared memory, across the
+// block barrier every step ends with.  A block whose item list runs out
+// keeps its warps in the loop on an empty item (no early exit before a
+// barrier).
+template <typename T, int G, int RMAX, bool HAS_S, bool RFIXED, bool PASS, int NH = 1>
+__global__ void __launch_bounds__(32 * WarpCfg<T, G, RMAX, NH>::WPB, WarpCfg<T, G, RMAX, NH>::MINB)
     sweep2d_warp_kernel(const SweepLaunch L) {
-  constexpr int WPB = WarpCfg<T, G, RMAX>::WPB;
+  constexpr int WPB = WarpCfg<T, G, RMAX, NH>::WPB;
   constexpr int CH = (4 * sizeof(T)) / 16;  // 16-byte parts per record
-  constexpr int NST = WarpCfg<T, G, RMAX>::NST;
+  constexpr int NST = WarpCfg<T, G, RMAX, NH>::NST;
+  static_assert(NH == 1 || (RFIXED && sizeof(T) == 4 && !HAS_S && G % 2 == 0), "two-warp groups: FP32 pairs");
   __shared__ __align__(16) uint4 recbuf[WPB][NST][CH][32 * RMAX];
-  __shared__ __align__(16) T scratch_all[WPB][32][G];
+  // a cell's G values for the out-of-line epilogue (two-warp groups: a
+  // thread-local array, which keeps the static shared memory under 48 KB)
+  __shared__ __align__(16) T scratch_all[NH == 1 ? WPB : 1][32][G];
   __shared__ __align__(16) T kcoef[WPB][2][G];  // |K_gx|, |K_gy| of the warp's group (rare path only)
   // a step's T_L partials of every warp, by row (two step parities)
   __shared__ __align__(16) T tlbuf[2][WPB][32 * RMAX];
+  // two-warp groups: top row of each half, by step parity
+  __shared__ __align__(16) T xch[NH == 2 ? 2 : 1][4][2][G];
   const int lane = threadIdx.x & 31;
   const int wib = threadIdx.x >> 5;
-  T* scratch = &scratch_all[wib][lane][0];
+  T* scratch = &scratch_all[NH == 1 ? wib : 0][lane][0];
   const int flags = L.flags;
   constexpr bool rare_pass = PASS;
   const unsigned FULL = 0xffffffffu;
+  const int gi = NH == 2 ? (wib & 3) : wib;    // group of the block
+  const int half = NH == 2 ? (wib >> 2) : 0;   // half of the group's rows
 
-  int item = blockIdx.x * WPB + wib;
+  int item = NH == 2 ? blockIdx.x * 4 + gi : blockIdx.x * WPB + wib;
   for (;;) {
     if (L.item_counter) {
       int it = 0;
       if (lane == 0) it = atomicAdd(L.item_counter, 1);
       item = __shfl_sync(FULL, it, 0);
     }
-    if (item >= L.n_items) return;
-    const WorkItem wi = L.items[item];
+    if (NH == 1 && item >= L.n_items) return;
+    WorkItem wi = L.items[item < L.n_items ? item : 0];
+    if (item >= L.n_items) wi.count = 0;  // (NH = 2) an empty group
     const GeomDev& gm = L.geoms[wi.geom];
     if (*(volatile const int*)gm.done) {
       if (!L.item_counter) return;
@@ -204,8 +223,10 @@ __global__ void __launch_bounds__(32 * WarpCfg<T, G, RMAX>::WPB, WarpCfg<T, G, R
     const int sy = (q & 2) ? -1 : 1;
     const int o0 = wi.o0, cnt = wi.count, d0 = wi.d0;
     const double dT = gm.dT;
-    const bool active = lane < tpp;
-    const int j0 = lane * R;
+    const bool active = NH == 2 || lane < tpp;
+    const int jl = lane * R;                   // first row of the lane within the warp's rows
+    const int rh = NH == 2 ? half * 32 * RMAX : 0;  // first row of the warp's rows
+    const int j0 = rh + jl;
     const T* __restrict__ recq = reinterpret_cast<const T*>(gm.rec4) + (size_t)q * nx * ny * 4;
     double* tl_acc = gm.TL_acc;
     double* tlq = gm.tlq ? gm.tlq + (size_t)q * nx * ny : nullptr;
@@ -285,9 +306,9 @@ __global__ void __launch_bounds__(32 * WarpCfg<T, G, RMAX>::WPB, WarpCfg<T, G, R
       const int jr = m / CH, c = m % CH;
       pslot[k] = (unsigned)__cvta_generic_to_shared(&recbuf[wib][0][c][rec_slot<RMAX>(jr / RMAX, jr % RMAX)]);
     }
-    const bool full_run = ny * CH >= 32 * RMAX * CH;  // every lane copies every k
+    const bool full_run = NH == 2 || ny * CH >= 32 * RMAX * CH;  // every lane copies every k
     auto prefetch = [&](int s, int b) {
-      const char* g0 = reinterpret_cast<const char*>(recq + (size_t)s * ny * 4);
+      const char* g0 = reinterpret_cast<const char*>(recq + ((size_t)s * ny + rh) * 4);
       if (RFIXED && full_run) {
         CpRun<0, RMAX * CH, KP, CH>::go(pslot, (unsigned)(b * CH * 32 * RMAX * 16), g0 + lane * 16);
       } else if (RFIXED) {
@@ -342,8 +363,8 @@ __global__ void __launch_bounds__(32 * WarpCfg<T, G, RMAX>::WPB, WarpCfg<T, G, R
     // one start column, so row j's partials of the four warps are added in
     // shared memory (FP32, fixed order) and each warp issues the atomics of a
     // quarter of the rows: a block barrier per step, a quarter of the atomics
-    const bool comb = WPB == 4 && RFIXED && full_run && tr_atom && (flags & SWEEP_BLOCK_COMBINE) &&
-                      !L.item_counter;
+    const bool comb = (WPB == 4 || NH == 2) && RFIXED && full_run && tr_atom &&
+                      (flags & SWEEP_BLOCK_COMBINE) && !L.item_counter;
     int par = 0;
     // hot-face flux: each row crosses the hot column once per sweep, so its
     // sum_g K_gx T_g is kept per row in the sweep precision and widened once
@@ -353,6 +374,13 @@ __global__ void __launch_bounds__(32 * WarpCfg<T, G, RMAX>::WPB, WarpCfg<T, G, R
     int n_hot = 0;
     // diagonals of steps d .. d + NST - 2 are in flight at the top of step d
     // (they wrap around nx, so the copies past the last step stay in bounds)
+    if constexpr (NH == 2) {
+      // the other half reads this half's top row of "step -1" at step 0
+      if (lane == 31)
+#pragma unroll
+        for (int g = 0; g < G; ++g) xch[1][gi][half][g] = VG(RMAX - 1, g);
+      __syncthreads();
+    }
     int s = d0;
     int sf = d0;  // diagonal of the next copy
 #pragma unroll
@@ -376,6 +404,15 @@ __global__ void __launch_bounds__(32 * WarpCfg<T, G, RMAX>::WPB, WarpCfg<T, G, R
           dn0[h].y = __shfl_sync(FULL, v[RMAX - 1][h].y, below);
         } else {
           dn0[h] = __shfl_sync(FULL, v[RMAX - 1][h], below);
+        }
+      }
+      if constexpr (NH == 2) {
+        // lane 0: the other half's top row of the previous step (for the
+        // lower half across the y period; a wall's record ignores it)
+        if (lane == 0) {
+          const float2* xo = reinterpret_cast<const float2*>(&xch[(d + 1) & 1][gi][half ^ 1][0]);
+#pragma unroll
+          for (int h = 0; h < GV; ++h) dn0[h] = xo[h];
         }
       }
       if (active) {
@@ -481,8 +518,10 @@ __global__ void __launch_bounds__(32 * WarpCfg<T, G, RMAX>::WPB, WarpCfg<T, G, R
             const bool last = packed & REC_LAST;
             if constexpr (PASS) {
 #pragma unroll
-              for (int g = 0; g < G; ++g) scratch[g] = VG(r, g);
-              phi += cell_epilogue_2d<T, G>(gm, scratch, cell, packed, last, o0, cnt, sx, sy,
+              T loc[NH == 2 ? G : 1];
+              T* sc = NH == 2 ? loc : scratch;
+              for (int g = 0; g < G; ++g) sc[g] = VG(r, g);
+              phi += cell_epilogue_2d<T, G>(gm, sc, cell, packed, last, o0, cnt, sx, sy,
                                             flags, kx_sum);
               continue;
             }
@@ -507,7 +546,7 @@ __global__ void __launch_bounds__(32 * WarpCfg<T, G, RMAX>::WPB, WarpCfg<T, G, R
         if (tr_atom) {
 #pragma unroll
           for (int r = 0; r < RMAX; ++r)
-            if (RFIXED || r >= rb) tlbuf[par][wib][j0 + r - rb] = (pk[r] & REC_SOLID) ? tls[r] : T(0);
+            if (RFIXED || r >= rb) tlbuf[par][wib][jl + r - rb] = (pk[r] & REC_SOLID) ? tls[r] : T(0);
         } else {
 #pragma unroll
           for (int r = 0; r < RMAX; ++r)
@@ -515,30 +554,42 @@ __global__ void __launch_bounds__(32 * WarpCfg<T, G, RMAX>::WPB, WarpCfg<T, G, R
               atomicAdd(tl_acc + (pk[r] & REC_CELL_MASK), X2 ? widen(tls[r]) : (double)tls[r]);
         }
       }
+      if constexpr (NH == 2) {
+        if (lane == 31)
+#pragma unroll
+          for (int h = 0; h < GV; ++h)
+            reinterpret_cast<float2*>(&xch[d & 1][gi][half][0])[h] = v[RMAX - 1][h];
+      }
       if (comb) {
         __syncthreads();
-        // warp wib adds the quarter of the 32 RMAX rows starting at
-        // wib * 8 RMAX: row wib * 8 RMAX + 32 k + lane for 32 k + lane < 8 RMAX
-        // (fewer than 32 rows for RMAX < 4: the other lanes idle)
+        // warp wib adds the quarter of the 32 RMAX rows (of its half, NH = 2)
+        // starting at gi * 8 RMAX: row gi * 8 RMAX + 32 k + lane for
+        // 32 k + lane < 8 RMAX (fewer than 32 rows for RMAX < 4: the other
+        // lanes idle); the four warps of a half hold the same rows
         constexpr int RQ = (8 * RMAX + 31) / 32;
+        const int w0 = NH == 2 ? half * 4 : 0;
 #pragma unroll
         for (int k = 0; k < RQ; ++k) {
           const int local = 32 * k + lane;
-          const int j = wib * 8 * RMAX + local;
+          const int j = gi * 8 * RMAX + local;
           if ((8 * RMAX) % 32 == 0 || local < 8 * RMAX) {
-            const T t01 = tlbuf[par][0][j] + tlbuf[par][1][j];
-            const T t23 = tlbuf[par][2][j] + tlbuf[par][3][j];
-            atomicAdd(tlq + (size_t)s * ny + j, (double)(t01 + t23));
+            const T t01 = tlbuf[par][w0 + 0][j] + tlbuf[par][w0 + 1][j];
+            const T t23 = tlbuf[par][w0 + 2][j] + tlbuf[par][w0 + 3][j];
+            atomicAdd(tlq + (size_t)s * ny + rh + j, (double)(t01 + t23));
           }
         }
         par ^= 1;
       } else if (tr_atom) {
-        __syncwarp();
-        double* row = tlq + (size_t)s * ny + lane;
+        if (NH == 2) __syncthreads();  // the exchange of the top rows
+        else __syncwarp();
+        double* row = tlq + (size_t)s * ny + rh + lane;
 #pragma unroll
         for (int r = 0; r < RMAX; ++r)
           if (RFIXED && full_run ? true : 32 * r + lane < ny)
             atomicAdd(row + 32 * r, (double)tlbuf[par][wib][32 * r + lane]);
+        if (NH == 2) par ^= 1;
+      } else if (NH == 2) {
+        __syncthreads();
       }
       s = s_next;
       cur = (cur + 1 == NST) ? 0 : cur + 1;

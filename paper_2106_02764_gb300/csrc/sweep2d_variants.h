@@ -71,3 +71,31 @@ OBTE_SWEEP2D_VARIANTS(OBTE_SWEEP2D_DECLARE)
       obte::sweep2d_warp_kernel<T, G, R, S, F, false><<<b, 32 * wpb, 0, st>>>(*L);              \
     return cudaGetLastError();                                                                 \
   }
+
+// Two-warp groups (NH = 2, sweep2d_warp_kernel): X(T, G, RMAX), FP32 without
+// s(x), rows fill 64 lanes (ny = 64 RMAX), four groups per block of eight
+// warps.
+#define OBTE_SWEEP2D_W2(X) X(float, 8, 4)
+
+#define OBTE_SWEEP2D_W2_NAME(T, G, R) obte_sweep2d_split_##T##_##G##_##R
+#define OBTE_SWEEP2D_W2_DECLARE(T, G, R) \
+  cudaError_t OBTE_SWEEP2D_W2_NAME(T, G, R)(const SweepLaunch* L, int blocks, cudaStream_t st, int* wpb);
+OBTE_SWEEP2D_W2(OBTE_SWEEP2D_W2_DECLARE)
+
+#define OBTE_SWEEP2D_W2_DEFINE(T, G, R)                                                        \
+  cudaError_t OBTE_SWEEP2D_W2_NAME(T, G, R)(const SweepLaunch* L, int blocks, cudaStream_t st, \
+                                            int* wpb_out) {                                  \
+    constexpr int wpb = obte::WarpCfg<T, G, R, 2>::WPB;                                       \
+    if (!L) {                                                                                \
+      *wpb_out = wpb;                                                                        \
+      return cudaSuccess;                                                                    \
+    }                                                                                        \
+    if (L->item_counter) return cudaErrorInvalidValue;                                        \
+    const int need = (L->n_items + 3) / 4;                                                   \
+    const int b = (blocks > 0 && blocks < need) ? blocks : need;                             \
+    if (L->flags & (SWEEP_FLUX | SWEEP_RECORD))                                              \
+      obte::sweep2d_warp_kernel<T, G, R, false, true, true, 2><<<b, 32 * wpb, 0, st>>>(*L);   \
+    else                                                                                     \
+      obte::sweep2d_warp_kernel<T, G, R, false, true, false, 2><<<b, 32 * wpb, 0, st>>>(*L);  \
+    return cudaGetLastError();                                                               \
+  }

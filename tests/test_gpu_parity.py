@@ -231,12 +231,13 @@ def test_fma_rate_measurement():
 
 
 @pytest.mark.parametrize("ny,G,R", [(32, 8, 1), (32, 16, 1), (64, 8, 2), (64, 16, 2), (96, 8, 3),
-                                    (160, 8, 5), (192, 8, 6)])
+                                    (160, 8, 5), (192, 8, 6), (256, 8, 4)])
 def test_full_lane_variants_block_combine(ny, G, R):
-    """Fixed-rows variants whose rows fill the 32 lanes (N_y = 32 R) add the four
-    warps' moments of a block in shared memory before the atomics; every row
-    range must be added once, also with fewer than four or a number of rows per
-    lane that is not a power of two (plain record-slot order).
+    """Fixed-rows variants whose rows fill the 32 lanes (N_y = 32 R), or the 64
+    lanes of a two-warp group (N_y = 64 R), add the four groups' moments of a
+    block in shared memory before the atomics; every row range must be added
+    once, also with fewer than four or a number of rows per lane that is not a
+    power of two (plain record-slot order).
 
     The row-combining logic is checked against the 8 x 8 variant on the same
     mesh, whose rows fill at most 24 lanes, so that each warp issues its own
@@ -258,6 +259,8 @@ def test_full_lane_variants_block_combine(ny, G, R):
     pr, ref = oracle(wl)
     s, st = gpu(wl, "mixed", group_size=G, rows_per_thread=R)
     assert st["group_size"] == G and st["rows_per_thread"] == R and st["kernel"] == 2
+    if ny == 64 * R:  # two-warp groups: eight warps per block
+        assert st["threads_per_block"] == 256
     b, sb = gpu(wl, "mixed", group_size=8, rows_per_thread=8)
     assert sb["rows_per_thread"] == 8 and sb["kernel"] == 2
     TL, TLb = solid_vector(pr, s.T_L()), solid_vector(pr, b.T_L())
