@@ -366,12 +366,37 @@ __global__ void __launch_bounds__(32 * WarpCfg<T, G, RMAX, NH>::WPB, WarpCfg<T, 
     const bool comb = (WPB == 4 || NH == 2) && RFIXED && full_run && tr_atom &&
                       (flags & SWEEP_BLOCK_COMBINE) && !L.item_counter;
     int par = 0;
+    // block-combined moments of a step, done one step later (after the next
+    // step's rows, so that their loads overlap that step's arithmetic)
+    auto comb_rows = [&](int s_c, int par_c) {
+      constexpr int RQ = (8 * RMAX + 31) / 32;
+      const int w0 = NH == 2 ? half * 4 : 0;
+#pragma unroll
+      for (int k = 0; k < RQ; ++k) {
+        const int local = 32 * k + lane;
+        const int j = gi * 8 * RMAX + local;
+        if ((8 * RMAX) % 32 == 0 || local < 8 * RMAX) {
+          const T t01 = tlbuf[par_c][w0 + 0][j] + tlbuf[par_c][w0 + 1][j];
+          const T t23 = tlbuf[par_c][w0 + 2][j] + tlbuf[par_c][w0 + 3][j];
+          atomicAdd(tlq + (size_t)s_c * ny + rh + j, (double)(t01 + t23));
+        }
+      }
+    };
+    int s_prev = -1;
     // hot-face flux: each row crosses the hot column once per sweep, so its
     // sum_g K_gx T_g is kept per row in the sweep precision and widened once
     T hot[RMAX];
 #pragma unroll
     for (int r = 0; r < RMAX; ++r) hot[r] = T(0);
     int n_hot = 0;
+    // Hot column without a branch (FP32 pairs, fixed rows, nx a multiple of
+    // the rows per lane): at step d the rows at the hot column are the rows
+    // j = d + d0 + 1 (mod nx), all at register row (d + d0 + 1) mod RMAX of
+    // their lanes, so every lane adds that register row's K_x dot under a
+    // predicate inside the row loop and keeps it where the row is hot
+    const bool uni_hot = X2 && RFIXED && !PASS && (nx % RMAX == 0) && ((RMAX & (RMAX - 1)) == 0);
+    float hot8 = 0.f;     // this lane's hot-row fluxes of up to RMAX steps
+    double hot_d = 0.0;   // and their sum
     // diagonals of steps d .. d + NST - 2 are in flight at the top of step d
     // (they wrap around nx, so the copies past the last step stay in bounds)
     if constexpr (NH == 2) {
@@ -418,6 +443,18 @@ __global__ void __launch_bounds__(32 * WarpCfg<T, G, RMAX, NH>::WPB, WarpCfg<T, 
       if (active) {
         uint32_t pk[RMAX];
         T tls[RMAX];
+        // uniform hot column: the hot row of this step is register row rs of
+        // whichever lane holds it; its K_x dot accumulates under a predicate
+        const int rs = (d + d0 + 1) & (RMAX - 1);
+        float2 hk = make_float2(0.f, 0.f);
+        uint32_t pkh = 0;
+        VV K2v[X2 ? GV : 1];
+        if constexpr (X2) {
+          if (uni_hot) {
+#pragma unroll
+            for (int h = 0; h < GV; ++h) K2v[h] = reinterpret_cast<const float2*>(kcoef[wib][0])[h];
+          }
+        }
         // branch-free update of all rows of the step (top row first: the row
         // below still holds its previous value, the y upwind neighbour)
 #pragma unroll
@@ -455,7 +492,9 @@ __global__ void __launch_bounds__(32 * WarpCfg<T, G, RMAX, NH>::WPB, WarpCfg<T, 
                 acc = __ffma2_rn(AXv[h], ux, acc);
                 v[r][h] = acc;
                 tlp = __ffma2_rn(AWv[h], acc, tlp);
+                if (uni_hot && r == rs) hk = __ffma2_rn(K2v[h], acc, hk);
               }
+              if (uni_hot && r == rs) pkh = packed;
               pk[r] = packed;
               tls[r] = tlp.x + tlp.y;
             } else {
@@ -490,7 +529,9 @@ __global__ void __launch_bounds__(32 * WarpCfg<T, G, RMAX, NH>::WPB, WarpCfg<T, 
             }
           }
         }
-        constexpr uint32_t RARE = REC_WOUT_X | REC_WOUT_Y | REC_LAST;
+        if (comb && s_prev >= 0) comb_rows(s_prev, par ^ 1);
+        // walls per row; the hot column per row too unless uni_hot took it
+        const uint32_t RARE = REC_WOUT_X | REC_WOUT_Y | (uni_hot ? 0u : (uint32_t)REC_LAST);
         uint32_t any = 0;
 #pragma unroll
         for (int r = 0; r < RMAX; ++r)
@@ -525,7 +566,7 @@ __global__ void __launch_bounds__(32 * WarpCfg<T, G, RMAX, NH>::WPB, WarpCfg<T, 
                                             flags, kx_sum);
               continue;
             }
-            if (packed & (REC_WOUT_X | REC_LAST)) {
+            if (packed & (REC_WOUT_X | (uni_hot ? 0u : (uint32_t)REC_LAST))) {
               const T sk = kdot(KX, KXr, r);
               if (packed & REC_WOUT_X) {
                 atomicAdd(wacc + (size_t)cell * 6 + out_x_side, widen(sk));
@@ -537,6 +578,18 @@ __global__ void __launch_bounds__(32 * WarpCfg<T, G, RMAX, NH>::WPB, WarpCfg<T, 
             if (packed & REC_WOUT_Y) {
               const T sy_k = kdot(KY, KYr, r);
               atomicAdd(wacc + (size_t)cell * 6 + out_y_side, widen(sy_k));
+            }
+          }
+        }
+        if constexpr (X2 && RFIXED && !PASS) {
+          if (uni_hot) {
+            if ((pkh & (REC_LAST | REC_SOLID | REC_WOUT_X)) == (REC_LAST | REC_SOLID)) {
+              hot8 += hk.x + hk.y;
+              ++n_hot;
+            }
+            if (rs == RMAX - 1) {
+              hot_d += widen(hot8);
+              hot8 = 0.f;
             }
           }
         }
@@ -562,22 +615,7 @@ __global__ void __launch_bounds__(32 * WarpCfg<T, G, RMAX, NH>::WPB, WarpCfg<T, 
       }
       if (comb) {
         __syncthreads();
-        // warp wib adds the quarter of the 32 RMAX rows (of its half, NH = 2)
-        // starting at gi * 8 RMAX: row gi * 8 RMAX + 32 k + lane for
-        // 32 k + lane < 8 RMAX (fewer than 32 rows for RMAX < 4: the other
-        // lanes idle); the four warps of a half hold the same rows
-        constexpr int RQ = (8 * RMAX + 31) / 32;
-        const int w0 = NH == 2 ? half * 4 : 0;
-#pragma unroll
-        for (int k = 0; k < RQ; ++k) {
-          const int local = 32 * k + lane;
-          const int j = gi * 8 * RMAX + local;
-          if ((8 * RMAX) % 32 == 0 || local < 8 * RMAX) {
-            const T t01 = tlbuf[par][w0 + 0][j] + tlbuf[par][w0 + 1][j];
-            const T t23 = tlbuf[par][w0 + 2][j] + tlbuf[par][w0 + 3][j];
-            atomicAdd(tlq + (size_t)s * ny + rh + j, (double)(t01 + t23));
-          }
-        }
+        s_prev = s;
         par ^= 1;
       } else if (tr_atom) {
         if (NH == 2) __syncthreads();  // the exchange of the top rows
@@ -595,6 +633,7 @@ __global__ void __launch_bounds__(32 * WarpCfg<T, G, RMAX, NH>::WPB, WarpCfg<T, 
       cur = (cur + 1 == NST) ? 0 : cur + 1;
       __syncwarp();
     }
+    if (comb && s_prev >= 0) comb_rows(s_prev, par ^ 1);  // the last step's moments
     cp_async_wait<0>();  // copies past the last step land before the buffers are reused
     __syncwarp();
 
@@ -610,6 +649,8 @@ __global__ void __launch_bounds__(32 * WarpCfg<T, G, RMAX, NH>::WPB, WarpCfg<T, 
       const double dk = widen(hot[r]);
       phi += sx > 0 ? dk : -dk;
     }
+    hot_d += widen(hot8);
+    phi += sx > 0 ? hot_d : -hot_d;
     if (sx > 0) phi += (double)n_hot * dT * kx_sum;
     for (int o = 16; o > 0; o >>= 1) phi += __shfl_xor_sync(FULL, phi, o);
     if (lane == 0 && phi != 0.0) atomicAdd(gm.phi_acc, phi);
