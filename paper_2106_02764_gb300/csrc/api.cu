@@ -1111,8 +1111,12 @@ static int prepare_state(obte_ctx* ctx, int precision, int G, int R, bool warp, 
 }
 
 // the context's 2D warp-kernel variant (one- or two-warp groups)
+// (after a batched solve the context's rows per lane may have no fixed-rows
+// instance: the general-rows instance then serves its flux and record passes)
 static cudaError_t launch_ctx_warp(obte_ctx* ctx, const SweepLaunch& L) {
   if (ctx->nh == 2) return launch_sweep2d_split(L, ctx->precision, ctx->G, ctx->R, 0, ctx->stream);
+  if (!sweep2d_warp_exists(ctx->precision, ctx->G, ctx->R, ctx->has_s, true))
+    return launch_sweep2d_warp(L, ctx->precision, ctx->G, 8, ctx->has_s, false, 0, ctx->stream);
   return launch_sweep2d_warp(L, ctx->precision, ctx->G, ctx->R, ctx->has_s, true, 0, ctx->stream);
 }
 
