@@ -53,6 +53,7 @@ def _args():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--no-extra", action="store_true", help="skip the config-3 / config-4 / sharded legs")
     return ap.parse_args()
 
 
@@ -162,20 +163,147 @@ def reference_arm(a, rank, world):
 
 
 # --------------------------------------------------------------------------- GPU arm
-def time_to_kappa(stats, kappa_star, rtol=1e-4):
-    """Device time from solve entry to the first iterate within rtol of kappa*
-    that stays within it (Fourier guess + that many iterations)."""
-    h = np.array(stats["kappa_history"])
+def crossing(history, kappa_star, rtol=1e-4):
+    """Iterations until kappa_n is within rtol of kappa* and stays within it."""
+    h = np.array(history)
     ok = np.abs(h - kappa_star) <= rtol * abs(kappa_star)
     if not ok.any():
-        return None, None
-    n = len(h)
+        return None
     last_bad = np.nonzero(~ok)[0]
     first = int(last_bad[-1]) + 1 if len(last_bad) else 0
-    if first >= n:
+    return first + 1 if first < len(h) else None
+
+
+def time_to_kappa(stats, kappa_star, rtol=1e-4):
+    """Derived from one solve's kappa history: Fourier guess + the mean
+    iteration time x the crossing index (see measured_time_to_kappa)."""
+    n = crossing(stats["kappa_history"], kappa_star, rtol)
+    if n is None:
         return None, None
     per_it = stats["time_iter_ms"] / max(1, stats["iterations"])
-    return stats["time_fourier_ms"] + (first + 1) * per_it, first + 1
+    return stats["time_fourier_ms"] + n * per_it, n
+
+
+def measured_time_to_kappa(run, n_iter, reps=3):
+    """Device time (CUDA events on the solve stream) of a solve stopped after
+    exactly n_iter iterations, the crossing index of a full solve: the
+    measured time to kappa within 1e-4 (median of reps, after one warm-up)."""
+    import torch
+    st = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ts = []
+    for i in range(reps + 1):
+        torch.cuda.synchronize()
+        e0.record(st)
+        run(n_iter)
+        e1.record(st)
+        torch.cuda.synchronize()
+        if i:
+            ts.append(e0.elapsed_time(e1))
+    return statistics.median(ts)
+
+
+def batch_leg(local, rtol=1e-4):
+    """Config 4 (64 geometries, N = 48 ... 192): the mixed batched form against
+    the plain FP64 batched form, time until every geometry with a stored
+    oracle value has kappa within 1e-4 of it (measured as a batch solve
+    stopped at that iteration), and the batch's update rate."""
+    from paper_2106_02764_gb300 import inputs as I
+    from paper_2106_02764_gb300.binding import Solver, solve_batch
+    geoms = I.config4()
+    stars = {}
+    for gi in range(len(geoms)):
+        p = os.path.join(ROOT, "tests", "golden", f"kappa_star_cfg4_{gi}.json")
+        if os.path.exists(p):
+            with open(p) as f:
+                stars[gi] = json.load(f)["kappa_eff"]
+    if not stars:
+        return None
+    out = {"geometries": len(geoms), "with_oracle_value": sorted(stars),
+           "updates_per_iteration": int(sum(w.n_solid * w.n_ordinates for w in geoms))}
+    for prec in ("mixed", "fp64"):
+        solvers = [Solver.from_workload(w, device=local) for w in geoms]
+        kw = dict(precision=prec, check_every=8, accel=ACCEL, allow_not_converged=True)
+        stats = solve_batch(solvers, tol=1e-6, max_iter=3000, **kw)
+        ns = [crossing(stats[gi]["kappa_history"], k, rtol) for gi, k in stars.items()]
+        if any(n is None for n in ns):
+            out[prec] = {"time_to_kappa_1e-4_ms": None}
+            continue
+        n_star = max(ns)
+
+        def run(n):
+            solve_batch(solvers, tol=0.0, max_iter=n, **kw)
+        t = measured_time_to_kappa(run, n_star)
+        iters = max(s["iterations"] for s in stats)
+        out[prec] = {"time_to_kappa_1e-4_ms": t, "iterations_to_kappa_1e-4": n_star,
+                     "solve_ms": stats[0]["time_total_ms"], "iterations": iters,
+                     "updates_per_s": out["updates_per_iteration"] * iters / (stats[0]["time_iter_ms"] * 1e-3)}
+        for s in solvers:
+            s.close()
+    if out["mixed"].get("time_to_kappa_1e-4_ms") and out["fp64"].get("time_to_kappa_1e-4_ms"):
+        out["speedup_time_to_kappa_vs_fp64"] = out["fp64"]["time_to_kappa_1e-4_ms"] / out["mixed"]["time_to_kappa_1e-4_ms"]
+    return out
+
+
+def film_leg(local):
+    """Config 3 (3D film 64 x 64 x 32, 8640 ordinates): per-launch time of the 3D
+    sweep over 40 iterations in each precision, with its ALU roofline (9 flop
+    per solid cell-ordinate update: 2D + the z inflow)."""
+    from paper_2106_02764_gb300 import inputs as I
+    from paper_2106_02764_gb300.binding import Solver
+    wl = I.config3()
+    out = {"workload": wl.name, "n_solid": wl.n_solid, "n_ordinates": wl.n_ordinates}
+    for prec in ("mixed", "fp64"):
+        s = Solver.from_workload(wl, device=local)
+        st = s.solve(precision=prec, tol=0.0, max_iter=40, check_every=8, profile=True,
+                     allow_not_converged=True)
+        ms = st["time_sweep_ms"] / max(1, st["n_sweeps"])
+        flop = 9 * wl.n_solid * wl.n_ordinates
+        out[prec] = {"sweep_ms": ms, "achieved_tflops": flop / (ms * 1e-3) / 1e12,
+                     "updates_per_s": wl.n_solid * wl.n_ordinates / (ms * 1e-3),
+                     "group_size": st["group_size"], "rows_per_thread": st["rows_per_thread"]}
+        s.close()
+    return out
+
+
+def sharded_leg(wl, local, rank, world, dist, kappa_star):
+    """One config-2 solve with its ordinate groups spread over the ranks (Sec.
+    3: directions over processes): per iteration each rank sweeps its share,
+    the FP64 moment partials are summed by an all-reduce (NCCL under torchrun;
+    nothing to sum on one rank) and every rank finalises.  Plain source
+    iteration (the sharded form has no Anderson mixing), mixed precision, stop
+    at a relative kappa change of 1e-6."""
+    import torch
+    from paper_2106_02764_gb300.binding import Solver
+    s = Solver.from_workload(wl, device=local).set_shard(rank, world)
+    buf = torch.empty(s.shard_partials_count(), dtype=torch.float64, device="cuda")
+    st = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    e0.record(st)
+    s.shard_begin(precision="mixed", tol=1e-6, max_iter=5000, group_size=8, rows_per_thread=8)
+    it = 0
+    while True:
+        s.shard_sweep(buf)
+        if dist:
+            dist.all_reduce(buf)
+        it += 1
+        if s.shard_finalize(buf):
+            break
+    e1.record(st)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    if dist:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    k = s.kappa_eff
+    return {"ranks": world, "iterations": it, "ms": ms,
+            "updates_per_s": wl.n_solid * wl.n_ordinates * it / (ms * 1e-3),
+            "kappa_eff": k, "kappa_rel_err": abs(k - kappa_star) / kappa_star if kappa_star else None,
+            "exchange": "all-reduce of %d FP64 partials per iteration" % s.shard_partials_count()}
 
 
 SWEEP_SOURCES = ("sweep2d.cuh", "sweep.cuh", "sweep2d_variants.h", "obte_internal.h")
@@ -215,13 +343,14 @@ def sweep_blocks(st):
 
 def launches_per_solve(iterations, check_every):
     """Kernels one mixed Anderson solve launches: the first guess (cluster CG)
-    and four start-of-solve kernels (state, wall temperatures, records,
-    Anderson history), then per launched iteration the sweep, finalize, its
-    tail and the three Anderson kernels.  Iterations go in graph chunks of
+    and five start-of-solve kernels (state, wall temperatures, records, their
+    deviation-form difference fields, Anderson history), then per launched
+    iteration the sweep, finalize, its tail, the three Anderson kernels and
+    the records' difference fields.  Iterations go in graph chunks of
     check_every and a solve stops inside a chunk, whose remaining iterations
     launch and return at once."""
     launched = -(-int(iterations) // int(check_every)) * int(check_every)
-    return 5 + 6 * launched
+    return 6 + 7 * launched
 
 
 def main():
@@ -294,6 +423,8 @@ def main():
     peak = N_SM * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12
 
     extra = {}
+    if not a.no_extra:
+        extra["ordinate_sharded_config2"] = sharded_leg(wl, local, rank, world, dist, kappa_star)
     if rank == 0:
         # time to kappa_eff (1e-4 rel): mixed (timed steps) vs plain FP64 sweep
         ref_k = kappa_star
@@ -310,15 +441,23 @@ def main():
                 ref_k = fp64["kappa_eff"]
         ttk = [time_to_kappa(s, ref_k) for s in stats] if ref_k else []
         ttk_ms = [t for t, _ in ttk if t is not None]
-        extra["time_to_kappa_1e-4_ms"] = statistics.median(ttk_ms) if ttk_ms else None
-        extra["iterations_to_kappa_1e-4"] = ttk[0][1] if ttk else None
+        n_star = ttk[0][1] if ttk else None
+        extra["iterations_to_kappa_1e-4"] = n_star
+        extra["time_to_kappa_1e-4_ms_derived"] = statistics.median(ttk_ms) if ttk_ms else None
+        extra["time_to_kappa_1e-4_ms"] = (measured_time_to_kappa(
+            lambda n: solver.solve(**{**opts, "tol": 0.0, "max_iter": n, "profile": False},
+                                   allow_not_converged=True), n_star) if n_star else None)
         extra["kappa_eff"] = stats[-1]["kappa_eff"]
         extra["kappa_rel_err"] = abs(stats[-1]["kappa_eff"] - ref_k) / abs(ref_k) if ref_k else None
         extra["iterations_per_step"] = stats[-1]["iterations"]
         extra["fourier_ms"] = stats[-1]["time_fourier_ms"]
         if fp64:
-            t64, n64 = time_to_kappa(fp64, ref_k)
-            extra["fp64"] = {"time_to_kappa_1e-4_ms": t64, "iterations_to_kappa_1e-4": n64,
+            _t64, n64 = time_to_kappa(fp64, ref_k)
+            t64 = measured_time_to_kappa(
+                lambda n: s64.solve(precision="fp64", tol=0.0, max_iter=n, check_every=8, accel=ACCEL,
+                                    allow_not_converged=True), n64) if n64 else None
+            extra["fp64"] = {"time_to_kappa_1e-4_ms": t64, "time_to_kappa_1e-4_ms_derived": _t64,
+                             "iterations_to_kappa_1e-4": n64,
                              "updates_per_s": fp64["updates_per_s"],
                              "sweep_ms": fp64["time_sweep_ms"] / max(1, fp64["n_sweeps"]),
                              "kappa_eff": fp64["kappa_eff"], "iterations": fp64["iterations"]}
@@ -348,6 +487,9 @@ def main():
         from paper_2106_02764_gb300.binding import measure_fma_rate
         fma32 = measure_fma_rate("mixed", local) / 1e12
         fma64 = measure_fma_rate("fp64", local) / 1e12
+        if not a.no_extra:
+            extra["batched_config4"] = batch_leg(local)
+            extra["film_config3"] = film_leg(local)
         cpu = None
         if not a.no_cpu_baseline:
             cpu = cpu_oracle_rate(wl, a.cpu_seconds)

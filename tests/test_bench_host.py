@@ -5,16 +5,15 @@ import sys
 sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
 
 
-def test_launch_count_matches_the_launch_list():
-    """The bench's own launch list (ncu, 5 solves of the config-2 workload at
-    34 iterations each, check every 8) holds 1225 kernels of the library:
-    40 launches each of the sweep, finalize, its tail and the three Anderson
-    kernels, plus the first guess and four start-of-solve kernels, per solve."""
+def test_launch_count_of_a_solve():
+    """A config-2 solve of 38 iterations, checked every 8, launches 40
+    iterations of seven kernels (sweep, finalize, its tail, three Anderson
+    kernels, the records' difference fields) plus the first guess and five
+    start-of-solve kernels: 286 kernels of the library."""
     import bench
-    assert bench.launches_per_solve(34, 8) == 245
-    assert 5 * bench.launches_per_solve(34, 8) == 1225
-    assert bench.launches_per_solve(32, 8) == 5 + 6 * 32
-    assert bench.launches_per_solve(1, 8) == 5 + 6 * 8
+    assert bench.launches_per_solve(38, 8) == 286
+    assert bench.launches_per_solve(32, 8) == 6 + 7 * 32
+    assert bench.launches_per_solve(1, 8) == 6 + 7 * 8
 
 
 def test_sweep_blocks_of_the_warp_kernel():
