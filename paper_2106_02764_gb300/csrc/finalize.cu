@@ -368,7 +368,10 @@ __global__ void build_records_kernel(const GeomDev* geoms) {
       if (ip == g.nx - 1) packed |= REC_LAST;
       T* r = rec + (size_t)g.rec_w * k;
       const T pk = sizeof(T) == 4 ? (T)__uint_as_float(packed) : (T)__longlong_as_double((long long)packed);
-      r[0] = src[c];
+      // deviation form (3D): field 0 holds the packed word too (no source
+      // field is read), so one 16-byte load gives the packed word and the
+      // three wall / difference fields
+      r[0] = (g.psi && g.rec_w == 8) ? pk : src[c];
       // x field: the upwind wall temperature, or +-dT on the jump column
       r[1] = (packed & REC_JUMP) ? (T)((q & 1) ? -g.dT : g.dT) : twc[(size_t)c * 6 + ((q & 1) ? 1 : 0)];
       r[2] = twc[(size_t)c * 6 + ((q & 2) ? 3 : 2)];

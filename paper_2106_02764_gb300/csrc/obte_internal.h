@@ -78,6 +78,8 @@ struct GeomDev {
   //     (the in-x field holds sign(p_x) dT instead on the jump column, REC_JUMP;
   //     wall fields of sides without a wall hold 0)
   //     {s_i T_L,i, T_w in-x, in-y, in-z sides, packed, 0, 0, 0}
+  //     (deviation form: the wall / difference fields u - T_L,cell, and the
+  //     packed word also in field 0, so that one 16-byte load serves a row)
   //   packed = cell (bits 0-21) | REC_* flags of octant q (bits 22-31)
   //   rec_idx[c * n_octants + q] = record index (q * nx + s) * rows + row of cell c
   //   tlq[(q * nx + s) * rows + row]: T_L partial sums of the running sweep in
