@@ -2,7 +2,7 @@
 
     python -m paper_2106_02764_gb300.profile_case --config 2 --precision mixed \
         [--iters 4] [--accel 5] [--kernel auto|warp|block|block3d] \
-        [--group-size G] [--rows-per-thread R] [--time]
+        [--group-size G] [--rows-per-thread R] [--time] [--grad]
 
 Without --time: one solve of ``--iters`` source iterations launched one by
 one (no CUDA graph), so that a profiler sees every launch; a capture of the
@@ -10,6 +10,8 @@ n-th sweep launch then picks a steady-state sweep.  With --time: a full solve
 with per-launch CUDA events and one JSON line of per-launch sweep and
 finalisation times (the figures used to order the compiled variants).
 Config 4 (the batch of 64 geometries) is solved through ``solve_batch``.
+With --grad the solve is followed by one d kappa / d s (record passes and
+contractions; config 5 has s(x)).
 """
 from __future__ import annotations
 
@@ -33,6 +35,7 @@ def main(argv=None):
     ap.add_argument("--fourier-tol", type=float, default=0.0)
     ap.add_argument("--fourier-max-iter", type=int, default=0)
     ap.add_argument("--time", action="store_true")
+    ap.add_argument("--grad", action="store_true")
     a = ap.parse_args(argv)
     build.build()
     wl = inputs.CONFIGS[a.config]()
@@ -51,6 +54,8 @@ def main(argv=None):
     else:
         s = Solver.from_workload(wl)
         st = s.solve(allow_not_converged=True, **kw)
+        if a.grad:
+            s.kappa_grad_s()
     wall = time.perf_counter() - t0
     out = {"config": a.config, "precision": a.precision, "iterations": st["iterations"],
            "kappa_eff": st["kappa_eff"], "group_size": st["group_size"],
