@@ -394,7 +394,10 @@ __global__ void __launch_bounds__(32 * WarpCfg<T, G, RMAX, NH>::WPB, WarpCfg<T, 
     // j = d + d0 + 1 (mod nx), all at register row (d + d0 + 1) mod RMAX of
     // their lanes, so every lane adds that register row's K_x dot under a
     // predicate inside the row loop and keeps it where the row is hot
-    const bool uni_hot = X2 && RFIXED && !PASS && (nx % RMAX == 0) && ((RMAX & (RMAX - 1)) == 0);
+    // (two-warp groups keep the per-row path: the extra registers spill at
+    // their 128-register bound)
+    const bool uni_hot = NH == 1 && X2 && RFIXED && !PASS && (nx % RMAX == 0) &&
+                         ((RMAX & (RMAX - 1)) == 0);
     float hot8 = 0.f;     // this lane's hot-row fluxes of up to RMAX steps
     double hot_d = 0.0;   // and their sum
     // diagonals of steps d .. d + NST - 2 are in flight at the top of step d
