@@ -1735,6 +1735,35 @@ extern "C" int obte_solve_fourier(obte_ctx* ctx, double tol, int max_iter, doubl
 // ---------------------------------------------------------------------------
 // d kappa / d s
 // ---------------------------------------------------------------------------
+// Batches of reversed ordinate pairs (o, rev(o)) for the gradient's record
+// passes, o running over the first octant of each reversed octant pair; up to
+// cap pairs per batch, octant pairs merged, so that a record pass holds as
+// many groups as the field budget allows.
+static std::vector<std::vector<int>> grad_batches(const obte_ctx* ctx, size_t cap) {
+  const int O = ctx->O;
+  std::vector<std::pair<int, int>> pairs;
+  int o = 0;
+  while (o < O) {
+    const int q = ctx->octant[o];
+    int e1 = o;
+    while (e1 < O && ctx->octant[e1] == q) ++e1;
+    int e2 = e1;
+    while (e2 < O && ctx->octant[e2] == ctx->octant[e1]) ++e2;
+    for (int k = o; k < e1; ++k) pairs.push_back({k, ctx->rev_o[k]});
+    o = e2;
+  }
+  std::vector<std::vector<int>> batches;
+  for (size_t a = 0; a < pairs.size(); a += cap) {
+    std::vector<int> b;
+    for (size_t k = a; k < std::min(pairs.size(), a + cap); ++k) {
+      b.push_back(pairs[k].first);
+      b.push_back(pairs[k].second);
+    }
+    batches.push_back(b);
+  }
+  return batches;
+}
+
 extern "C" int obte_kappa_grad_s(obte_ctx* ctx, double* out, size_t max_field_bytes) {
   if (!ctx || !out) return OBTE_EINVAL;
   if (!ctx->solved) return ctx->fail(OBTE_ESTATE, "solve first");
@@ -1750,28 +1779,8 @@ extern "C" int obte_kappa_grad_s(obte_ctx* ctx, double* out, size_t max_field_by
   const size_t e = ctx->precision == 0 ? 8 : 4;
   const size_t per_ord = e * (size_t)ctx->n_cells;
   // batches: whole reversed octant pairs when they fit, else matching slices
-  std::vector<std::vector<int>> batches;
-  {
-    int o = 0;
-    while (o < O) {
-      const int q = ctx->octant[o];
-      int e1 = o;
-      while (e1 < O && ctx->octant[e1] == q) ++e1;
-      int e2 = e1;
-      while (e2 < O && ctx->octant[e2] == ctx->octant[e1]) ++e2;
-      const int half = e1 - o;  // ordinates per octant
-      const size_t cap = std::max<size_t>(1, max_field_bytes / (2 * per_ord));
-      for (int a = 0; a < half; a += (int)cap) {
-        std::vector<int> b;
-        for (int k2 = a; k2 < std::min(half, a + (int)cap); ++k2) {
-          b.push_back(o + k2);
-          b.push_back(rev[o + k2]);
-        }
-        batches.push_back(b);
-      }
-      o = e2;
-    }
-  }
+  const std::vector<std::vector<int>> batches =
+      grad_batches(ctx, std::max<size_t>(1, max_field_bytes / (2 * per_ord)));
   size_t max_b = 0;
   for (auto& b : batches) max_b = std::max(max_b, b.size());
   void* rec = ctx->dalloc(per_ord * max_b);
@@ -2400,27 +2409,7 @@ extern "C" int obte_kappa_grad_s_noalloc(obte_ctx* ctx, double* out) {
   void* rec = carve(e * (size_t)ctx->n_cells * 2 * pairs_cap);
   if (end > OBTE_NOALLOC_SCRATCH_BYTES) return ctx->fail(OBTE_EINVAL, "no-allocation scratch layout overflow");
   // batches of reversed ordinate pairs
-  std::vector<std::vector<int>> batches;
-  {
-    int o = 0;
-    while (o < O) {
-      const int q = ctx->octant[o];
-      int e1 = o;
-      while (e1 < O && ctx->octant[e1] == q) ++e1;
-      int e2 = e1;
-      while (e2 < O && ctx->octant[e2] == ctx->octant[e1]) ++e2;
-      const int half = e1 - o;
-      for (int a = 0; a < half; a += (int)pairs_cap) {
-        std::vector<int> b;
-        for (int k2 = a; k2 < std::min(half, a + (int)pairs_cap); ++k2) {
-          b.push_back(o + k2);
-          b.push_back(rev[o + k2]);
-        }
-        batches.push_back(b);
-      }
-      o = e2;
-    }
-  }
+  const std::vector<std::vector<int>> batches = grad_batches(ctx, pairs_cap);
   // the scratch keeps the previous call's contents: start the sum at zero
   CK(cudaMemsetAsync(grad_d, 0, sizeof(double) * ctx->n_cells, ctx->stream));
   const double jadj = -ctx->kappa_scale * ctx->h[0] * ctx->w_total;

@@ -48,10 +48,10 @@ def test_noalloc_gradient_matches_allocating_entry_point(precision):
 
 def test_noalloc_gradient_in_several_batches():
     """Config 5 in FP64 (128 x 128 cells, 640 ordinates): the 32 MiB hold 127
-    reversed pairs of fields against 160 per pair of octants, so each octant
-    pair runs as two batches and the gradient is summed across them.  Compared
-    with the allocating entry point with its default field budget and with a
-    budget of 4 pairs (many batches), two calls in a row."""
+    reversed pairs of fields against the 320 pairs of the material, so the
+    gradient runs as three batches and is summed across them.  Compared with
+    the allocating entry point with its default field budget (one batch) and
+    with a budget of 4 pairs (80 batches), two calls in a row."""
     wl = I.config5()
     s, tol = _solved(wl, "fp64")
     ref = s.kappa_grad_s()
