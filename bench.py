@@ -266,6 +266,78 @@ def film_leg(local):
     return out
 
 
+def small_leg(local, rtol=1e-4):
+    """Config 1 (2D 32^2, 8 bins x 16 directions): time to kappa within 1e-4 of
+    the oracle's stored value in each precision, measured as a solve stopped at
+    the crossing iteration (the same solve options as the main leg)."""
+    from paper_2106_02764_gb300 import inputs as I
+    from paper_2106_02764_gb300.binding import Solver
+    p = os.path.join(ROOT, "tests", "golden", "kappa_star_cfg1.json")
+    if not os.path.exists(p):
+        return None
+    with open(p) as f:
+        k_star = json.load(f)["kappa_eff"]
+    wl = I.config1()
+    out = {"workload": wl.name, "updates_per_iteration": wl.n_solid * wl.n_ordinates}
+    for prec in ("fp64", "mixed"):
+        s = Solver.from_workload(wl, device=local)
+        kw = dict(precision=prec, check_every=8, accel=ACCEL, allow_not_converged=True)
+        st = s.solve(tol=1e-6, max_iter=3000, **kw)
+        n = crossing(st["kappa_history"], k_star, rtol)
+        t = None
+        if n is not None:
+            t = measured_time_to_kappa(lambda m: s.solve(tol=0.0, max_iter=m, **kw), n)
+        out[prec] = {"time_to_kappa_1e-4_ms": t, "iterations_to_kappa_1e-4": n,
+                     "solve_ms": st["time_total_ms"], "iterations": st["iterations"],
+                     "kappa_rel_err": abs(st["kappa_eff"] - k_star) / k_star}
+        s.close()
+    return out
+
+
+def gradient_leg(local, reps=3):
+    """Config 5 (2D 128^2, s(x) ~ U[0.5, 2], 640 ordinates): d kappa_eff / d s
+    over every cell after a tight solve (Anderson(5); FP64 to a relative kappa
+    change of 1e-12, mixed a fixed 600 iterations): the solve's device time,
+    the gradient call's wall time (median of reps after one warm-up; record
+    passes, contractions and the host copies of one obte_kappa_grad_s) and its
+    error against the oracle adjoint stored with the tests."""
+    import time as _time
+    from paper_2106_02764_gb300 import inputs as I
+    from paper_2106_02764_gb300.binding import Solver
+    pj = os.path.join(ROOT, "tests", "golden", "grad_cfg5.json")
+    pz = os.path.join(ROOT, "tests", "golden", "grad_cfg5.npz")
+    ref = None
+    if os.path.exists(pz):
+        z = np.load(pz)
+        ref = (z["grad"], z["coords"])
+    wl = I.config5()
+    out = {"workload": wl.name, "n_solid": wl.n_solid, "n_ordinates": wl.n_ordinates}
+    for prec in ("mixed", "fp64"):
+        s = Solver.from_workload(wl, device=local)
+        if prec == "fp64":
+            st = s.solve(precision="fp64", tol=1e-12, tol_TL=1e-13, max_iter=20000, check_every=16,
+                         accel=ACCEL, allow_not_converged=True)
+        else:
+            st = s.solve(precision="mixed", tol=0.0, max_iter=600, check_every=50, accel=ACCEL,
+                         allow_not_converged=True)
+        ts = []
+        for i in range(reps + 1):
+            t0 = _time.perf_counter()
+            g = s.kappa_grad_s()
+            if i:
+                ts.append((_time.perf_counter() - t0) * 1e3)
+        e = {"solve_ms": st["time_total_ms"], "iterations": st["iterations"],
+             "gradient_ms": statistics.median(ts)}
+        if ref is not None:
+            gr, c = ref
+            gg = g[c[:, 2], c[:, 1], c[:, 0]]
+            e["grad_err_rel_max"] = float(np.abs(gg - gr).max() / np.abs(gr).max())
+        out[prec] = e
+        s.close()
+    out["reference"] = "oracle adjoint (tests/golden/grad_cfg5.npz)" if ref is not None else None
+    return out
+
+
 def sharded_leg(wl, local, rank, world, dist, kappa_star):
     """One config-2 solve with its ordinate groups spread over the ranks (Sec.
     3: directions over processes): per iteration each rank sweeps its share,
@@ -490,6 +562,8 @@ def main():
         if not a.no_extra:
             extra["batched_config4"] = batch_leg(local)
             extra["film_config3"] = film_leg(local)
+            extra["small_config1"] = small_leg(local)
+            extra["gradient_config5"] = gradient_leg(local)
         cpu = None
         if not a.no_cpu_baseline:
             cpu = cpu_oracle_rate(wl, a.cpu_seconds)

@@ -247,20 +247,33 @@ __global__ void gauge_kernel(const uint8_t* code, const double* TL, int n, doubl
 // field of o (see obte_kappa_grad_s).
 // With psi the recorded fields are deviations T_o - T_L (deviation-form
 // sweeps): then T_o - T_L is the record itself and T_rev = record + T_L.
+// Block: 32 consecutive cells (x) times GC_SLICES slices of the records (y);
+// each thread sums every GC_SLICES-th record of its cell (coalesced loads
+// across the warp), the slices are added in shared memory in a fixed order.
+constexpr int GC_SLICES = 8;
+
 template <typename T>
-__global__ void grad_contract_kernel(const uint8_t* code, const double* TL, int n, const T* rec,
-                                     int n_rec, const int* rev_local, const double* a_rec,
-                                     double jscale, double* grad, int psi) {
-  for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < n; c += gridDim.x * blockDim.x) {
-    if (!(code[c] & CODE_SOLID)) continue;
+__global__ void __launch_bounds__(32 * GC_SLICES) grad_contract_kernel(
+    const uint8_t* code, const double* TL, int n, const T* rec, int n_rec, const int* rev_local,
+    const double* a_rec, double jscale, double* grad, int psi) {
+  __shared__ double part[GC_SLICES][32];
+  const int c = blockIdx.x * 32 + threadIdx.x;
+  double acc = 0.0;
+  if (c < n && (code[c] & CODE_SOLID)) {
     const double tl = TL[c];
-    double acc = 0.0;
-    for (int k = 0; k < n_rec; ++k) {
+    for (int k = threadIdx.y; k < n_rec; k += GC_SLICES) {
       const double f = (double)rec[(size_t)k * n + c];
       const double b = (double)rec[(size_t)rev_local[k] * n + c];
       acc += psi ? a_rec[k] * (b + tl) * f : a_rec[k] * b * (f - tl);
     }
-    grad[c] -= jscale * acc;
+  }
+  part[threadIdx.y][threadIdx.x] = acc;
+  __syncthreads();
+  if (threadIdx.y == 0 && c < n && (code[c] & CODE_SOLID)) {
+    double t = 0.0;
+#pragma unroll
+    for (int y = 0; y < GC_SLICES; ++y) t += part[y][threadIdx.x];
+    grad[c] -= jscale * t;
   }
 }
 
@@ -526,13 +539,13 @@ cudaError_t launch_grad_contract2(const uint8_t* code, const double* TL, int n, 
                                   int n_rec, const int* rev_local, const double* a_rec,
                                   double jscale, double* grad, int precision, int psi,
                                   cudaStream_t st) {
-  int blocks = (n + 255) / 256;
-  if (blocks > 2048) blocks = 2048;
+  const int blocks = (n + 31) / 32;
+  const dim3 thr(32, GC_SLICES);
   if (precision == 0)
-    grad_contract_kernel<double><<<blocks, 256, 0, st>>>(code, TL, n, (const double*)rec, n_rec,
+    grad_contract_kernel<double><<<blocks, thr, 0, st>>>(code, TL, n, (const double*)rec, n_rec,
                                                          rev_local, a_rec, jscale, grad, psi);
   else
-    grad_contract_kernel<float><<<blocks, 256, 0, st>>>(code, TL, n, (const float*)rec, n_rec,
+    grad_contract_kernel<float><<<blocks, thr, 0, st>>>(code, TL, n, (const float*)rec, n_rec,
                                                         rev_local, a_rec, jscale, grad, psi);
   return cudaGetLastError();
 }

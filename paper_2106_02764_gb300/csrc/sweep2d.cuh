@@ -174,8 +174,12 @@ __device__ __forceinline__ int rec_slot(int lane, int r) {
 // block barrier every step ends with.  A block whose item list runs out
 // keeps its warps in the loop on an empty item (no early exit before a
 // barrier).
+// Flux / record passes run once per solve or per gradient batch: their
+// register budget is not cut for residency (a spilled pass costs more than
+// the resident warps it would buy).
 template <typename T, int G, int RMAX, bool HAS_S, bool RFIXED, bool PASS, int NH = 1>
-__global__ void __launch_bounds__(32 * WarpCfg<T, G, RMAX, NH>::WPB, WarpCfg<T, G, RMAX, NH>::MINB)
+__global__ void __launch_bounds__(32 * WarpCfg<T, G, RMAX, NH>::WPB,
+                                  (PASS && NH == 1) ? 1 : WarpCfg<T, G, RMAX, NH>::MINB)
     sweep2d_warp_kernel(const SweepLaunch L) {
   constexpr int WPB = WarpCfg<T, G, RMAX, NH>::WPB;
   constexpr int CH = (4 * sizeof(T)) / 16;  // 16-byte parts per record
@@ -263,6 +267,15 @@ __global__ void __launch_bounds__(32 * WarpCfg<T, G, RMAX, NH>::WPB, WarpCfg<T, 
       AW[g] = ok ? ld<T>(gm.aw, o) : T(0);
       if (JSEL) JX[JSEL ? g : 0] = (T)(ax * (double)sx * dT);
       if (ok) kx_sum += (double)sx * (double)ld<T>(gm.kxa, o);
+    }
+    // record-only pass (the adjoint's field records): each solid cell's G
+    // values go straight to their record slots; the pass's wall, hot-face
+    // and moment sums are not used, so the out-of-line epilogue is skipped
+    const bool rec_only = PASS && (flags & (SWEEP_FLUX | SWEEP_RECORD)) == SWEEP_RECORD;
+    int rsl[PASS ? G : 1];
+    if constexpr (PASS) {
+#pragma unroll
+      for (int g = 0; g < G; ++g) rsl[g] = (rec_only && g < cnt) ? gm.rec_slot[o0 + g] : -1;
     }
 
     // Row values.  FP32 without s(x), G even: ordinates in pairs (float2),
@@ -561,6 +574,13 @@ __global__ void __launch_bounds__(32 * WarpCfg<T, G, RMAX, NH>::WPB, WarpCfg<T, 
             const int cell = (int)(packed & REC_CELL_MASK);
             const bool last = packed & REC_LAST;
             if constexpr (PASS) {
+              if (rec_only) {
+                T* rec = reinterpret_cast<T*>(gm.rec);
+#pragma unroll
+                for (int g = 0; g < G; ++g)
+                  if (rsl[g] >= 0) rec[(size_t)rsl[g] * gm.n_cells + cell] = VG(r, g);
+                continue;
+              }
 #pragma unroll
               T loc[NH == 2 ? G : 1];
               T* sc = NH == 2 ? loc : scratch;
