@@ -8,9 +8,10 @@ tight fixed point in both precisions and held to the bars: kappa_eff within
 1e-6 relative (FP64) / 1e-4 (mixed), each bin's share of kappa within the
 same fraction of kappa_eff, T_L within 1e-5 K in every solid cell, J within
 the kappa bar of max |J|.  The 3D film of config 3 is too large for the
-oracle's sparse LU factors (0.4 GB per ordinate); the same 64 x 64 x 32 film
-mesh with 3 bins x 8 x 4 directions stands in for it against the oracle, and
-the full film is checked through properties that hold at any size.
+oracle's sparse LU factors (about 1 GB per ordinate); the same 64 x 64 x 32
+film mesh with 2 bins x 8 x 2 sphere directions (32 ordinates) stands in for
+it against the oracle, and the full film is checked through properties that
+hold at any size.
 """
 import copy
 import os
@@ -127,7 +128,7 @@ def test_config2_bench_launch():
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
 def test_config3_film_mesh_vs_oracle(precision):
     """The 64 x 64 x 32 film mesh of config 3 (cylindrical pore, diffuse
-    film walls) with 3 bins x 8 x 4 sphere directions against the oracle."""
+    film walls) with 2 bins x 8 x 2 sphere directions against the oracle."""
     wl = I.config3_reduced()
     if precision == "fp64":
         s, _ = gpu(wl, "fp64", tol=1e-12, tol_TL=1e-12, max_iter=20000, check_every=32, accel=5)
