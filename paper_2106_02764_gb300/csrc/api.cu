@@ -941,7 +941,7 @@ static int prepare_state(obte_ctx* ctx, int precision, int G, int R, bool warp, 
     ctx->rec_idx = ctx->dalloc_t<int>((size_t)nq * ctx->n_cells);
     NEED(ctx->rec4);
     NEED(ctx->rec_idx);
-    if (rec_w == 4) {  // skewed T_L partials of the 2D warp kernel
+    {  // skewed T_L partials of the 2D warp kernel and of the 3D kernel
       ctx->tlq = ctx->dalloc_t<double>((size_t)nq * ctx->n_cells);
       NEED(ctx->tlq);
       CK(cudaMemsetAsync(ctx->tlq, 0, sizeof(double) * nq * (size_t)ctx->n_cells, ctx->stream));
@@ -1022,6 +1022,7 @@ static int prepare_state(obte_ctx* ctx, int precision, int G, int R, bool warp, 
   g.rec4 = rec_w ? ctx->rec4 : nullptr;
   g.rec_idx = rec_w ? ctx->rec_idx : nullptr;
   g.tlq = rec_w == 4 ? ctx->tlq : nullptr;
+  g.tlq3 = rec_w == 8 ? ctx->tlq : nullptr;
   g.blk_part = ctx->blk_part;
   g.rec_w = rec_w;
   g.psi = (precision == 1 && rec_w > 0) ? 1 : 0;  // float record kernels: deviation form
@@ -1612,7 +1613,7 @@ static int run_flux_pass(obte_ctx* ctx) {
   CK(sweep_once(ctx, SWEEP_FLUX));
   // the pass does not advance the iterate: drop its moment accumulations
   CK(cudaMemsetAsync(ctx->TL_acc, 0, sizeof(double) * ctx->n_cells, ctx->stream));
-  if (ctx->tlq) CK(cudaMemsetAsync(ctx->tlq, 0, sizeof(double) * 4 * (size_t)ctx->n_cells, ctx->stream));
+  if (ctx->tlq) CK(cudaMemsetAsync(ctx->tlq, 0, sizeof(double) * (ctx->dim == 3 ? 8 : 4) * (size_t)ctx->n_cells, ctx->stream));
   CK(cudaMemsetAsync(ctx->wall_acc, 0, sizeof(double) * 6 * (size_t)ctx->n_cells, ctx->stream));
   CK(cudaMemsetAsync(ctx->scal, 0, sizeof(double), ctx->stream));
   int one = 1;
@@ -1849,7 +1850,7 @@ extern "C" int obte_kappa_grad_s(obte_ctx* ctx, double* out, size_t max_field_by
     CK(launch_grad_contract2(ctx->code_d, ctx->TL, ctx->n_cells, rec, (int)b.size(), revl_d, a_d,
                              jscale, grad_d, ctx->precision, ctx->gh.psi, ctx->stream));
     CK(cudaMemsetAsync(ctx->TL_acc, 0, sizeof(double) * ctx->n_cells, ctx->stream));
-    if (ctx->tlq) CK(cudaMemsetAsync(ctx->tlq, 0, sizeof(double) * 4 * (size_t)ctx->n_cells, ctx->stream));
+    if (ctx->tlq) CK(cudaMemsetAsync(ctx->tlq, 0, sizeof(double) * (ctx->dim == 3 ? 8 : 4) * (size_t)ctx->n_cells, ctx->stream));
     CK(cudaMemsetAsync(ctx->wall_acc, 0, sizeof(double) * 6 * (size_t)ctx->n_cells, ctx->stream));
     CK(cudaMemsetAsync(ctx->scal, 0, sizeof(double), ctx->stream));
     CK(cudaStreamSynchronize(ctx->stream));
@@ -2460,7 +2461,7 @@ extern "C" int obte_kappa_grad_s_noalloc(obte_ctx* ctx, double* out) {
     CK(launch_grad_contract2(ctx->code_d, ctx->TL, ctx->n_cells, rec, (int)b.size(), revl_d, a_d,
                              jscale, grad_d, ctx->precision, ctx->gh.psi, ctx->stream));
     CK(cudaMemsetAsync(ctx->TL_acc, 0, sizeof(double) * ctx->n_cells, ctx->stream));
-    if (ctx->tlq) CK(cudaMemsetAsync(ctx->tlq, 0, sizeof(double) * 4 * (size_t)ctx->n_cells, ctx->stream));
+    if (ctx->tlq) CK(cudaMemsetAsync(ctx->tlq, 0, sizeof(double) * (ctx->dim == 3 ? 8 : 4) * (size_t)ctx->n_cells, ctx->stream));
     CK(cudaMemsetAsync(ctx->wall_acc, 0, sizeof(double) * 6 * (size_t)ctx->n_cells, ctx->stream));
     CK(cudaMemsetAsync(ctx->scal, 0, sizeof(double), ctx->stream));
     CK(cudaStreamSynchronize(ctx->stream));  // host vectors above are copy sources

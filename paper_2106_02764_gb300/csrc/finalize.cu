@@ -47,7 +47,18 @@ __global__ void finalize_kernel(const GeomDev* geoms) {
     if (!(code[c] & CODE_SOLID)) continue;
     double t = 0.0;
     size_t k[4];  // 2D warp kernel: skewed index of the cell in each quadrant
-    if (!g.tlq) {  // per-cell accumulator (the 2D warp kernel uses the skewed one only)
+    if (g.tlq3) {  // skewed per-octant partials of the 3D kernel (fixed order)
+      double p[8];
+      int k3[8];
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        k3[q] = g.rec_idx[(size_t)c * 8 + q];
+        p[q] = g.tlq3[k3[q]];
+      }
+      t = ((p[0] + p[1]) + (p[2] + p[3])) + ((p[4] + p[5]) + (p[6] + p[7]));
+#pragma unroll
+      for (int q = 0; q < 8; ++q) g.tlq3[k3[q]] = 0.0;
+    } else if (!g.tlq) {  // per-cell accumulator
       t = TL_acc[c];
       TL_acc[c] = 0.0;
     } else {  // skewed per-quadrant partials of the 2D warp kernel
@@ -425,7 +436,18 @@ __global__ void shard_export_kernel(const GeomDev* geoms, double* out) {
   const int tid = blockIdx.x * blockDim.x + threadIdx.x;
   for (int c = tid; c < g.n_cells; c += stride) {
     double t = 0.0;
-    if (!g.tlq) {
+    if (g.tlq3) {
+      double p[8];
+      int k3[8];
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        k3[q] = g.rec_idx[(size_t)c * 8 + q];
+        p[q] = g.tlq3[k3[q]];
+      }
+      t = ((p[0] + p[1]) + (p[2] + p[3])) + ((p[4] + p[5]) + (p[6] + p[7]));
+#pragma unroll
+      for (int q = 0; q < 8; ++q) g.tlq3[k3[q]] = 0.0;
+    } else if (!g.tlq) {
       t = g.TL_acc[c];
       g.TL_acc[c] = 0.0;
     } else {
@@ -459,7 +481,8 @@ __global__ void shard_import_kernel(const GeomDev* geoms, const double* in) {
   const int stride = gridDim.x * blockDim.x;
   const int tid = blockIdx.x * blockDim.x + threadIdx.x;
   for (int c = tid; c < g.n_cells; c += stride) {
-    if (g.tlq) g.tlq[skew_index(g, c, 0)] = in[c];
+    if (g.tlq3) g.tlq3[g.rec_idx[(size_t)c * 8]] = in[c];
+    else if (g.tlq) g.tlq[skew_index(g, c, 0)] = in[c];
     else g.TL_acc[c] = in[c];
   }
   for (int f = tid; f < g.n_walls; f += stride)

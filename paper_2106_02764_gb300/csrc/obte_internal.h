@@ -85,9 +85,12 @@ struct GeomDev {
   //   tlq[(q * nx + s) * rows + row]: T_L partial sums of the running sweep in
   //     the same skewed order (2D warp kernel; FP64); the finalisation adds
   //     them to TL_acc's
+  //   tlq3: the same for the 3D kernel (eight octants, rows = ny nz), read
+  //     through rec_idx
   void* rec4;
   int* rec_idx;
   double* tlq;
+  double* tlq3;
   int rec_w;              // values per record: 4 (2D warp kernel), 8 (3D kernel); 0: none
   // Deviation form (float record kernels): the sweep carries psi_o = T_o - T_L
   // per cell, the records' wall / neighbour fields hold the FP64 differences

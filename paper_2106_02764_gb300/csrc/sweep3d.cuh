@@ -150,6 +150,21 @@ __global__ void __launch_bounds__(Sweep3DCfg<RMAX>::NT, 1) sweep3d_kernel(const 
   const T* __restrict__ recq = reinterpret_cast<const T*>(gm.rec4) + (size_t)q * nx * rows * 8;
   double* tl_acc = gm.TL_acc;
   const double* __restrict__ sv_ptr = gm.s;
+  // T_L partials in the skewed order of the records ([s][row] of the
+  // octant): a step's rows go through shared memory, by row, so that the
+  // FP64 atomics of 32 consecutive rows are one coalesced request; they are
+  // issued one step later, after the next step's rows
+  double* tlq3 = gm.tlq3 ? gm.tlq3 + (size_t)q * nx * rows : nullptr;
+  constexpr int NTR = NT * RMAX;  // rows of a block, at most
+  T* tlb = scratch + G * NT;      // [2][NTR] after the scratch
+  auto flush_rows = [&](int buf, int sd) {
+    const T* b = tlb + buf * NTR;
+    double* dst = tlq3 + (size_t)sd * rows;
+    for (int row = t; row < rows; row += blockDim.x) {  // threads launched: a multiple of 32 <= NT
+      const T v = b[row];
+      if (v != T(0)) atomicAdd(dst + row, widen(v));
+    }
+  };
 
   T A0[G], AX[G], AY[G], AZ[G], AW[G], JX[G];
   double kx_sum = 0.0;
@@ -306,6 +321,7 @@ __global__ void __launch_bounds__(Sweep3DCfg<RMAX>::NT, 1) sweep3d_kernel(const 
     const int s_next = (s + 1 == nx) ? 0 : s + 1;
 
     if (defer_z && d > 0) top_plane_walls(prv, s == 0 ? nx - 1 : s - 1);
+    const int s_prev = s == 0 ? nx - 1 : s - 1;
     if (active) {
       VV dny[GV];
 #pragma unroll
@@ -428,24 +444,32 @@ __global__ void __launch_bounds__(Sweep3DCfg<RMAX>::NT, 1) sweep3d_kernel(const 
           }
         }
       }
-      // moment atomics after all rows (a generic-address atomic between rows
-      // would keep later shared-memory loads from moving ahead of it)
+      if (tlq3) {
 #pragma unroll
-      for (int r = 0; r < RMAX; ++r)
-        if (pk[r] & REC_SOLID) atomicAdd(tl_acc + (pk[r] & REC_CELL_MASK), widen(tls[r]));
+        for (int r = 0; r < RMAX; ++r) tlb[cur * NTR + row0 + r] = (pk[r] & REC_SOLID) ? tls[r] : T(0);
+      } else {
+        // moment atomics after all rows (a generic-address atomic between
+        // rows would keep later shared-memory loads from moving ahead of it)
+#pragma unroll
+        for (int r = 0; r < RMAX; ++r)
+          if (pk[r] & REC_SOLID) atomicAdd(tl_acc + (pk[r] & REC_CELL_MASK), widen(tls[r]));
+      }
 #pragma unroll
       for (int r = 0; r < RMAX; ++r)
 #pragma unroll
         for (int h = 0; h < GV; ++h) XP(cur, r, h, t) = v[r][h];
     }
+    // the previous step's partials (written before the barrier that ended it)
+    if (tlq3 && d > 0) flush_rows(prv, s_prev);
     if (d + 1 < nx) load_recs(s_next, rc);
     s = s_next;
     __syncthreads();
   }
 
   // the last step's plane nz - 1 (its values were published before the
-  // loop's final barrier; s is one past the last diagonal)
+  // loop's final barrier; s is one past the last diagonal) and its partials
   if (defer_z) top_plane_walls((nx - 1) & 1, s == 0 ? nx - 1 : s - 1);
+  if (tlq3) flush_rows((nx - 1) & 1, s == 0 ? nx - 1 : s - 1);
   {
     const double dk = widen(hot_sum);
     phi += sx > 0 ? dk : -dk;
