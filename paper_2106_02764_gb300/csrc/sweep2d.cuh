@@ -429,10 +429,24 @@ __global__ void __launch_bounds__(32 * WarpCfg<T, G, RMAX, NH>::WPB,
       prefetch(sf, b);
       sf = (sf + 1 == nx) ? 0 : sf + 1;
     }
+    // 8 ordinates x 8 rows per lane (the widest FP32 form): a second copy of
+    // the step loop with the launch-constant conditions of its common case
+    // (full warps, block combine, hot column under a predicate) known at
+    // compile time, unrolled by two steps so that the buffer parities are
+    // constants (about 3 % per launch on a 256 x 256 mesh)
+    auto step_loop = [&](auto FASTV) {
+      constexpr bool F = decltype(FASTV)::value;
     int cur = 0, bf = NST - 1;  // buffer of step d, buffer of the next copy
+#pragma unroll(F ? 2 : 1)
     for (int d = 0; d < nx; ++d) {
       const int s_next = (s + 1 == nx) ? 0 : s + 1;
-      prefetch(sf, bf);
+      if constexpr (F) {
+        const char* g0f = reinterpret_cast<const char*>(recq + ((size_t)sf * ny + rh) * 4);
+        CpRun<0, RMAX * CH, KP, CH>::go(pslot, (unsigned)(bf * CH * 32 * RMAX * 16), g0f + lane * 16);
+        cp_async_commit();
+      } else {
+        prefetch(sf, bf);
+      }
       sf = (sf + 1 == nx) ? 0 : sf + 1;
       bf = (bf + 1 == NST) ? 0 : bf + 1;
       cp_async_wait<NST - 1>();
@@ -456,7 +470,7 @@ __global__ void __launch_bounds__(32 * WarpCfg<T, G, RMAX, NH>::WPB,
           for (int h = 0; h < GV; ++h) dn0[h] = xo[h];
         }
       }
-      if (active) {
+      if (F || active) {
         uint32_t pk[RMAX];
         T tls[RMAX];
         // uniform hot column: the hot row of this step is register row rs of
@@ -466,7 +480,7 @@ __global__ void __launch_bounds__(32 * WarpCfg<T, G, RMAX, NH>::WPB,
         uint32_t pkh = 0;
         VV K2v[X2 ? GV : 1];
         if constexpr (X2) {
-          if (uni_hot) {
+          if (F || uni_hot) {
 #pragma unroll
             for (int h = 0; h < GV; ++h) K2v[h] = reinterpret_cast<const float2*>(kcoef[wib][0])[h];
           }
@@ -508,9 +522,9 @@ __global__ void __launch_bounds__(32 * WarpCfg<T, G, RMAX, NH>::WPB,
                 acc = __ffma2_rn(AXv[h], ux, acc);
                 v[r][h] = acc;
                 tlp = __ffma2_rn(AWv[h], acc, tlp);
-                if (uni_hot && r == rs) hk = __ffma2_rn(K2v[h], acc, hk);
+                if ((F || uni_hot) && r == rs) hk = __ffma2_rn(K2v[h], acc, hk);
               }
-              if (uni_hot && r == rs) pkh = packed;
+              if ((F || uni_hot) && r == rs) pkh = packed;
               pk[r] = packed;
               tls[r] = tlp.x + tlp.y;
             } else {
@@ -545,9 +559,9 @@ __global__ void __launch_bounds__(32 * WarpCfg<T, G, RMAX, NH>::WPB,
             }
           }
         }
-        if (comb && s_prev >= 0) comb_rows(s_prev, par ^ 1);
+        if ((F || comb) && s_prev >= 0) comb_rows(s_prev, par ^ 1);
         // walls per row; the hot column per row too unless uni_hot took it
-        const uint32_t RARE = REC_WOUT_X | REC_WOUT_Y | (uni_hot ? 0u : (uint32_t)REC_LAST);
+        const uint32_t RARE = REC_WOUT_X | REC_WOUT_Y | ((F || uni_hot) ? 0u : (uint32_t)REC_LAST);
         uint32_t any = 0;
 #pragma unroll
         for (int r = 0; r < RMAX; ++r)
@@ -589,7 +603,7 @@ __global__ void __launch_bounds__(32 * WarpCfg<T, G, RMAX, NH>::WPB,
                                             flags, kx_sum);
               continue;
             }
-            if (packed & (REC_WOUT_X | (uni_hot ? 0u : (uint32_t)REC_LAST))) {
+            if (packed & (REC_WOUT_X | ((F || uni_hot) ? 0u : (uint32_t)REC_LAST))) {
               const T sk = kdot(KX, KXr, r);
               if (packed & REC_WOUT_X) {
                 atomicAdd(wacc + (size_t)cell * 6 + out_x_side, widen(sk));
@@ -605,7 +619,7 @@ __global__ void __launch_bounds__(32 * WarpCfg<T, G, RMAX, NH>::WPB,
           }
         }
         if constexpr (X2 && RFIXED && !PASS) {
-          if (uni_hot) {
+          if (F || uni_hot) {
             if ((pkh & (REC_LAST | REC_SOLID | REC_WOUT_X)) == (REC_LAST | REC_SOLID)) {
               hot8 += hk.x + hk.y;
               ++n_hot;
@@ -619,7 +633,7 @@ __global__ void __launch_bounds__(32 * WarpCfg<T, G, RMAX, NH>::WPB,
         // the moment atomics come after all rows: a generic-address atomic
         // between two rows would keep the next row's shared-memory loads from
         // being scheduled ahead of it
-        if (tr_atom) {
+        if (F || tr_atom) {
 #pragma unroll
           for (int r = 0; r < RMAX; ++r)
             if (RFIXED || r >= rb) tlbuf[par][wib][jl + r - rb] = (pk[r] & REC_SOLID) ? tls[r] : T(0);
@@ -636,7 +650,7 @@ __global__ void __launch_bounds__(32 * WarpCfg<T, G, RMAX, NH>::WPB,
           for (int h = 0; h < GV; ++h)
             reinterpret_cast<float2*>(&xch[d & 1][gi][half][0])[h] = v[RMAX - 1][h];
       }
-      if (comb) {
+      if (F || comb) {
         __syncthreads();
         s_prev = s;
         par ^= 1;
@@ -655,6 +669,13 @@ __global__ void __launch_bounds__(32 * WarpCfg<T, G, RMAX, NH>::WPB,
       s = s_next;
       cur = (cur + 1 == NST) ? 0 : cur + 1;
       __syncwarp();
+    }
+    };
+    if constexpr (X2 && RFIXED && !PASS && NH == 1 && G == 8 && RMAX == 8) {
+      if (comb && uni_hot && tpp == 32) step_loop(std::true_type{});
+      else step_loop(std::false_type{});
+    } else {
+      step_loop(std::false_type{});
     }
     if (comb && s_prev >= 0) comb_rows(s_prev, par ^ 1);  // the last step's moments
     cp_async_wait<0>();  // copies past the last step land before the buffers are reused
