@@ -143,12 +143,16 @@ def tall_cell(ny, nx=16, length=100e-9):
     return wl
 
 
-def quantised_iteration(pr, n_iter, form):
+def quantised_iteration(pr, n_iter, form, run=32):
     """Algorithm 1 from the Fourier first guess with the per-ordinate solves
     exact and the values a float sweep would carry rounded to float: form
     "T" rounds the source T_L and every T_o; form "psi" rounds only
-    psi_o = T_o - T_L (T_L and the moments stay FP64).  Returns max |T_L -
-    T_L*| against the exact fixed point after n_iter iterations (gauged)."""
+    psi_o = T_o - T_L (T_L and the moments stay FP64); form "psi_sums" also
+    forms the moment partial sum_o a_o psi_o of each run of ``run``
+    consecutive ordinates in float (sequential float32 adds, float a_o), as
+    the sweep's per-lane and block-combined partials are, before the FP64
+    accumulation.  Returns max |T_L - T_L*| against the exact fixed point
+    after n_iter iterations (gauged)."""
     ref = bte.solve_mode_B(pr, rtol=1e-13)
     tr = bte.Transport(pr)
     me, od = pr.mesh, pr.ords
@@ -157,11 +161,22 @@ def quantised_iteration(pr, n_iter, form):
     for _ in range(n_iter):
         src = T_L.astype(f32).astype(np.float64) if form == "T" else T_L
         TL_new, wn = np.zeros(me.nc), np.zeros(me.nw)
+        part = np.zeros(me.nc, dtype=f32)
         for o in range(od.n):
             T = tr.lu(o).solve(tr.rhs(o, src, T_w))
-            T = T.astype(f32).astype(np.float64) if form == "T" else \
-                T_L + (T - T_L).astype(f32).astype(np.float64)
-            TL_new += od.a[o] * T
+            if form == "psi_sums":
+                psi = (T - T_L).astype(f32)
+                part = part + f32(od.a[o]) * psi          # float32 multiply-add
+                if (o + 1) % run == 0 or o + 1 == od.n:
+                    TL_new += part.astype(np.float64)
+                    part = np.zeros(me.nc, dtype=f32)
+                T = T_L + psi.astype(np.float64)
+            else:
+                T = T.astype(f32).astype(np.float64) if form == "T" else \
+                    T_L + (T - T_L).astype(f32).astype(np.float64)
+                TL_new += od.a[o] * T
             wn += tr.w_out[o] * T[wc]
+        if form == "psi_sums":
+            TL_new += T_L      # sum_o a_o = 1: T_L added back in FP64
         T_L, T_w = TL_new, wn / tr.w_den
     return float(np.abs(bte.gauge(T_L, T_w)[0] - ref.T_L).max())
