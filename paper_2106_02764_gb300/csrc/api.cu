@@ -787,7 +787,7 @@ void push_fitting(std::vector<Variant>& out, const Variant (&v)[N], int precisio
     } else if (v[i].k3d) {
       const int thr = threads_for(ny, nz, v[i].R);
       if (dim != 3 || thr > (v[i].R >= 8 ? 256 : 512)) continue;
-      if (sweep3d_smem_bytes(precision, v[i].G, v[i].R, thr) > 200 * 1024) continue;
+      if (sweep3d_smem_bytes(precision, v[i].G, v[i].R, thr) > 226 * 1024) continue;
       if (!sweep3d_exists(precision, v[i].G, v[i].R, has_s)) continue;
     } else {
       const int thr = threads_for(ny, nz, v[i].R);

@@ -119,5 +119,7 @@ size_t sweep3d_smem_bytes(int precision, int G, int RMAX, int threads) {
   const size_t nt = RMAX >= 8 ? 256 : 512;  // the kernel's compile-time block stride
   (void)threads;
   // exchange [2][R][G][nt] + scratch [G][nt] + T_L partials by row [2][nt R]
-  return (2 * (size_t)RMAX + 1) * G * nt * e + 2 * nt * (size_t)RMAX * e;
+  // FP32: records of two steps [2][R][nt] of 16 bytes
+  return (2 * (size_t)RMAX + 1) * G * nt * e + 2 * nt * (size_t)RMAX * e +
+         (precision == 1 ? 2 * (size_t)RMAX * nt * 16 : 0);
 }

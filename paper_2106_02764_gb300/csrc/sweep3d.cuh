@@ -16,16 +16,19 @@
 // s = (i' + j' + k') mod nx = (d + d0) mod nx of the octant frame, so the
 // finalisation stores every cell's record {s T_L, T_w through the upwind x,
 // y and z sides, packed cell / code / column flags} per octant at
-// [s][j' + ny k']: a thread's rows of one step are contiguous records, loaded
-// one step ahead into registers.  The T_L moment goes to the cell's FP64
-// accumulator.
+// [s][j' + ny k']: a thread's rows of one step are contiguous records, copied
+// one step ahead (FP32: by cp.async into shared memory, FP64: loaded into
+// registers).  The T_L moment goes by row through shared memory into a skewed
+// per-octant FP64 accumulator.
 //
 // FP32 groups run in deviation form like the 2D warp kernel (sweep2d.cuh):
 // row values psi = T_o - T_L, record fields holding the upwind value minus
 // the cell's T_L, moments of psi, T_L added back in FP64; their records keep
-// the packed word in field 0, so a row's record is one 16-byte load, issued
-// at the end of the previous step (config 3: 3.01 -> 2.41 ms per launch
-// against a 16-byte plus a 4-byte load held one step ahead in registers).
+// the packed word in field 0, so a row's record is one 16-byte copy, which
+// each thread makes for its own rows one step ahead into shared memory
+// (config 3: 3.01 ms per launch with a 16-byte plus a 4-byte load held one
+// step ahead in registers, 2.41 with one 16-byte load, 2.17 with the copies
+// and the skewed T_L accumulator).
 //
 // Cells update branch-free (pore values never reach a solid cell, whose faces
 // towards a pore are walls); atomics and the rare epilogue (walls the
@@ -38,6 +41,14 @@
 #include "sweep.cuh"
 
 namespace obte {
+
+__device__ __forceinline__ void cp16_3d(void* smem, const void* gmem) {
+  const unsigned a = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(a), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void commit_3d() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void wait_3d() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
 
 template <typename T>
 __device__ __forceinline__ uint32_t rec3_bits(T v);
@@ -291,9 +302,22 @@ __global__ void __launch_bounds__(Sweep3DCfg<RMAX>::NT, 1) sweep3d_kernel(const 
       return sk;
     }
   };
+  // FP32: each thread copies its own rows' 16-byte records one step ahead
+  // into shared memory ([buffer][row r][thread], conflict-free 16-byte
+  // loads) and reads them back in the step; FP64 loads them into registers
+  constexpr bool SREC = sizeof(T) == 4;
+  float4* rsm = reinterpret_cast<float4*>(tlb + 2 * NTR);
+  auto copy_recs = [&](int sd, int buf) {
+    if (active)
+#pragma unroll
+      for (int r = 0; r < RMAX; ++r)
+        cp16_3d(&rsm[(buf * RMAX + r) * NT + t], recq + ((size_t)sd * rows + row0 + r) * 8);
+    commit_3d();
+  };
   // records of the first step
-  T rc[RMAX][5];
-  auto load_recs = [&](int sd, T (&dst)[RMAX][5]) {
+  T rc[SREC ? 1 : RMAX][5];
+  auto load_recs = [&](int sd, T (&dst)[SREC ? 1 : RMAX][5]) {
+    if constexpr (!SREC) {
 #pragma unroll
     for (int r = 0; r < RMAX; ++r) {
       if (active) {
@@ -312,13 +336,20 @@ __global__ void __launch_bounds__(Sweep3DCfg<RMAX>::NT, 1) sweep3d_kernel(const 
         for (int f = 0; f < 5; ++f) dst[r][f] = T(0);
       }
     }
+    }
   };
-  load_recs(s, rc);
+  if constexpr (SREC) copy_recs(s, 0);
+  else load_recs(s, rc);
   __syncthreads();
 
   for (int d = 0; d < nx; ++d) {
     const int cur = d & 1, prv = cur ^ 1;
     const int s_next = (s + 1 == nx) ? 0 : s + 1;
+    if constexpr (SREC) {
+      if (d + 1 < nx) copy_recs(s_next, cur ^ 1);
+      else commit_3d();
+      wait_3d<1>();  // this step's records (this thread's own copies)
+    }
 
     if (defer_z && d > 0) top_plane_walls(prv, s == 0 ? nx - 1 : s - 1);
     const int s_prev = s == 0 ? nx - 1 : s - 1;
@@ -336,8 +367,22 @@ __global__ void __launch_bounds__(Sweep3DCfg<RMAX>::NT, 1) sweep3d_kernel(const 
 #pragma unroll
       for (int rr = 0; rr < RMAX; ++rr) {
         const int r = RMAX - 1 - rr;
-        const T src = rc[r][0], twx = rc[r][1], twy = rc[r][2], twz = rc[r][3];
-        const uint32_t packed = rec3_bits<T>(rc[r][4]);
+        T src, twx, twy, twz;
+        uint32_t packed;
+        if constexpr (SREC) {
+          const float4 a = rsm[(cur * RMAX + r) * NT + t];
+          src = T(0);
+          twx = (T)a.y;
+          twy = (T)a.z;
+          twz = (T)a.w;
+          packed = __float_as_uint(a.x);  // deviation form: the packed word sits in field 0
+        } else {
+          src = rc[SREC ? 0 : r][0];
+          twx = rc[SREC ? 0 : r][1];
+          twy = rc[SREC ? 0 : r][2];
+          twz = rc[SREC ? 0 : r][3];
+          packed = rec3_bits<T>(rc[SREC ? 0 : r][4]);
+        }
         const bool wx = packed & REC_WIN_X, wy = packed & REC_WIN_Y, wz = packed & REC_WIN_Z;
         const bool jump = packed & REC_JUMP;
         T sval = T(1);
@@ -461,7 +506,9 @@ __global__ void __launch_bounds__(Sweep3DCfg<RMAX>::NT, 1) sweep3d_kernel(const 
     }
     // the previous step's partials (written before the barrier that ended it)
     if (tlq3 && d > 0) flush_rows(prv, s_prev);
-    if (d + 1 < nx) load_recs(s_next, rc);
+    if constexpr (!SREC) {
+      if (d + 1 < nx) load_recs(s_next, rc);
+    }
     s = s_next;
     __syncthreads();
   }

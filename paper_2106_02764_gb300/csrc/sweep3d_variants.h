@@ -28,7 +28,7 @@ OBTE_SWEEP3D_VARIANTS(OBTE_SWEEP3D_DECLARE)
     static bool configured = false;                                                          \
     if (!configured) {                                                                       \
       cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,    \
-                                           200 * 1024);                                      \
+                                           226 * 1024);                                      \
       if (e != cudaSuccess) return e;                                                        \
       configured = true;                                                                     \
     }                                                                                        \
