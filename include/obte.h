@@ -104,7 +104,9 @@ typedef struct {
   int accel;            /* Anderson acceleration window (0: plain source
                            iteration as in Algorithm 1; 1..7: mix the last
                            accel iterates of (T_L, T_w, carried row values);
-                           same fixed point)                                   */
+                           same fixed point; with mixing two consecutive
+                           kappas can agree by chance, so pair tol with
+                           tol_TL at large windows)                            */
 } obte_solve_opts;
 
 #define OBTE_MAX_HISTORY 4096
