@@ -436,240 +436,240 @@ __global__ void __launch_bounds__(32 * WarpCfg<T, G, RMAX, NH>::WPB,
     // constants (about 3 % per launch on a 256 x 256 mesh)
     auto step_loop = [&](auto FASTV) {
       constexpr bool F = decltype(FASTV)::value;
-    int cur = 0, bf = NST - 1;  // buffer of step d, buffer of the next copy
+      int cur = 0, bf = NST - 1;  // buffer of step d, buffer of the next copy
 #pragma unroll(F ? 2 : 1)
-    for (int d = 0; d < nx; ++d) {
-      const int s_next = (s + 1 == nx) ? 0 : s + 1;
-      if constexpr (F) {
-        const char* g0f = reinterpret_cast<const char*>(recq + ((size_t)sf * ny + rh) * 4);
-        CpRun<0, RMAX * CH, KP, CH>::go(pslot, (unsigned)(bf * CH * 32 * RMAX * 16), g0f + lane * 16);
-        cp_async_commit();
-      } else {
-        prefetch(sf, bf);
-      }
-      sf = (sf + 1 == nx) ? 0 : sf + 1;
-      bf = (bf + 1 == NST) ? 0 : bf + 1;
-      cp_async_wait<NST - 1>();
-      __syncwarp();  // parts copied by other lanes are visible
-      VV dn0[GV];
-#pragma unroll
-      for (int h = 0; h < GV; ++h) {
-        if constexpr (X2) {
-          dn0[h].x = __shfl_sync(FULL, v[RMAX - 1][h].x, below);
-          dn0[h].y = __shfl_sync(FULL, v[RMAX - 1][h].y, below);
+      for (int d = 0; d < nx; ++d) {
+        const int s_next = (s + 1 == nx) ? 0 : s + 1;
+        if constexpr (F) {
+          const char* g0f = reinterpret_cast<const char*>(recq + ((size_t)sf * ny + rh) * 4);
+          CpRun<0, RMAX * CH, KP, CH>::go(pslot, (unsigned)(bf * CH * 32 * RMAX * 16), g0f + lane * 16);
+          cp_async_commit();
         } else {
-          dn0[h] = __shfl_sync(FULL, v[RMAX - 1][h], below);
+          prefetch(sf, bf);
         }
-      }
-      if constexpr (NH == 2) {
-        // lane 0: the other half's top row of the previous step (for the
-        // lower half across the y period; a wall's record ignores it)
-        if (lane == 0) {
-          const float2* xo = reinterpret_cast<const float2*>(&xch[(d + 1) & 1][gi][half ^ 1][0]);
+        sf = (sf + 1 == nx) ? 0 : sf + 1;
+        bf = (bf + 1 == NST) ? 0 : bf + 1;
+        cp_async_wait<NST - 1>();
+        __syncwarp();  // parts copied by other lanes are visible
+        VV dn0[GV];
 #pragma unroll
-          for (int h = 0; h < GV; ++h) dn0[h] = xo[h];
-        }
-      }
-      if (F || active) {
-        uint32_t pk[RMAX];
-        T tls[RMAX];
-        // uniform hot column: the hot row of this step is register row rs of
-        // whichever lane holds it; its K_x dot accumulates under a predicate
-        const int rs = (d + d0 + 1) & (RMAX - 1);
-        float2 hk = make_float2(0.f, 0.f);
-        uint32_t pkh = 0;
-        VV K2v[X2 ? GV : 1];
-        if constexpr (X2) {
-          if (F || uni_hot) {
-#pragma unroll
-            for (int h = 0; h < GV; ++h) K2v[h] = reinterpret_cast<const float2*>(kcoef[wib][0])[h];
+        for (int h = 0; h < GV; ++h) {
+          if constexpr (X2) {
+            dn0[h].x = __shfl_sync(FULL, v[RMAX - 1][h].x, below);
+            dn0[h].y = __shfl_sync(FULL, v[RMAX - 1][h].y, below);
+          } else {
+            dn0[h] = __shfl_sync(FULL, v[RMAX - 1][h], below);
           }
         }
-        // branch-free update of all rows of the step (top row first: the row
-        // below still holds its previous value, the y upwind neighbour)
+        if constexpr (NH == 2) {
+          // lane 0: the other half's top row of the previous step (for the
+          // lower half across the y period; a wall's record ignores it)
+          if (lane == 0) {
+            const float2* xo = reinterpret_cast<const float2*>(&xch[(d + 1) & 1][gi][half ^ 1][0]);
 #pragma unroll
-        for (int rr = 0; rr < RMAX; ++rr) {
-          const int r = RMAX - 1 - rr;
-          if (RFIXED || r >= rb) {
-            const int slot = rec_slot<RMAX>(lane, r);
-            const T* rc0 = reinterpret_cast<const T*>(&recbuf[wib][cur][0][slot]);
-            const T* rc1 = reinterpret_cast<const T*>(&recbuf[wib][cur][CH - 1][slot]);
-            const T src = rc0[0], twx = rc0[1];
-            const T twy = CH == 1 ? rc0[2] : rc1[0];
-            const uint32_t packed = rec_bits(CH == 1 ? rc0[3] : rc1[1]);
-            const bool wx = packed & REC_WIN_X, wy = packed & REC_WIN_Y;
-            const bool jump = packed & REC_JUMP;
-            const bool below_in_lane = RFIXED ? (r > 0) : (r > rb);
-            T sval = T(1);
-            if (HAS_S) sval = (T)__ldg(sv_ptr + (packed & REC_CELL_MASK));
+            for (int h = 0; h < GV; ++h) dn0[h] = xo[h];
+          }
+        }
+        if (F || active) {
+          uint32_t pk[RMAX];
+          T tls[RMAX];
+          // uniform hot column: the hot row of this step is register row rs of
+          // whichever lane holds it; its K_x dot accumulates under a predicate
+          const int rs = (d + d0 + 1) & (RMAX - 1);
+          float2 hk = make_float2(0.f, 0.f);
+          uint32_t pkh = 0;
+          VV K2v[X2 ? GV : 1];
+          if constexpr (X2) {
+            if (F || uni_hot) {
+#pragma unroll
+              for (int h = 0; h < GV; ++h) K2v[h] = reinterpret_cast<const float2*>(kcoef[wib][0])[h];
+            }
+          }
+          // branch-free update of all rows of the step (top row first: the row
+          // below still holds its previous value, the y upwind neighbour)
+#pragma unroll
+          for (int rr = 0; rr < RMAX; ++rr) {
+            const int r = RMAX - 1 - rr;
+            if (RFIXED || r >= rb) {
+              const int slot = rec_slot<RMAX>(lane, r);
+              const T* rc0 = reinterpret_cast<const T*>(&recbuf[wib][cur][0][slot]);
+              const T* rc1 = reinterpret_cast<const T*>(&recbuf[wib][cur][CH - 1][slot]);
+              const T src = rc0[0], twx = rc0[1];
+              const T twy = CH == 1 ? rc0[2] : rc1[0];
+              const uint32_t packed = rec_bits(CH == 1 ? rc0[3] : rc1[1]);
+              const bool wx = packed & REC_WIN_X, wy = packed & REC_WIN_Y;
+              const bool jump = packed & REC_JUMP;
+              const bool below_in_lane = RFIXED ? (r > 0) : (r > rb);
+              T sval = T(1);
+              if (HAS_S) sval = (T)__ldg(sv_ptr + (packed & REC_CELL_MASK));
+              if constexpr (X2) {
+                // deviation form: u_a - T_L,cell = m_a psi_a + t_a, with the
+                // upwind row's psi (m = 1, t = its T_L minus this cell's, the
+                // jump included on the jump column) or a wall (m = 0, t =
+                // T_w - T_L,cell); psi = A_x (u_x - T_L) + A_y (u_y - T_L).
+                // The weight of T_L is exactly 1 - A_x - A_y whatever the float
+                // rounding of A_x and A_y, and no float value carries T_L
+                const float mx = wx ? 0.f : 1.f, my = wy ? 0.f : 1.f;
+                const float2 mx2 = make_float2(mx, mx), tx2 = make_float2(twx, twx);
+                const float2 my2 = make_float2(my, my), ty2 = make_float2(twy, twy);
+                float2 tlp = make_float2(0.f, 0.f);
+#pragma unroll
+                for (int h = 0; h < GV; ++h) {
+                  const float2 ux = __ffma2_rn(mx2, v[r][h], tx2);  // u_x - T_L,cell
+                  const float2 ud = below_in_lane ? v[r > 0 ? r - 1 : 0][h] : dn0[h];
+                  const float2 uy = __ffma2_rn(my2, ud, ty2);       // u_y - T_L,cell
+                  float2 acc = __fmul2_rn(AYv[h], uy);
+                  acc = __ffma2_rn(AXv[h], ux, acc);
+                  v[r][h] = acc;
+                  tlp = __ffma2_rn(AWv[h], acc, tlp);
+                  if ((F || uni_hot) && r == rs) hk = __ffma2_rn(K2v[h], acc, hk);
+                }
+                if ((F || uni_hot) && r == rs) pkh = packed;
+                pk[r] = packed;
+                tls[r] = tlp.x + tlp.y;
+              } else {
+              T tl = T(0), tl2 = T(0);  // two partial chains of the T_L moment
+              // FP32: the deviation form of the paired path (with s(x):
+              // psi = (beta_x (u_x - T_L) + beta_y (u_y - T_L)) / (s + D));
+              // FP64 carries T_o, the jump premultiplied (JX)
+#pragma unroll
+              for (int g = 0; g < G; ++g) {
+                const T ux = JSEL ? (wx ? twx : VG(r, g)) : (wx ? T(0) : VG(r, g)) + twx;
+                const T ud = below_in_lane ? VG(r > 0 ? r - 1 : 0, g) : dn0[g];
+                const T uy = JSEL ? (wy ? twy : ud) : (wy ? T(0) : ud) + twy;
+                const T jx = (JSEL && jump) ? JX[JSEL ? g : 0] : T(0);
+                T acc;
+                if (!JSEL) acc = AY[g] * uy;
+                else if (HAS_S) acc = fma(AY[g], uy, src + jx);
+                else acc = fma(AY[g], uy, fma(src, A0[g], jx));
+                acc = fma(AX[g], ux, acc);
+                T val;
+                if (HAS_S) {
+                  if (sizeof(T) == 4) val = (T)__fdividef((float)acc, (float)(sval + A0[g]));
+                  else val = acc / (sval + A0[g]);
+                } else {
+                  val = acc;
+                }
+                VG(r, g) = val;
+                if (g & 1) tl2 = fma(AW[g], val, tl2);
+                else tl = fma(AW[g], val, tl);
+              }
+              pk[r] = packed;
+              tls[r] = tl + tl2;
+              }
+            }
+          }
+          if ((F || comb) && s_prev >= 0) comb_rows(s_prev, par ^ 1);
+          // walls per row; the hot column per row too unless uni_hot took it
+          const uint32_t RARE = REC_WOUT_X | REC_WOUT_Y | ((F || uni_hot) ? 0u : (uint32_t)REC_LAST);
+          uint32_t any = 0;
+#pragma unroll
+          for (int r = 0; r < RMAX; ++r)
+            if (RFIXED || r >= rb) any |= pk[r];
+          // cells leaving into a wall, the hot-contact column, flux / record passes
+          if ((any & RARE) || rare_pass) {
+            const T* KX = kcoef[wib][0];
+            const T* KY = kcoef[wib][1];
+            // the coefficients once per step (a generic-address atomic between
+            // rows would otherwise force them to be reloaded)
+            VV KXr[GV], KYr[GV];
             if constexpr (X2) {
-              // deviation form: u_a - T_L,cell = m_a psi_a + t_a, with the
-              // upwind row's psi (m = 1, t = its T_L minus this cell's, the
-              // jump included on the jump column) or a wall (m = 0, t =
-              // T_w - T_L,cell); psi = A_x (u_x - T_L) + A_y (u_y - T_L).
-              // The weight of T_L is exactly 1 - A_x - A_y whatever the float
-              // rounding of A_x and A_y, and no float value carries T_L
-              const float mx = wx ? 0.f : 1.f, my = wy ? 0.f : 1.f;
-              const float2 mx2 = make_float2(mx, mx), tx2 = make_float2(twx, twx);
-              const float2 my2 = make_float2(my, my), ty2 = make_float2(twy, twy);
-              float2 tlp = make_float2(0.f, 0.f);
 #pragma unroll
               for (int h = 0; h < GV; ++h) {
-                const float2 ux = __ffma2_rn(mx2, v[r][h], tx2);  // u_x - T_L,cell
-                const float2 ud = below_in_lane ? v[r > 0 ? r - 1 : 0][h] : dn0[h];
-                const float2 uy = __ffma2_rn(my2, ud, ty2);       // u_y - T_L,cell
-                float2 acc = __fmul2_rn(AYv[h], uy);
-                acc = __ffma2_rn(AXv[h], ux, acc);
-                v[r][h] = acc;
-                tlp = __ffma2_rn(AWv[h], acc, tlp);
-                if ((F || uni_hot) && r == rs) hk = __ffma2_rn(K2v[h], acc, hk);
+                KXr[h] = reinterpret_cast<const float2*>(KX)[h];
+                KYr[h] = reinterpret_cast<const float2*>(KY)[h];
               }
-              if ((F || uni_hot) && r == rs) pkh = packed;
-              pk[r] = packed;
-              tls[r] = tlp.x + tlp.y;
-            } else {
-            T tl = T(0), tl2 = T(0);  // two partial chains of the T_L moment
-            // FP32: the deviation form of the paired path (with s(x):
-            // psi = (beta_x (u_x - T_L) + beta_y (u_y - T_L)) / (s + D));
-            // FP64 carries T_o, the jump premultiplied (JX)
-#pragma unroll
-            for (int g = 0; g < G; ++g) {
-              const T ux = JSEL ? (wx ? twx : VG(r, g)) : (wx ? T(0) : VG(r, g)) + twx;
-              const T ud = below_in_lane ? VG(r > 0 ? r - 1 : 0, g) : dn0[g];
-              const T uy = JSEL ? (wy ? twy : ud) : (wy ? T(0) : ud) + twy;
-              const T jx = (JSEL && jump) ? JX[JSEL ? g : 0] : T(0);
-              T acc;
-              if (!JSEL) acc = AY[g] * uy;
-              else if (HAS_S) acc = fma(AY[g], uy, src + jx);
-              else acc = fma(AY[g], uy, fma(src, A0[g], jx));
-              acc = fma(AX[g], ux, acc);
-              T val;
-              if (HAS_S) {
-                if (sizeof(T) == 4) val = (T)__fdividef((float)acc, (float)(sval + A0[g]));
-                else val = acc / (sval + A0[g]);
-              } else {
-                val = acc;
-              }
-              VG(r, g) = val;
-              if (g & 1) tl2 = fma(AW[g], val, tl2);
-              else tl = fma(AW[g], val, tl);
             }
-            pk[r] = packed;
-            tls[r] = tl + tl2;
-            }
-          }
-        }
-        if ((F || comb) && s_prev >= 0) comb_rows(s_prev, par ^ 1);
-        // walls per row; the hot column per row too unless uni_hot took it
-        const uint32_t RARE = REC_WOUT_X | REC_WOUT_Y | ((F || uni_hot) ? 0u : (uint32_t)REC_LAST);
-        uint32_t any = 0;
 #pragma unroll
-        for (int r = 0; r < RMAX; ++r)
-          if (RFIXED || r >= rb) any |= pk[r];
-        // cells leaving into a wall, the hot-contact column, flux / record passes
-        if ((any & RARE) || rare_pass) {
-          const T* KX = kcoef[wib][0];
-          const T* KY = kcoef[wib][1];
-          // the coefficients once per step (a generic-address atomic between
-          // rows would otherwise force them to be reloaded)
-          VV KXr[GV], KYr[GV];
-          if constexpr (X2) {
+            for (int r = 0; r < RMAX; ++r) {
+              if (!(RFIXED || r >= rb)) continue;
+              const uint32_t packed = pk[r];
+              if (!(packed & REC_SOLID) || !((packed & RARE) || rare_pass)) continue;
+              const int cell = (int)(packed & REC_CELL_MASK);
+              const bool last = packed & REC_LAST;
+              if constexpr (PASS) {
+                if (rec_only) {
+                  T* rec = reinterpret_cast<T*>(gm.rec);
 #pragma unroll
-            for (int h = 0; h < GV; ++h) {
-              KXr[h] = reinterpret_cast<const float2*>(KX)[h];
-              KYr[h] = reinterpret_cast<const float2*>(KY)[h];
-            }
-          }
+                  for (int g = 0; g < G; ++g)
+                    if (rsl[g] >= 0) rec[(size_t)rsl[g] * gm.n_cells + cell] = VG(r, g);
+                  continue;
+                }
 #pragma unroll
-          for (int r = 0; r < RMAX; ++r) {
-            if (!(RFIXED || r >= rb)) continue;
-            const uint32_t packed = pk[r];
-            if (!(packed & REC_SOLID) || !((packed & RARE) || rare_pass)) continue;
-            const int cell = (int)(packed & REC_CELL_MASK);
-            const bool last = packed & REC_LAST;
-            if constexpr (PASS) {
-              if (rec_only) {
-                T* rec = reinterpret_cast<T*>(gm.rec);
-#pragma unroll
-                for (int g = 0; g < G; ++g)
-                  if (rsl[g] >= 0) rec[(size_t)rsl[g] * gm.n_cells + cell] = VG(r, g);
+                T loc[NH == 2 ? G : 1];
+                T* sc = NH == 2 ? loc : scratch;
+                for (int g = 0; g < G; ++g) sc[g] = VG(r, g);
+                phi += cell_epilogue_2d<T, G>(gm, sc, cell, packed, last, o0, cnt, sx, sy,
+                                              flags, kx_sum);
                 continue;
               }
-#pragma unroll
-              T loc[NH == 2 ? G : 1];
-              T* sc = NH == 2 ? loc : scratch;
-              for (int g = 0; g < G; ++g) sc[g] = VG(r, g);
-              phi += cell_epilogue_2d<T, G>(gm, sc, cell, packed, last, o0, cnt, sx, sy,
-                                            flags, kx_sum);
-              continue;
-            }
-            if (packed & (REC_WOUT_X | ((F || uni_hot) ? 0u : (uint32_t)REC_LAST))) {
-              const T sk = kdot(KX, KXr, r);
-              if (packed & REC_WOUT_X) {
-                atomicAdd(wacc + (size_t)cell * 6 + out_x_side, widen(sk));
-              } else {
-                hot[r] = sk;
-                ++n_hot;
+              if (packed & (REC_WOUT_X | ((F || uni_hot) ? 0u : (uint32_t)REC_LAST))) {
+                const T sk = kdot(KX, KXr, r);
+                if (packed & REC_WOUT_X) {
+                  atomicAdd(wacc + (size_t)cell * 6 + out_x_side, widen(sk));
+                } else {
+                  hot[r] = sk;
+                  ++n_hot;
+                }
+              }
+              if (packed & REC_WOUT_Y) {
+                const T sy_k = kdot(KY, KYr, r);
+                atomicAdd(wacc + (size_t)cell * 6 + out_y_side, widen(sy_k));
               }
             }
-            if (packed & REC_WOUT_Y) {
-              const T sy_k = kdot(KY, KYr, r);
-              atomicAdd(wacc + (size_t)cell * 6 + out_y_side, widen(sy_k));
+          }
+          if constexpr (X2 && RFIXED && !PASS) {
+            if (F || uni_hot) {
+              if ((pkh & (REC_LAST | REC_SOLID | REC_WOUT_X)) == (REC_LAST | REC_SOLID)) {
+                hot8 += hk.x + hk.y;
+                ++n_hot;
+              }
+              if (rs == RMAX - 1) {
+                hot_d += widen(hot8);
+                hot8 = 0.f;
+              }
             }
           }
-        }
-        if constexpr (X2 && RFIXED && !PASS) {
-          if (F || uni_hot) {
-            if ((pkh & (REC_LAST | REC_SOLID | REC_WOUT_X)) == (REC_LAST | REC_SOLID)) {
-              hot8 += hk.x + hk.y;
-              ++n_hot;
-            }
-            if (rs == RMAX - 1) {
-              hot_d += widen(hot8);
-              hot8 = 0.f;
-            }
+          // the moment atomics come after all rows: a generic-address atomic
+          // between two rows would keep the next row's shared-memory loads from
+          // being scheduled ahead of it
+          if (F || tr_atom) {
+#pragma unroll
+            for (int r = 0; r < RMAX; ++r)
+              if (RFIXED || r >= rb) tlbuf[par][wib][jl + r - rb] = (pk[r] & REC_SOLID) ? tls[r] : T(0);
+          } else {
+#pragma unroll
+            for (int r = 0; r < RMAX; ++r)
+              if ((RFIXED || r >= rb) && (pk[r] & REC_SOLID))
+                atomicAdd(tl_acc + (pk[r] & REC_CELL_MASK), X2 ? widen(tls[r]) : (double)tls[r]);
           }
         }
-        // the moment atomics come after all rows: a generic-address atomic
-        // between two rows would keep the next row's shared-memory loads from
-        // being scheduled ahead of it
-        if (F || tr_atom) {
+        if constexpr (NH == 2) {
+          if (lane == 31)
 #pragma unroll
-          for (int r = 0; r < RMAX; ++r)
-            if (RFIXED || r >= rb) tlbuf[par][wib][jl + r - rb] = (pk[r] & REC_SOLID) ? tls[r] : T(0);
-        } else {
-#pragma unroll
-          for (int r = 0; r < RMAX; ++r)
-            if ((RFIXED || r >= rb) && (pk[r] & REC_SOLID))
-              atomicAdd(tl_acc + (pk[r] & REC_CELL_MASK), X2 ? widen(tls[r]) : (double)tls[r]);
+            for (int h = 0; h < GV; ++h)
+              reinterpret_cast<float2*>(&xch[d & 1][gi][half][0])[h] = v[RMAX - 1][h];
         }
-      }
-      if constexpr (NH == 2) {
-        if (lane == 31)
+        if (F || comb) {
+          __syncthreads();
+          s_prev = s;
+          par ^= 1;
+        } else if (tr_atom) {
+          if (NH == 2) __syncthreads();  // the exchange of the top rows
+          else __syncwarp();
+          double* row = tlq + (size_t)s * ny + rh + lane;
 #pragma unroll
-          for (int h = 0; h < GV; ++h)
-            reinterpret_cast<float2*>(&xch[d & 1][gi][half][0])[h] = v[RMAX - 1][h];
+          for (int r = 0; r < RMAX; ++r)
+            if (RFIXED && full_run ? true : 32 * r + lane < ny)
+              atomicAdd(row + 32 * r, (double)tlbuf[par][wib][32 * r + lane]);
+          if (NH == 2) par ^= 1;
+        } else if (NH == 2) {
+          __syncthreads();
+        }
+        s = s_next;
+        cur = (cur + 1 == NST) ? 0 : cur + 1;
+        __syncwarp();
       }
-      if (F || comb) {
-        __syncthreads();
-        s_prev = s;
-        par ^= 1;
-      } else if (tr_atom) {
-        if (NH == 2) __syncthreads();  // the exchange of the top rows
-        else __syncwarp();
-        double* row = tlq + (size_t)s * ny + rh + lane;
-#pragma unroll
-        for (int r = 0; r < RMAX; ++r)
-          if (RFIXED && full_run ? true : 32 * r + lane < ny)
-            atomicAdd(row + 32 * r, (double)tlbuf[par][wib][32 * r + lane]);
-        if (NH == 2) par ^= 1;
-      } else if (NH == 2) {
-        __syncthreads();
-      }
-      s = s_next;
-      cur = (cur + 1 == NST) ? 0 : cur + 1;
-      __syncwarp();
-    }
     };
     if constexpr (X2 && RFIXED && !PASS && NH == 1 && G == 8 && RMAX == 8) {
       if (comb && uni_hot && tpp == 32) step_loop(std::true_type{});
