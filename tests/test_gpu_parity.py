@@ -283,3 +283,29 @@ def test_single_solve_autotune(precision):
     assert (st2["kernel"], st2["group_size"], st2["rows_per_thread"]) == \
         (st["kernel"], st["group_size"], st["rows_per_thread"])
     _check(wl, pr, ref, s2, precision)
+
+
+def test_fast_step_loop_8x8_tall_cell():
+    """The 8 x 8 FP32 form's compile-time step loop (two steps per trip) runs
+    when the rows fill the 32 lanes (N_y = 256), the block combines four
+    groups of one quadrant and nx is a multiple of 8: a 16 x 256 cell with a
+    square pore, 2 bins x 16 directions, against the FP64 oracle at the
+    mixed bars, and against the same mesh on the general loop (8 x 4 rows,
+    two warps per group) within the T_L bar."""
+    from paper_2106_02764_gb300 import inputs as I
+    L, nx, ny = 100e-9, 16, 256
+    Ly = L * ny / nx
+    wl = I.make_2d("fast256", nx, L, [], 2, I.circle_quadrature(16))
+    wl.mask = I.pores_mask(nx, ny, L, Ly, [I.square_pore(L, Ly, 0.1, x=0.35 * L, y=0.6 * Ly)])
+    wl.shape = (nx, ny, 1)
+    wl.lengths = (L, Ly, 0.0)
+    pr, ref = oracle(wl)
+    s, st = gpu(wl, "mixed", group_size=8, rows_per_thread=8)
+    assert st["group_size"] == 8 and st["rows_per_thread"] == 8 and st["kernel"] == 2
+    assert st["threads_per_block"] == 128  # four one-warp groups per block: the block combine
+    b, sb = gpu(wl, "mixed", group_size=8, rows_per_thread=4)
+    assert sb["rows_per_thread"] == 4
+    TL, TLb = solid_vector(pr, s.T_L()), solid_vector(pr, b.T_L())
+    assert abs(s.kappa_eff - ref.kappa) <= KAPPA_RTOL["mixed"] * abs(ref.kappa)
+    assert np.abs(TL - ref.T_L).max() <= TL_ATOL
+    assert np.abs(TL - TLb).max() <= TL_ATOL
