@@ -259,8 +259,12 @@ __global__ void gauge_kernel(const uint8_t* code, const double* TL, int n, doubl
 // With psi the recorded fields are deviations T_o - T_L (deviation-form
 // sweeps): then T_o - T_L is the record itself and T_rev = record + T_L.
 // Block: 32 consecutive cells (x) times GC_SLICES slices of the records (y);
-// each thread sums every GC_SLICES-th record of its cell (coalesced loads
-// across the warp), the slices are added in shared memory in a fixed order.
+// each thread takes every GC_SLICES-th record k of its cell (coalesced loads
+// across the warp) whose reverse comes later, and adds the terms of both
+// ordinates of the pair from the two loaded fields; the slices are added in
+// shared memory in a fixed order.  Deviation-form (FP32) records: products
+// and the thread's sum in FP32 (the fields themselves are FP32), widened
+// once per thread.
 constexpr int GC_SLICES = 8;
 
 template <typename T>
@@ -272,10 +276,31 @@ __global__ void __launch_bounds__(32 * GC_SLICES) grad_contract_kernel(
   double acc = 0.0;
   if (c < n && (code[c] & CODE_SOLID)) {
     const double tl = TL[c];
-    for (int k = threadIdx.y; k < n_rec; k += GC_SLICES) {
-      const double f = (double)rec[(size_t)k * n + c];
-      const double b = (double)rec[(size_t)rev_local[k] * n + c];
-      acc += psi ? a_rec[k] * (b + tl) * f : a_rec[k] * b * (f - tl);
+    if (sizeof(T) == 4 && psi) {
+      const float tlf = (float)tl;
+      float accf = 0.f;
+      for (int k = threadIdx.y; k < n_rec; k += GC_SLICES) {
+        const int rk = rev_local[k];
+        if (rk < k) continue;  // the pair's terms were added at rk
+        const float f = (float)rec[(size_t)k * n + c];
+        if (rk == k) {
+          accf = fmaf((float)a_rec[k] * (f + tlf), f, accf);
+          continue;
+        }
+        const float b = (float)rec[(size_t)rk * n + c];
+        accf = fmaf((float)a_rec[k] * (b + tlf), f, accf);
+        accf = fmaf((float)a_rec[rk] * (f + tlf), b, accf);
+      }
+      acc = (double)accf;
+    } else {
+      for (int k = threadIdx.y; k < n_rec; k += GC_SLICES) {
+        const int rk = rev_local[k];
+        if (rk < k) continue;
+        const double f = (double)rec[(size_t)k * n + c];
+        const double b = rk == k ? f : (double)rec[(size_t)rk * n + c];
+        acc += psi ? a_rec[k] * (b + tl) * f : a_rec[k] * b * (f - tl);
+        if (rk != k) acc += psi ? a_rec[rk] * (f + tl) * b : a_rec[rk] * f * (b - tl);
+      }
     }
   }
   part[threadIdx.y][threadIdx.x] = acc;
