@@ -417,12 +417,13 @@ def launches_per_solve(iterations, check_every):
     """Kernels one mixed Anderson solve launches: the first guess (cluster CG)
     and five start-of-solve kernels (state, wall temperatures, records, their
     deviation-form difference fields, Anderson history), then per launched
-    iteration the sweep, finalize, its tail, the three Anderson kernels and
-    the records' difference fields.  Iterations go in graph chunks of
-    check_every and a solve stops inside a chunk, whose remaining iterations
-    launch and return at once."""
+    iteration the sweep, finalize, the zeroing of the skewed T_L partials,
+    the finalisation tail, the three Anderson kernels and the records'
+    difference fields.  Iterations go in graph chunks of check_every and a
+    solve stops inside a chunk, whose remaining iterations launch and return
+    at once."""
     launched = -(-int(iterations) // int(check_every)) * int(check_every)
-    return 6 + 7 * launched
+    return 6 + 8 * launched
 
 
 def main():

@@ -56,8 +56,7 @@ __global__ void finalize_kernel(const GeomDev* geoms) {
         p[q] = g.tlq3[k3[q]];
       }
       t = ((p[0] + p[1]) + (p[2] + p[3])) + ((p[4] + p[5]) + (p[6] + p[7]));
-#pragma unroll
-      for (int q = 0; q < 8; ++q) g.tlq3[k3[q]] = 0.0;
+      // (the skewed partials are zeroed by tlq_zero_kernel, in their own order)
     } else if (!g.tlq) {  // per-cell accumulator
       t = TL_acc[c];
       TL_acc[c] = 0.0;
@@ -73,8 +72,6 @@ __global__ void finalize_kernel(const GeomDev* geoms) {
         p[q] = g.tlq[k[q]];
       }
       t += (p[0] + p[1]) + (p[2] + p[3]);
-#pragma unroll
-      for (int q = 0; q < 4; ++q) g.tlq[k[q]] = 0.0;
     }
     if (g.psi) {
       // deviation form: the accumulators hold sums of psi = T_o - T_L, so
@@ -131,6 +128,22 @@ __global__ void finalize_kernel(const GeomDev* geoms) {
     for (int w = 0; w < (int)((blockDim.x + 31) >> 5); ++w) m = fmax(m, red[w]);
     g.blk_part[blockIdx.x] = m;
   }
+}
+
+// After finalize_kernel: the skewed T_L partials it read go back to zero in
+// their own (coalesced) order; zeroing them per cell in the finalisation
+// scatters one 32-byte sector per value (config 2: 13 us of a 0.10 ms
+// finalisation, Anderson and records step).  Grid: x = blocks, y = geometry.
+__global__ void tlq_zero_kernel(const GeomDev* geoms) {
+  const GeomDev& g = geoms[blockIdx.y];
+  double* q = g.tlq ? g.tlq : g.tlq3;
+  if (!q) return;
+  const long n = (long)g.n_cells * (g.tlq ? 4 : 8);
+  const long n2 = n / 2;  // double2 stores (the arrays are 16-byte aligned)
+  double2* q2 = reinterpret_cast<double2*>(q);
+  for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n2; i += (long)gridDim.x * blockDim.x)
+    q2[i] = make_double2(0.0, 0.0);
+  if ((n & 1) && blockIdx.x == 0 && threadIdx.x == 0) q[n - 1] = 0.0;
 }
 
 // After finalize_kernel (one warp per geometry): max |dT_L| over the block
@@ -542,6 +555,7 @@ cudaError_t launch_finalize(const GeomDev* geoms_dev, int n_geoms, int precision
   dim3 grid(blocks, n_geoms);
   if (precision == 0) finalize_kernel<double><<<grid, 256, 0, st>>>(geoms_dev);
   else finalize_kernel<float><<<grid, 256, 0, st>>>(geoms_dev);
+  tlq_zero_kernel<<<grid, 256, 0, st>>>(geoms_dev);
   finalize_tail_kernel<<<n_geoms, 32, 0, st>>>(geoms_dev, blocks);
   return cudaGetLastError();
 }
